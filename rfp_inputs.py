@@ -1,0 +1,102 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+This module holds only input recipes (random matrices with a prescribed
+structure); none of the factorization, solve, inversion or packing
+arithmetic lives here.  Every generator is a pure function of its arguments.
+
+Recipes (the paper publishes no matrices; these are the workloads the
+benchmark configurations describe):
+
+* ``spd_bbt(n, seed)``: B with i.i.d. uniform[-1, 1] entries drawn from
+  ``numpy.random.default_rng(seed)`` (PCG64), A = B B^T / n + I.  The
+  condition number is O(1-10).  ``rhs(...)`` continues the same generator.
+* ``spd_spectrum(n, seed, kappa)``: A = Q diag(lam) Q^T with Q Haar-random
+  orthogonal (QR of a Gaussian matrix, signs fixed by diag(R) > 0), lam_1 = 1,
+  lam_n = kappa and the others 10^U(0, log10 kappa): the 2-norm condition
+  number is exactly kappa.  For n > 4096 the same recipe runs on a CUDA device
+  with torch in FP64 (device RNG) when one is present.
+* ``spd_integer_factor(n, seed)``: A = L0 L0^T with L0 unit lower triangular
+  with small integer entries; the exact Cholesky factor is L0.
+* ``pascal(n)``: P_ij = C(i+j, i); its Cholesky factor is L_ij = C(i, j).
+"""
+from __future__ import annotations
+
+from math import comb
+
+import numpy as np
+
+
+def spd_bbt(n: int, seed: int = 0, return_rng: bool = False):
+    rng = np.random.default_rng(seed)
+    B = rng.uniform(-1.0, 1.0, (n, n))
+    A = B @ B.T / max(n, 1) + np.eye(n)
+    A = 0.5 * (A + A.T)
+    A = np.asfortranarray(A)
+    return (A, rng) if return_rng else A
+
+
+def rhs(n: int, nrhs: int, rng=None, seed: int | None = None):
+    if rng is None:
+        rng = np.random.default_rng(seed)
+    return np.asfortranarray(rng.uniform(-1.0, 1.0, (n, nrhs)))
+
+
+def spectrum(n: int, kappa: float, rng) -> np.ndarray:
+    if n == 1:
+        return np.ones(1)
+    lam = 10.0 ** rng.uniform(0.0, np.log10(kappa), n)
+    lam[0], lam[-1] = 1.0, float(kappa)
+    return lam
+
+
+def spd_spectrum(n: int, seed: int = 0, kappa: float = 1e4, device=None):
+    """A = Q diag(lam) Q^T, Haar Q.  Returns numpy (CPU) unless ``device`` is a
+    torch CUDA device, in which case a torch FP64 tensor on that device."""
+    if device is not None:
+        import torch
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        G = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+        Q, R = torch.linalg.qr(G)
+        Q *= torch.sign(torch.diagonal(R)).unsqueeze(0)
+        del G, R
+        u = torch.rand(n, dtype=torch.float64, device=device, generator=g)
+        lam = 10.0 ** (u * np.log10(kappa))
+        lam[0], lam[-1] = 1.0, float(kappa)
+        A = (Q * lam.unsqueeze(0)) @ Q.T
+        del Q
+        return 0.5 * (A + A.T)  # exactly symmetric: row- and column-major agree
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    Q *= np.sign(np.diag(R))[None, :]
+    lam = spectrum(n, kappa, rng)
+    A = (Q * lam[None, :]) @ Q.T
+    return np.asfortranarray(0.5 * (A + A.T))
+
+
+def spd_integer_factor(n: int, seed: int = 0, lo: int = -2, hi: int = 2):
+    """(A, L0) with A = L0 L0^T exactly in FP64 (small integers)."""
+    rng = np.random.default_rng(seed)
+    L0 = np.tril(rng.integers(lo, hi + 1, (n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L0 @ L0.T
+    return np.asfortranarray(A), L0
+
+
+def pascal(n: int):
+    """(P, L) with P_ij = C(i+j, i) and L_ij = C(i, j) (0-based)."""
+    P = np.array([[comb(i + j, i) for j in range(n)] for i in range(n)], dtype=np.float64)
+    L = np.array([[comb(i, j) for j in range(n)] for i in range(n)], dtype=np.float64)
+    return np.asfortranarray(P), L
+
+
+def second_difference(n: int):
+    """(K, K^{-1}) for the tridiagonal [-1, 2, -1] matrix; its inverse is
+    min(i,j) (n+1-max(i,j)) / (n+1) with 1-based i, j."""
+    K = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    i = np.arange(1, n + 1)
+    Kinv = np.minimum.outer(i, i) * (n + 1 - np.maximum.outer(i, i)) / (n + 1)
+    return np.asfortranarray(K), Kinv
+
+
+LAYOUTS = [(t, u) for t in "NT" for u in "LU"]
