@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the RFPF Cholesky hot path on GB300.
+
+One step = one pass of the whole path over one synthetic SPD matrix of order
+n = 16384 held in one of the eight RFPF layouts (step s uses layout s mod 8):
+  rfp_dpack (full -> RFPF), rfp_dpftrf, rfp_dpftrs (nrhs = 256),
+  rfp_dpftri, rfp_dunpack (RFPF -> full, the inverse).
+A = Q diag(lam) Q^T, Q Haar-random orthogonal, lam log-uniform on [1, 1e4]
+(rfp_inputs.spd_spectrum, seed 0); B uniform[-1, 1].  Inputs are resident in
+HBM before the timed region and larger than L2 (the RFP array alone is
+1.07 GB), so no L2 flush is needed.
+
+Reported metric (the benchmark spec): PFTRF+PFTRS TFLOP/s = (n^3/3 + 2 n^2 nrhs)
+summed over the timed steps / the device time of those two calls (CUDA
+events on the launching stream).  The other rows of the step are reported in
+"breakdown".  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PFTRF+PFTRS TFLOP/s & % peak; served solves/s, p50/p99 at ≤1e-12 bwd err"
+LAYOUTS = [(t, u) for t in "NT" for u in "LU"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--nrhs", type=int, default=256)
+    p.add_argument("--kappa", type=float, default=1e4)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-n", type=int, default=4096, help="oracle sample size (CPU legs)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sms = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (cpu_baseline and --impl reference)
+
+def oracle_sample(n: int, nrhs: int, kappa: float, seed: int = 0):
+    """Time the plain oracle's PFTRF + PFTRS on an n x n matrix of the same
+    recipe; returns (TFLOP/s, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    import rfp_inputs as gen
+    from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
+    A = gen.spd_spectrum(n, seed=seed, kappa=kappa)
+    B = gen.rhs(n, nrhs, seed=seed + 1)
+    arf = oracle.pack("N", "L", A)
+    t0 = time.perf_counter()
+    fac, info = oracle.pftrf("N", "L", n, arf)
+    oracle.pftrs("N", "L", n, fac, B)
+    dt = time.perf_counter() - t0
+    assert info == 0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return (pftrf_flops(n) + pftrs_flops(n, nrhs)) / dt / 1e12, dt, threads
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    nrhs = max(1, args.nrhs * args.cpu_n // args.n)
+    times, rates = [], []
+    for s in range(args.warmup + args.steps):
+        rate, dt, threads = oracle_sample(args.cpu_n, nrhs, args.kappa, seed=s)
+        if s >= args.warmup:
+            times.append(dt)
+            rates.append(rate)
+    total_flops = len(times) * ((args.cpu_n ** 3) / 3 + 2 * args.cpu_n ** 2 * nrhs)
+    value = total_flops / sum(times) / 1e12
+    sample = (f"plain C oracle PFTRF+PFTRS (unpack, textbook Cholesky, substitution), "
+              f"n={args.cpu_n}, nrhs={nrhs}, layout N/L, same spectrum recipe (kappa="
+              f"{args.kappa:g}), one matrix per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP64 SPD RFPF PFTRF+PFTRS, oracle sample n={args.cpu_n} "
+                               f"(of n={args.n}), nrhs={nrhs}", "kappa": args.kappa},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+
+def fp64_peak_tflops(sm_mhz: float | None) -> float:
+    """FP64 FMA peak of GB300 from unit counts and clock: 152 SMs x
+    FP64_FMA_PER_SM_CLK FMAs x 2 flops x SM clock (MHz)."""
+    from paper_0901_1696_gb300.peaks import FP64_FMA_PER_SM_CLK, SM_COUNT, SM_MAX_MHZ
+    mhz = sm_mhz or SM_MAX_MHZ
+    return SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+
+
+def run_ours(args, rank: int, world: int):
+    import numpy as np
+    import torch
+
+    import rfp_inputs as gen
+    from paper_0901_1696_gb300 import binding as rfp
+    from paper_0901_1696_gb300.flops import pack_bytes, pftrf_flops, pftri_flops, pftrs_flops
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = rfp.library()
+    n, nrhs = args.n, args.nrhs
+    nt = n * (n + 1) // 2
+
+    A = gen.spd_spectrum(n, seed=0, kappa=args.kappa, device=dev)     # symmetric: col-major
+    Bh = gen.rhs(n, nrhs, seed=1)
+    B0 = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev)          # (nrhs, n) = col-major
+    X = torch.empty_like(B0)
+    arf = torch.empty(nt, dtype=torch.float64, device=dev)
+    Ainv = torch.zeros(n, n, dtype=torch.float64, device=dev)
+    infos = torch.zeros(args.warmup + args.steps, 2, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = ["pack", "pftrf", "pftrs", "pftri", "unpack"]
+
+    def step(s, evs=None):
+        transr, uplo = LAYOUTS[s % len(LAYOUTS)]
+        rec = (lambda i: evs[i].record(stream)) if evs else (lambda i: None)
+        rec(0)
+        lib.rfp_dpack(transr, uplo, n, A, n, arf, stream)
+        rec(1)
+        lib.rfp_dpftrf(transr, uplo, n, arf, infos[s, 0:1], stream)
+        rec(2)
+        X.copy_(B0)
+        rec(3)
+        lib.rfp_dpftrs(transr, uplo, n, nrhs, arf, X, n, stream)
+        rec(4)
+        lib.rfp_dpftri(transr, uplo, n, arf, infos[s, 1:2], stream)
+        rec(5)
+        lib.rfp_dunpack(transr, uplo, n, arf, Ainv, n, stream)
+        rec(6)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize(dev)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = lib.rfp_kernel_launches()
+    lib.rfp_stage_timing(True)
+    sampler.start()
+    t_begin.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k, evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    stages = lib.rfp_stage_times()
+    lib.rfp_stage_timing(False)
+    launches = lib.rfp_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    total_ms = t_begin.elapsed_time(t_end)
+    assert int(infos.abs().sum().item()) == 0, "a factorization reported info != 0"
+
+    per_row = {r: 0.0 for r in rows}
+    for ev in evs:
+        per_row["pack"] += ev[0].elapsed_time(ev[1])
+        per_row["pftrf"] += ev[1].elapsed_time(ev[2])
+        per_row["pftrs"] += ev[3].elapsed_time(ev[4])
+        per_row["pftri"] += ev[4].elapsed_time(ev[5])
+        per_row["unpack"] += ev[5].elapsed_time(ev[6])
+    K = args.steps
+    metric_ms = per_row["pftrf"] + per_row["pftrs"]
+    metric_flops = K * (pftrf_flops(n) + pftrs_flops(n, nrhs))
+    if dist:
+        t = torch.tensor([metric_ms, total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        metric_ms, total_ms = float(t[0]), float(t[1])
+    value = world * metric_flops / (metric_ms * 1e-3) / 1e12
+
+    # steps of the paper's Fig. 4 (PFTRF) and the dominant kernel's launch:
+    # step 3 (T2 -= S S^T) is a single gemm_nt_kernel<double> launch
+    agg = {}
+    for name, ms in stages:
+        agg[name] = agg.get(name, 0.0) + ms
+    n1 = (n + 1) // 2
+    syrk_ms = agg.get("pftrf.syrk_t2", 0.0) / K
+    # per layout n1/n2 differ by one for odd n; at even n both are n/2
+    syrk_flops = n1 * (n - n1) * (n - n1 + 1)
+    peak = fp64_peak_tflops(clocks["sm_mhz"])
+    achieved = syrk_flops / (syrk_ms * 1e-3) / 1e12 if syrk_ms else None
+    pf = [agg.get(k, 0.0) for k in ("pftrf.potrf_t1", "pftrf.trsm_s", "pftrf.syrk_t2",
+                                    "pftrf.potrf_t2")]
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP64 SPD n={n} RFPF, 8 layouts cycled per step; pack + PFTRF + "
+                               f"PFTRS(nrhs={nrhs}) + PFTRI + unpack", "n": n, "nrhs": nrhs,
+                   "kappa": args.kappa, "matrix": "Q diag(lam) Q^T, Haar Q, log-uniform lam",
+                   "l2": "inputs larger than L2 (RFP 1.07 GB); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "gemm_nt_kernel<double>: PFTRF step 3 (T2 -= S S^T), one launch",
+                     "peak_source": "FP64 FMA pipe: 152 SMs x units x 2 x median SM clock"},
+        "breakdown": {
+            **{f"{r}_ms": per_row[r] / K for r in rows},
+            "pftrf_tflops": pftrf_flops(n) * K / (per_row["pftrf"] * 1e-3) / 1e12,
+            "pftrs_tflops": pftrs_flops(n, nrhs) * K / (per_row["pftrs"] * 1e-3) / 1e12,
+            "pftri_tflops": pftri_flops(n) * K / (per_row["pftri"] * 1e-3) / 1e12,
+            "pack_gbs": pack_bytes(n) * K / (per_row["pack"] * 1e-3) / 1e9,
+            "unpack_gbs": pack_bytes(n) * K / (per_row["unpack"] * 1e-3) / 1e9,
+            "pftrf_step_split": [round(x / sum(pf), 4) for x in pf] if sum(pf) else None,
+            "pftri_steps_ms": {k: v / K for k, v in agg.items() if k.startswith("pftri.")},
+        },
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e_leg(args, lib, A, B0, dev, stream)
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt, threads = oracle_sample(args.cpu_n, max(1, nrhs * args.cpu_n // n), args.kappa)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"plain C oracle PFTRF+PFTRS at n={args.cpu_n}, nrhs="
+                      f"{max(1, nrhs * args.cpu_n // n)}, layout N/L, same recipe ({dt:.1f} s)"}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e_leg(args, lib, A, B0, dev, stream):
+    """The same metric through the C ABI with host buffers: per step the RFP
+    array and B go host -> device from pinned memory, PFTRF + PFTRS run, and
+    X comes back device -> host."""
+    import torch
+
+    from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
+    n, nrhs = args.n, args.nrhs
+    nt = n * (n + 1) // 2
+    arf_d = torch.empty(nt, dtype=torch.float64, device=dev)
+    lib.rfp_dpack("N", "L", n, A, n, arf_d, stream)
+    arf_h = torch.empty(nt, dtype=torch.float64, pin_memory=True)
+    arf_h.copy_(arf_d)
+    B_h = torch.empty_like(B0, device="cpu").pin_memory()
+    B_h.copy_(B0)
+    X_h = torch.empty_like(B_h).pin_memory()
+    X_d = torch.empty_like(B0)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.e2e_steps):
+        arf_d.copy_(arf_h, non_blocking=True)
+        X_d.copy_(B_h, non_blocking=True)
+        lib.rfp_dpftrf("N", "L", n, arf_d, info, stream)
+        lib.rfp_dpftrs("N", "L", n, nrhs, arf_d, X_d, n, stream)
+        X_h.copy_(X_d, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1) / args.e2e_steps
+    assert int(info.item()) == 0
+    return {"value": (pftrf_flops(n) + pftrs_flops(n, nrhs)) / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "h2d_bytes_per_step": nt * 8 + n * nrhs * 8,
+            "d2h_bytes_per_step": n * nrhs * 8, "ms_per_step": ms}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * rfp.h - C ABI of the GB300 (sm_103a) library for Cholesky factorization,
+ * solution and inversion of a symmetric positive definite matrix held in
+ * Rectangular Full Packed Format (RFPF).
+ *
+ * Method: Gustavson, Wasniewski, Dongarra, Langou, "Rectangular Full Packed
+ * Format for Cholesky's Algorithm: Factorization, Solution and Inversion".
+ * Names and argument order follow the LAPACK 3.2 calling sequences listed in
+ * the paper's Table "lapack" (PFTRF, PFTRS, PFTRI, TRTTF, TFTTR), with a
+ * stream argument added and INFO moved to device memory.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - transr: 'N' (array A_R, LDAR x ceil(N/2), column-major) or 'T' (its
+ *    transpose, ceil(N/2) x LDAR); LDAR = N for odd N and N+1 for even N
+ *    (Section 7).  'C' is rejected: the library is real only.
+ *  - uplo: 'L' or 'U', which triangle of the symmetric matrix is stored
+ *    (Section 2, Eq. 1).  Lower/upper case letters are both accepted.
+ *  - The RFP array holds exactly n(n+1)/2 elements, no padding.
+ *  - Every pointer except `info` arguments is a DEVICE pointer owned by the
+ *    caller, aligned to its element size; `info` is a device int32.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All work is enqueued on it; no entry point synchronizes the device.
+ *  - Return value: an immediate host-side result.
+ *      0   success (work enqueued),
+ *     -i   argument i is invalid (LAPACK convention, 1-based), nothing enqueued,
+ *     >0   library error (RFP_ERR_*): a CUDA call failed; the stream's state
+ *          is then whatever CUDA reports.
+ *    Numerical failure is reported asynchronously through *info (see
+ *    rfp_dpftrf / rfp_dpftri).
+ *  - n = 0 (and nrhs = 0 for the solve) return 0 immediately.
+ *  - The library allocates no device memory.
+ *  - The s-variants (float) have the same shapes and semantics in IEEE
+ *    binary32 arithmetic.
+ */
+#ifndef RFP_H
+#define RFP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RFP_OK 0
+#define RFP_ERR_CUDA 1      /* a CUDA runtime call or kernel launch failed */
+
+/*
+ * Block descriptor of one RFPF layout (host only; no GPU needed).
+ *
+ * The logical lower factor is L = [L11 0; L21 L22] (for UPLO='U', L = U^T),
+ * split at n1 as drawn in Figs. 4-6: n1 = ceil(N/2) for 'L', floor(N/2) for
+ * 'U', n2 = N - n1.  Block X in {T1: L11 (n1 x n1, lower), S: L21 (n2 x n1),
+ * T2: L22 (n2 x n2, lower)} has its element (i, j) at array position
+ *     X_off + i + j*ld   if X_trans == 0,
+ *     X_off + j + i*ld   if X_trans == 1.
+ * ld = LDAR for transr='N' and ceil(N/2) for transr='T'.
+ * Returns 0, or -1 / -2 / -3 for an invalid transr / uplo / n.
+ */
+typedef struct rfp_layout {
+    int64_t n, n1, n2, ld;
+    int64_t t1_off, s_off, t2_off;
+    int32_t t1_trans, s_trans, t2_trans;
+} rfp_layout_t;
+
+int rfp_layout(char transr, char uplo, int64_t n, rfp_layout_t *out);
+
+/*
+ * rfp_dpack (TRTTF, Table "lapack"): copy the UPLO triangle of the
+ * column-major n x n matrix A (leading dimension lda >= max(1,n)) into the
+ * RFP array arf.  The other triangle of A is never read.  Bit-exact copy.
+ * Arguments: 1 transr, 2 uplo, 3 n, 4 A, 5 lda, 6 arf, 7 stream.
+ */
+int rfp_dpack(char transr, char uplo, int64_t n, const double *A, int64_t lda,
+              double *arf, void *stream);
+int rfp_spack(char transr, char uplo, int64_t n, const float *A, int64_t lda,
+              float *arf, void *stream);
+
+/*
+ * rfp_dunpack (TFTTR, Table "lapack"): write the UPLO triangle of A from
+ * arf; the other triangle of A is left untouched.  Bit-exact copy.
+ * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 A, 6 lda, 7 stream.
+ */
+int rfp_dunpack(char transr, char uplo, int64_t n, const double *arf, double *A,
+                int64_t lda, void *stream);
+int rfp_sunpack(char transr, char uplo, int64_t n, const float *arf, float *A,
+                int64_t lda, void *stream);
+
+/*
+ * rfp_dpftrf (PFTRF, Section 3, Eqs. 2-4, Fig. 4): Cholesky factorization
+ * A = L L^T (uplo 'L') or A = U^T U (uplo 'U') in place; arf then holds the
+ * factor in the same layout.  Four steps on the blocks: Cholesky of T1,
+ * triangular solve of S, symmetric rank-n1 update of T2, Cholesky of T2.
+ * *info (device) is set to 0, or to j > 0 when the leading minor of order j
+ * is not positive definite (a pivot <= 0 or NaN); arf is then unspecified.
+ * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
+ */
+int rfp_dpftrf(char transr, char uplo, int64_t n, double *arf, int32_t *info,
+               void *stream);
+int rfp_spftrf(char transr, char uplo, int64_t n, float *arf, int32_t *info,
+               void *stream);
+
+/*
+ * rfp_dpftrs (PFTRS, Section 4, Eqs. 5-8, Fig. 4): solve A X = B with the
+ * factor computed by rfp_dpftrf.  B is column-major n x nrhs (ldb >=
+ * max(1,n)) and is overwritten by X.  Forward: L11 Y1 = B1, B2 -= L21 Y1,
+ * L22 Y2 = B2; backward: L22^T X2 = Y2, Y1 -= L21^T X2, L11^T X1 = Y1, where
+ * B1 is rows [0, n1) of B.
+ * Arguments: 1 transr, 2 uplo, 3 n, 4 nrhs, 5 arf, 6 B, 7 ldb, 8 stream.
+ */
+int rfp_dpftrs(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
+               double *B, int64_t ldb, void *stream);
+int rfp_spftrs(char transr, char uplo, int64_t n, int64_t nrhs, const float *arf,
+               float *B, int64_t ldb, void *stream);
+
+/*
+ * rfp_dpftri (PFTRI, Section 5, Eqs. 9-11, Fig. 4): overwrite the factor in
+ * arf with the UPLO triangle of A^{-1} = W^T W (W = L^{-1}), same layout.
+ * *info (device) is set to 0, or to j > 0 when the j-th diagonal entry of the
+ * factor is exactly zero; arf is then unspecified.
+ * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
+ */
+int rfp_dpftri(char transr, char uplo, int64_t n, double *arf, int32_t *info,
+               void *stream);
+int rfp_spftri(char transr, char uplo, int64_t n, float *arf, int32_t *info,
+               void *stream);
+
+/* Text for a return code of this library (static storage, never NULL). */
+const char *rfp_status_string(int status);
+
+/* Name of the last CUDA error seen by the calling host thread inside this
+ * library ("no error" if none). */
+const char *rfp_last_cuda_error(void);
+
+/*
+ * Instrumentation (no effect on results).
+ *
+ * rfp_kernel_launches: number of kernels this library has enqueued in this
+ * process so far (all threads).
+ *
+ * rfp_stage_timing(1) makes the calling host thread record a CUDA event at
+ * the start of each later rfp_?pftrf / pftrs / pftri call and one after each
+ * of its steps (PFTRF: "pftrf.potrf_t1", "pftrf.trsm_s", "pftrf.syrk_t2",
+ * "pftrf.potrf_t2", the four steps of Fig. 4); rfp_stage_timing(0) stops
+ * recording.  Either call clears the history.  rfp_stage_times waits for
+ * the last recorded event, then writes up to `max` step durations in ms (and
+ * the steps' names, static strings) of every call recorded since the last
+ * rfp_stage_timing, in order; it returns the number written, 0 if none, or
+ * -RFP_ERR_CUDA.  At most 8192 events are kept.  Events are created on the
+ * device current when they are first needed.
+ */
+int64_t rfp_kernel_launches(void);
+int rfp_stage_timing(int enable);
+int rfp_stage_times(int max, float *ms, const char **names);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFP_H */

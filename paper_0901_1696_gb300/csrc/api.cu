@@ -1,0 +1,274 @@
+// extern "C" entry points declared in include/rfp.h: argument checks on the
+// host (LAPACK convention: -i for argument i), then the enqueued kernels.
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/rfp.h"
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+// Placement of T1 (L11), S (L21) and T2 (L22) for the eight layouts.  For
+// TRANSR='N' each block starts at row r0, column c0 of A_R (LDAR rows,
+// column-major) and is stored as drawn in Figs. 4-6:
+//   lower, odd : T1 (0,0) as is;  S (n1,0) as is;   T2 (0,1) transposed (L22^T)
+//   lower, even: T1 (1,0);        S (k+1,0);        T2 (0,0) transposed
+//   upper, odd : T1 (n2,0) (=U11^T); S (0,0) transposed (=U12); T2 (n1,0) transposed (=U22)
+//   upper, even: T1 (k+1,0);      S (0,0) transposed; T2 (k,0) transposed
+// TRANSR='T' stores A_R^T (ld = ceil(N/2)): row and column swap roles and
+// every block flips its transposition.
+bool make_layout(char transr, char uplo, int64_t n, Layout *out)
+{
+    const bool lower = (uplo == 'L' || uplo == 'l');
+    const bool trans = (transr == 'T' || transr == 't');
+    const int64_t n1 = lower ? (n + 1) / 2 : n / 2, n2 = n - n1;
+    const bool odd = (n % 2) == 1;
+    const int64_t ldar = odd ? n : n + 1, nc = (n + 1) / 2, k = n / 2;
+    struct RC { int64_t r0, c0; int tr; } b1, bs, b2;
+    if (lower) {
+        if (odd) { b1 = {0, 0, 0}; bs = {n1, 0, 0}; b2 = {0, 1, 1}; }
+        else { b1 = {1, 0, 0}; bs = {k + 1, 0, 0}; b2 = {0, 0, 1}; }
+    } else {
+        if (odd) { b1 = {n2, 0, 0}; bs = {0, 0, 1}; b2 = {n1, 0, 1}; }
+        else { b1 = {k + 1, 0, 0}; bs = {0, 0, 1}; b2 = {k, 0, 1}; }
+    }
+    auto place = [&](RC x) -> Block {
+        if (!trans) return Block{x.r0 + x.c0 * ldar, x.tr};
+        return Block{x.c0 + x.r0 * nc, x.tr ? 0 : 1};
+    };
+    out->n = n; out->n1 = n1; out->n2 = n2;
+    out->ld = trans ? nc : ldar;
+    out->t1 = place(b1); out->s = place(bs); out->t2 = place(b2);
+    return true;
+}
+
+// ---- instrumentation ------------------------------------------------------------
+
+namespace {
+std::atomic<int64_t> g_launch_count{0};
+constexpr size_t kMaxEvents = 8192;
+// Step timing history of one host thread: events[i] closes the step named
+// names[i]; an entry with a null name opens a new routine call.
+struct StageLog {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;      // created lazily, reused across enables
+    std::vector<const char *> names;    // one per recorded event
+};
+thread_local StageLog g_stages;
+
+void stage_record(cudaStream_t st, const char *name)
+{
+    StageLog &g = g_stages;
+    if (!g.enabled || g.names.size() >= kMaxEvents) return;
+    if (g.names.size() == g.pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        g.pool.push_back(e);
+    }
+    cudaEventRecord(g.pool[g.names.size()], st);
+    g.names.push_back(name);
+}
+}  // namespace
+
+void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
+void stage_begin(cudaStream_t st) { stage_record(st, nullptr); }
+void stage_mark(cudaStream_t st, const char *name)
+{
+    if (!g_stages.names.empty()) stage_record(st, name);
+}
+
+}  // namespace rfp
+
+namespace {
+
+thread_local const char *g_last_cuda_error = "no error";
+
+bool valid_transr(char c) { return c == 'N' || c == 'n' || c == 'T' || c == 't'; }
+bool valid_uplo(char c) { return c == 'L' || c == 'l' || c == 'U' || c == 'u'; }
+bool is_lower(char c) { return c == 'L' || c == 'l'; }
+constexpr int64_t kMaxN = int64_t(1) << 24;   // n(n+1)/2 and tile counts stay far from overflow
+
+template <typename T>
+bool aligned(const T *p) { return (reinterpret_cast<uintptr_t>(p) % alignof(T)) == 0; }
+
+int finish(cudaError_t e)
+{
+    if (e == cudaSuccess) return RFP_OK;
+    g_last_cuda_error = cudaGetErrorName(e);
+    return RFP_ERR_CUDA;
+}
+
+template <typename T>
+int pack_entry(char transr, char uplo, int64_t n, T *A, int64_t lda, T *arf, void *stream,
+               bool unpack)
+{
+    // argument numbering differs: pack (A=4, lda=5, arf=6), unpack (arf=4, A=5, lda=6)
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN) return -3;
+    if (n == 0) return RFP_OK;
+    const int argA = unpack ? 5 : 4, argLda = unpack ? 6 : 5, argArf = unpack ? 4 : 6;
+    if (unpack) {
+        if (!arf || !aligned(arf)) return -argArf;
+        if (!A || !aligned(A)) return -argA;
+    } else {
+        if (!A || !aligned(A)) return -argA;
+    }
+    if (lda < (n > 1 ? n : 1)) return -argLda;
+    if (!unpack && (!arf || !aligned(arf))) return -argArf;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    return finish(rfp::pack_copy<T>((cudaStream_t)stream, L, is_lower(uplo), A, lda, arf, unpack));
+}
+
+template <typename T>
+int pftrf_entry(char transr, char uplo, int64_t n, T *arf, int32_t *info, void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN) return -3;
+    if (n > 0 && (!arf || !aligned(arf))) return -4;
+    if (!info || !aligned(info)) return -5;
+    if (n == 0) return finish(cudaMemsetAsync(info, 0, sizeof(int32_t), (cudaStream_t)stream));
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    return finish(rfp::pftrf_impl<T>((cudaStream_t)stream, L, arf, info));
+}
+
+template <typename T>
+int pftrs_entry(char transr, char uplo, int64_t n, int64_t nrhs, const T *arf, T *B, int64_t ldb,
+                void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN) return -3;
+    if (nrhs < 0 || nrhs > (int64_t(1) << 31) - 1) return -4;
+    if (n == 0 || nrhs == 0) return RFP_OK;
+    if (!arf || !aligned(arf)) return -5;
+    if (!B || !aligned(B)) return -6;
+    if (ldb < (n > 1 ? n : 1)) return -7;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    return finish(rfp::pftrs_impl<T>((cudaStream_t)stream, L, arf, B, ldb, nrhs));
+}
+
+template <typename T>
+int pftri_entry(char transr, char uplo, int64_t n, T *arf, int32_t *info, void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN) return -3;
+    if (n > 0 && (!arf || !aligned(arf))) return -4;
+    if (!info || !aligned(info)) return -5;
+    if (n == 0) return finish(cudaMemsetAsync(info, 0, sizeof(int32_t), (cudaStream_t)stream));
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    return finish(rfp::pftri_impl<T>((cudaStream_t)stream, L, arf, info));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rfp_layout(char transr, char uplo, int64_t n, rfp_layout_t *out)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN) return -3;
+    if (!out) return -4;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    out->n = L.n; out->n1 = L.n1; out->n2 = L.n2; out->ld = L.ld;
+    out->t1_off = L.t1.off; out->s_off = L.s.off; out->t2_off = L.t2.off;
+    out->t1_trans = L.t1.trans; out->s_trans = L.s.trans; out->t2_trans = L.t2.trans;
+    return RFP_OK;
+}
+
+int rfp_dpack(char transr, char uplo, int64_t n, const double *A, int64_t lda, double *arf,
+              void *stream)
+{
+    return pack_entry<double>(transr, uplo, n, const_cast<double *>(A), lda, arf, stream, false);
+}
+int rfp_spack(char transr, char uplo, int64_t n, const float *A, int64_t lda, float *arf,
+              void *stream)
+{
+    return pack_entry<float>(transr, uplo, n, const_cast<float *>(A), lda, arf, stream, false);
+}
+int rfp_dunpack(char transr, char uplo, int64_t n, const double *arf, double *A, int64_t lda,
+                void *stream)
+{
+    return pack_entry<double>(transr, uplo, n, A, lda, const_cast<double *>(arf), stream, true);
+}
+int rfp_sunpack(char transr, char uplo, int64_t n, const float *arf, float *A, int64_t lda,
+                void *stream)
+{
+    return pack_entry<float>(transr, uplo, n, A, lda, const_cast<float *>(arf), stream, true);
+}
+
+int rfp_dpftrf(char transr, char uplo, int64_t n, double *arf, int32_t *info, void *stream)
+{
+    return pftrf_entry<double>(transr, uplo, n, arf, info, stream);
+}
+int rfp_spftrf(char transr, char uplo, int64_t n, float *arf, int32_t *info, void *stream)
+{
+    return pftrf_entry<float>(transr, uplo, n, arf, info, stream);
+}
+int rfp_dpftrs(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf, double *B,
+               int64_t ldb, void *stream)
+{
+    return pftrs_entry<double>(transr, uplo, n, nrhs, arf, B, ldb, stream);
+}
+int rfp_spftrs(char transr, char uplo, int64_t n, int64_t nrhs, const float *arf, float *B,
+               int64_t ldb, void *stream)
+{
+    return pftrs_entry<float>(transr, uplo, n, nrhs, arf, B, ldb, stream);
+}
+int rfp_dpftri(char transr, char uplo, int64_t n, double *arf, int32_t *info, void *stream)
+{
+    return pftri_entry<double>(transr, uplo, n, arf, info, stream);
+}
+int rfp_spftri(char transr, char uplo, int64_t n, float *arf, int32_t *info, void *stream)
+{
+    return pftri_entry<float>(transr, uplo, n, arf, info, stream);
+}
+
+const char *rfp_status_string(int status)
+{
+    if (status == RFP_OK) return "success";
+    if (status == RFP_ERR_CUDA) return "a CUDA call failed (see rfp_last_cuda_error)";
+    if (status < 0) return "invalid argument (the value is minus its 1-based position)";
+    return "unknown status";
+}
+
+const char *rfp_last_cuda_error(void) { return g_last_cuda_error; }
+
+int64_t rfp_kernel_launches(void) { return rfp::g_launch_count.load(); }
+
+int rfp_stage_timing(int enable)
+{
+    rfp::g_stages.enabled = enable != 0;
+    rfp::g_stages.names.clear();
+    return RFP_OK;
+}
+
+int rfp_stage_times(int max, float *ms, const char **names)
+{
+    rfp::StageLog &g = rfp::g_stages;
+    if (g.names.empty()) return 0;
+    cudaError_t e = cudaEventSynchronize(g.pool[g.names.size() - 1]);
+    if (e != cudaSuccess) return -finish(e);
+    int k = 0;
+    for (size_t i = 1; i < g.names.size() && k < max; ++i) {
+        if (!g.names[i]) continue;                // start of the next call
+        float t = 0.f;
+        cudaEventElapsedTime(&t, g.pool[i - 1], g.pool[i]);
+        if (ms) ms[k] = t;
+        if (names) names[k] = g.names[i];
+        ++k;
+    }
+    return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+// Blocked PFTRF, PFTRS and PFTRI on the RFP blocks (Sections 3, 4 and 5).
+//
+// Each routine is the paper's 2 x 2 block algorithm on the logical lower
+// factor L = [L11 0; L21 L22] (T1 = L11, S = L21, T2 = L22 as views of the
+// caller's array).  The full-format LAPACK / Level-3 BLAS calls of Fig. 4
+// are replaced by tiled kernels with 64-wide diagonal tiles:
+//   PFTRF: POTRF(T1); S <- S L11^{-T}; T2 <- T2 - S S^T; POTRF(T2)
+//   PFTRS: L11 Y1 = B1; B2 -= L21 Y1; L22 Y2 = B2;
+//          L22^T X2 = Y2; Y1 -= L21^T X2; L11^T X1 = Y1
+//   PFTRI: W21 = -L22^{-1} L21 L11^{-1}; T1 <- W11^T W11 + W21^T W21;
+//          S <- W22^T W21; T2 <- W22^T W22
+// Every step is in place and allocates nothing.  The in-place triangular
+// products are ordered so that no kernel reads a tile another CTA of the same
+// launch writes (right-looking blocked TRTRI and LAUUM below).
+#include <algorithm>
+
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+constexpr int64_t kNb = 64;   // diagonal tile width
+
+#define RFP_TRY(x)                               \
+    do {                                         \
+        cudaError_t e_ = (x);                    \
+        if (e_ != cudaSuccess) return e_;        \
+    } while (0)
+
+// ---- triangle-level building blocks ----------------------------------------
+
+// Right-looking blocked Cholesky of the m x m lower triangle V in place
+// (LAPACK POTRF 'L' on one RFP triangle).  Failure index offset by `base`.
+template <typename T>
+static cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info,
+                                 int64_t base)
+{
+    for (int64_t k0 = 0; k0 < m; k0 += kNb) {
+        const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        RFP_TRY(potrf_tile(st, V.sub(k0, k0), (int)w, info, base + k0));
+        if (k1 < m) {
+            RFP_TRY(trsm_strip(st, V.sub(k1, k0), V.sub(k0, k0), m - k1, (int)w, 1, T(1), info));
+            RFP_TRY(gemm_nt(st, V.sub(k1, k1), V.sub(k1, k0), V.sub(k1, k0), m - k1, m - k1, w,
+                            T(-1), T(1), MASK_LOWER, MASK_NONE, MASK_NONE, info));
+        }
+    }
+    return cudaSuccess;
+}
+
+// X (rows x m) <- X L^{-T}, L the m x m lower triangle V (right-looking).
+template <typename T>
+static cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
+                                          int64_t m, const int32_t *abort)
+{
+    for (int64_t k0 = 0; k0 < m; k0 += kNb) {
+        const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        RFP_TRY(trsm_strip(st, X.sub(0, k0), V.sub(k0, k0), rows, (int)w, 1, T(1), abort));
+        if (k1 < m)
+            RFP_TRY(gemm_nt(st, X.sub(0, k1), X.sub(0, k0), V.sub(k1, k0), rows, m - k1, w,
+                            T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
+    }
+    return cudaSuccess;
+}
+
+// X (rows x m) <- alpha X L^{-1}, L the m x m lower triangle V (columns from
+// the right).
+template <typename T>
+static cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
+                                            int64_t m, T alpha, const int32_t *abort)
+{
+    const int64_t nblk = (m + kNb - 1) / kNb;
+    for (int64_t b = nblk - 1; b >= 0; --b) {
+        const int64_t k0 = b * kNb, k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        const T a = (b == nblk - 1) ? alpha : T(1);
+        RFP_TRY(trsm_strip(st, X.sub(0, k0), V.sub(k0, k0), rows, (int)w, 0, a, abort));
+        if (k0 > 0)   // X(:, 0:k0) = a X(:, 0:k0) - X_b L(k0:k1, 0:k0)
+            RFP_TRY(gemm_nt(st, X, X.sub(0, k0), V.sub(k0, 0).t(), rows, k0, w, T(-1), a,
+                            MASK_NONE, MASK_NONE, MASK_NONE, abort));
+    }
+    return cudaSuccess;
+}
+
+// L X = B in place, B (m x nrhs), L the m x m lower triangle V (forward).
+template <typename T>
+static cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
+                                           int64_t m, const int32_t *abort)
+{
+    for (int64_t k0 = 0; k0 < m; k0 += kNb) {
+        const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        // L_pp X_p = B_p  <=>  X_p^T L_pp^T = B_p^T
+        RFP_TRY(trsm_strip(st, B.sub(k0, 0).t(), V.sub(k0, k0), nrhs, (int)w, 1, T(1), abort));
+        if (k1 < m)   // B(k1:m) -= L(k1:m, p) X_p
+            RFP_TRY(gemm_nt(st, B.sub(k1, 0), V.sub(k1, k0), B.sub(k0, 0).t(), m - k1, nrhs, w,
+                            T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
+    }
+    return cudaSuccess;
+}
+
+// L^T X = B in place, B (m x nrhs), L the m x m lower triangle V (backward).
+template <typename T>
+static cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
+                                         int64_t m, const int32_t *abort)
+{
+    const int64_t nblk = (m + kNb - 1) / kNb;
+    for (int64_t b = nblk - 1; b >= 0; --b) {
+        const int64_t k0 = b * kNb, k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        // L_pp^T X_p = B_p  <=>  X_p^T L_pp = B_p^T
+        RFP_TRY(trsm_strip(st, B.sub(k0, 0).t(), V.sub(k0, k0), nrhs, (int)w, 0, T(1), abort));
+        if (k0 > 0)   // B(0:k0) -= L(p, 0:k0)^T X_p
+            RFP_TRY(gemm_nt(st, B, V.sub(k0, 0).t(), B.sub(k0, 0).t(), k0, nrhs, w, T(-1), T(1),
+                            MASK_NONE, MASK_NONE, MASK_NONE, abort));
+    }
+    return cudaSuccess;
+}
+
+// In-place W = L^{-1} on an m x m lower triangle V.  Right-looking over the
+// block columns p: with X = C_{p-1}^{-1} ... C_1^{-1} held where L was
+// consumed, step p applies C_p^{-1} (block column p of L):
+//   W_pp = L_pp^{-1};  X(p, :p) <- W_pp X(p, :p);
+//   X(i>p, :p) -= L(i, p) X(p, :p);  X(i>p, p) <- -L(i, p) W_pp.
+template <typename T>
+static cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
+{
+    for (int64_t k0 = 0; k0 < m; k0 += kNb) {
+        const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        RFP_TRY(trtri_tile(st, V.sub(k0, k0), (int)w, abort));
+        if (k0 > 0)
+            RFP_TRY(gemm_nt(st, V.sub(k0, 0), V.sub(k0, k0), V.sub(k0, 0).t(), w, k0, w, T(1),
+                            T(0), MASK_NONE, MASK_LOWER, MASK_NONE, abort));
+        if (k1 < m) {
+            if (k0 > 0)
+                RFP_TRY(gemm_nt(st, V.sub(k1, 0), V.sub(k1, k0), V.sub(k0, 0).t(), m - k1, k0, w,
+                                T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
+            RFP_TRY(gemm_nt(st, V.sub(k1, k0), V.sub(k1, k0), V.sub(k0, k0).t(), m - k1, w, w,
+                            T(-1), T(0), MASK_NONE, MASK_NONE, MASK_UPPER, abort));
+        }
+    }
+    return cudaSuccess;
+}
+
+// In-place lower triangle of W^T W on an m x m lower triangle V holding W.
+// Block row q contributes W(q, :)^T W(q, :) to rows <= q; processed in
+// increasing q, rows < q already hold partial sums, row q still holds W.
+template <typename T>
+static cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
+{
+    for (int64_t k0 = 0; k0 < m; k0 += kNb) {
+        const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
+        if (k0 > 0) {
+            RFP_TRY(gemm_nt(st, V, V.sub(k0, 0).t(), V.sub(k0, 0).t(), k0, k0, w, T(1), T(1),
+                            MASK_LOWER, MASK_NONE, MASK_NONE, abort));
+            RFP_TRY(gemm_nt(st, V.sub(k0, 0), V.sub(k0, k0).t(), V.sub(k0, 0).t(), w, k0, w,
+                            T(1), T(0), MASK_NONE, MASK_UPPER, MASK_NONE, abort));
+        }
+        RFP_TRY(lauum_tile(st, V.sub(k0, k0), (int)w, abort));
+    }
+    return cudaSuccess;
+}
+
+// ---- the three routines --------------------------------------------------------
+
+template <typename T>
+cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
+{
+    View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
+    stage_begin(st);
+    RFP_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
+    // step 1: L11 L11^T = A11
+    RFP_TRY(potrf_blocked(st, t1, L.n1, info, 0));
+    stage_mark(st, "pftrf.potrf_t1");
+    if (L.n2 > 0 && L.n1 > 0) {
+        // step 2: L21 L11^T = A21
+        RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
+        stage_mark(st, "pftrf.trsm_s");
+        // step 3: A22 <- A22 - L21 L21^T (lower triangle of T2)
+        RFP_TRY(gemm_nt(st, t2, s, s, L.n2, L.n2, L.n1, T(-1), T(1), MASK_LOWER, MASK_NONE,
+                        MASK_NONE, info));
+        stage_mark(st, "pftrf.syrk_t2");
+    }
+    // step 4: L22 L22^T = A22
+    RFP_TRY(potrf_blocked(st, t2, L.n2, info, L.n1));
+    stage_mark(st, "pftrf.potrf_t2");
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t pftrs_impl(cudaStream_t st, const Layout &L, const T *arf_c, T *Bp, int64_t ldb,
+                       int64_t nrhs)
+{
+    T *arf = const_cast<T *>(arf_c);   // read only below
+    View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
+    View<T> B{Bp, 1, ldb};
+    View<T> B1 = B, B2 = B.sub(L.n1, 0);
+    stage_begin(st);
+    // L Y = B
+    RFP_TRY(trsm_left_lower_notrans(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
+    RFP_TRY(gemm_nt(st, B2, s, B1.t(), L.n2, nrhs, L.n1, T(-1), T(1), MASK_NONE, MASK_NONE,
+                    MASK_NONE, (const int32_t *)nullptr));
+    RFP_TRY(trsm_left_lower_notrans(st, B2, nrhs, t2, L.n2, (const int32_t *)nullptr));
+    stage_mark(st, "pftrs.forward");
+    // L^T X = Y
+    RFP_TRY(trsm_left_lower_trans(st, B2, nrhs, t2, L.n2, (const int32_t *)nullptr));
+    RFP_TRY(gemm_nt(st, B1, s.t(), B2.t(), L.n1, nrhs, L.n2, T(-1), T(1), MASK_NONE, MASK_NONE,
+                    MASK_NONE, (const int32_t *)nullptr));
+    RFP_TRY(trsm_left_lower_trans(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
+    stage_mark(st, "pftrs.backward");
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
+{
+    View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
+    stage_begin(st);
+    RFP_TRY(check_diag(st, t1, L.n1, t2, L.n2, info));
+    if (L.n1 > 0 && L.n2 > 0) {
+        // W21 = -L22^{-1} L21 L11^{-1}: two in-place solves with the factor
+        RFP_TRY(trsm_right_lower_notrans(st, s, L.n2, t1, L.n1, T(-1), info));
+        RFP_TRY(trsm_left_lower_notrans(st, s, L.n1, t2, L.n2, info));
+    }
+    stage_mark(st, "pftri.w21");
+    // T1 <- W11^T W11 + W21^T W21
+    RFP_TRY(trtri_blocked(st, t1, L.n1, info));
+    stage_mark(st, "pftri.trtri_t1");
+    RFP_TRY(lauum_blocked(st, t1, L.n1, info));
+    stage_mark(st, "pftri.lauum_t1");
+    if (L.n1 > 0 && L.n2 > 0) {
+        RFP_TRY(gemm_nt(st, t1, s.t(), s.t(), L.n1, L.n1, L.n2, T(1), T(1), MASK_LOWER,
+                        MASK_NONE, MASK_NONE, info));
+        stage_mark(st, "pftri.syrk_t1");
+        // S <- W22^T W21 = L22^{-T} W21 (T2 still holds L22)
+        RFP_TRY(trsm_left_lower_trans(st, s, L.n1, t2, L.n2, info));
+        stage_mark(st, "pftri.trmm_s");
+    }
+    // T2 <- W22^T W22
+    RFP_TRY(trtri_blocked(st, t2, L.n2, info));
+    stage_mark(st, "pftri.trtri_t2");
+    RFP_TRY(lauum_blocked(st, t2, L.n2, info));
+    stage_mark(st, "pftri.lauum_t2");
+    return cudaSuccess;
+}
+
+template cudaError_t pftrf_impl<double>(cudaStream_t, const Layout &, double *, int32_t *);
+template cudaError_t pftrf_impl<float>(cudaStream_t, const Layout &, float *, int32_t *);
+template cudaError_t pftrs_impl<double>(cudaStream_t, const Layout &, const double *, double *,
+                                        int64_t, int64_t);
+template cudaError_t pftrs_impl<float>(cudaStream_t, const Layout &, const float *, float *,
+                                       int64_t, int64_t);
+template cudaError_t pftri_impl<double>(cudaStream_t, const Layout &, double *, int32_t *);
+template cudaError_t pftri_impl<float>(cudaStream_t, const Layout &, float *, int32_t *);
+
+}  // namespace rfp

@@ -1,0 +1,126 @@
+// TRTTF / TFTTR (Table "lapack"): full <-> RFPF copies.
+//
+// Pure data movement, bound by HBM bandwidth: each element of the stored
+// triangle is read once and written once (8 n(n+1) bytes per FP64 call).
+// The three blocks T1, S and T2 are cut into 64 x 64 tiles; each CTA copies
+// one tile through shared memory so that both the read and the write walk
+// their array's unit-stride direction (a transposed block such as T2 = L22^T
+// under TRANSR='N' is a shared-memory transpose).  Tiles on the diagonal of
+// T1 / T2 copy only i >= j, so the other triangle of A is never read (pack)
+// nor written (unpack), and the copy is bit-exact.
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+constexpr int kPackTile = 64, kPackThreads = 256;
+constexpr int kPackPer = kPackTile * kPackTile / kPackThreads;   // 16 elements per thread
+
+template <typename T>
+struct PackArgs {
+    T *A;
+    int64_t lda;
+    int lowerA;             // 1: A's lower triangle is stored (UPLO='L')
+    T *arf;
+    int64_t ld;
+    int64_t n1, n2;
+    Block t1, s, t2;
+    int64_t nt1, nt2, ntri1, nrect;
+    int unpack;
+};
+
+// Row/column of the t-th tile of a lower-triangular tile grid (row-major).
+__device__ __forceinline__ void tri_tile(int64_t t, int64_t &ti, int64_t &tj)
+{
+    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    ti = r;
+    tj = t - r * (r + 1) / 2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(PackArgs<T> a)
+{
+    __shared__ T tile[kPackTile][kPackTile + 1];
+    const int64_t t = blockIdx.x;
+    int64_t ti, tj, rows, cols, roff, coff;
+    Block b;
+    bool tri;
+    if (t < a.ntri1) {
+        tri_tile(t, ti, tj);
+        rows = cols = a.n1; roff = coff = 0; b = a.t1; tri = true;
+    } else if (t < a.ntri1 + a.nrect) {
+        const int64_t u = t - a.ntri1;
+        ti = u / a.nt1; tj = u % a.nt1;
+        rows = a.n2; cols = a.n1; roff = a.n1; coff = 0; b = a.s; tri = false;
+    } else {
+        tri_tile(t - a.ntri1 - a.nrect, ti, tj);
+        rows = cols = a.n2; roff = coff = a.n1; b = a.t2; tri = true;
+    }
+    const int64_t bi0 = ti * kPackTile, bj0 = tj * kPackTile;
+    const int h = (int)(rows - bi0 < kPackTile ? rows - bi0 : kPackTile);
+    const int wd = (int)(cols - bj0 < kPackTile ? cols - bj0 : kPackTile);
+
+    // Logical block element (bi, bj) is A(roff+bi, coff+bj) of the stored
+    // triangle (A(j, i) for UPLO='U') and X(bi, bj) of RFP block b.
+    View<T> vA = a.lowerA ? View<T>{a.A + (roff + bi0) + (coff + bj0) * a.lda, 1, a.lda}
+                          : View<T>{a.A + (coff + bj0) + (roff + bi0) * a.lda, a.lda, 1};
+    View<T> vR = b.trans ? View<T>{a.arf + b.off + bj0 + bi0 * a.ld, a.ld, 1}
+                         : View<T>{a.arf + b.off + bi0 + bj0 * a.ld, 1, a.ld};
+    const View<T> src = a.unpack ? vR : vA;
+    const View<T> dst = a.unpack ? vA : vR;
+
+    const int fast = threadIdx.x % kPackTile, slow0 = threadIdx.x / kPackTile;
+    auto valid = [&](int bi, int bj) {
+        return bi < h && bj < wd && (!tri || bi0 + bi >= bj0 + bj);
+    };
+
+    T v[kPackPer];
+    const bool src_rows = (src.rs == 1);
+#pragma unroll
+    for (int q = 0; q < kPackPer; ++q) {
+        const int s = slow0 + q * (kPackThreads / kPackTile);
+        const int bi = src_rows ? fast : s, bj = src_rows ? s : fast;
+        if (valid(bi, bj)) v[q] = src(bi, bj);
+    }
+#pragma unroll
+    for (int q = 0; q < kPackPer; ++q) {
+        const int s = slow0 + q * (kPackThreads / kPackTile);
+        const int bi = src_rows ? fast : s, bj = src_rows ? s : fast;
+        if (valid(bi, bj)) tile[bi][bj] = v[q];
+    }
+    __syncthreads();
+    const bool dst_rows = (dst.rs == 1);
+#pragma unroll
+    for (int q = 0; q < kPackPer; ++q) {
+        const int s = slow0 + q * (kPackThreads / kPackTile);
+        const int bi = dst_rows ? fast : s, bj = dst_rows ? s : fast;
+        if (valid(bi, bj)) dst(bi, bj) = tile[bi][bj];
+    }
+}
+
+template <typename T>
+cudaError_t pack_copy(cudaStream_t st, const Layout &L, bool lowerA, T *A, int64_t lda, T *arf,
+                      bool unpack)
+{
+    PackArgs<T> a;
+    a.A = A; a.lda = lda; a.lowerA = lowerA ? 1 : 0; a.arf = arf; a.ld = L.ld;
+    a.n1 = L.n1; a.n2 = L.n2; a.t1 = L.t1; a.s = L.s; a.t2 = L.t2;
+    a.nt1 = (L.n1 + kPackTile - 1) / kPackTile;
+    a.nt2 = (L.n2 + kPackTile - 1) / kPackTile;
+    a.ntri1 = a.nt1 * (a.nt1 + 1) / 2;
+    a.nrect = a.nt2 * a.nt1;
+    a.unpack = unpack ? 1 : 0;
+    const int64_t ntiles = a.ntri1 + a.nrect + a.nt2 * (a.nt2 + 1) / 2;
+    if (ntiles <= 0) return cudaSuccess;
+    pack_kernel<T><<<(unsigned)ntiles, kPackThreads, 0, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t pack_copy<double>(cudaStream_t, const Layout &, bool, double *, int64_t,
+                                       double *, bool);
+template cudaError_t pack_copy<float>(cudaStream_t, const Layout &, bool, float *, int64_t,
+                                      float *, bool);
+
+}  // namespace rfp

@@ -1,0 +1,104 @@
+// Internal declarations of the RFPF CUDA library (not part of the C ABI).
+//
+// Everything in this library works on "views": a matrix whose element (i, j)
+// lives at p[i*rs + j*cs].  The three RFPF blocks T1, S and T2 are views of
+// the caller's array, so a transposed block is just a view with its strides
+// swapped, and every algorithm below is written once, on the logical lower
+// factor L = [L11 0; L21 L22] (Section 3, Eq. 3), for all eight layouts.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rfp {
+
+template <typename T>
+struct View {
+    T *p;
+    int64_t rs, cs;
+    __host__ __device__ View sub(int64_t i, int64_t j) const { return {p + i * rs + j * cs, rs, cs}; }
+    __host__ __device__ View t() const { return {p, cs, rs}; }   // transpose
+    __host__ __device__ T &operator()(int64_t i, int64_t j) const { return p[i * rs + j * cs]; }
+};
+
+// One block of the RFP array: element (i, j) at off + i + j*ld (trans = 0) or
+// off + j + i*ld (trans = 1).
+struct Block {
+    int64_t off;
+    int trans;
+};
+
+// Block split and placement of one of the eight layouts (see make_layout).
+struct Layout {
+    int64_t n, n1, n2, ld;
+    Block t1, s, t2;
+};
+
+bool make_layout(char transr, char uplo, int64_t n, Layout *out);
+
+template <typename T>
+inline View<T> block_view(T *arf, const Layout &L, const Block &b)
+{
+    return b.trans ? View<T>{arf + b.off, L.ld, 1} : View<T>{arf + b.off, 1, L.ld};
+}
+
+// Operand / output triangle masks used by the tile GEMM.
+enum Mask : int { MASK_NONE = 0, MASK_LOWER = 1, MASK_UPPER = 2 };
+
+// ---- instrumentation (api.cu): launch counter and optional step timing ----
+void note_launch();                                   // one kernel enqueued
+void stage_begin(cudaStream_t st);                    // start of a timed routine
+void stage_mark(cudaStream_t st, const char *name);   // end of one of its steps
+
+// ---- launchers (all enqueue on `st`, return cudaSuccess or the launch error)
+
+// C(M x N) = alpha * A(M x K) * B(N x K)^T + beta * C.  cmode MASK_LOWER
+// writes only i >= j.  amask / bmask treat an operand as triangular (entries
+// outside the triangle read as zero and are never loaded).  A may alias C
+// when every C tile's rows cover the whole K range of A (N <= tile width),
+// which the in-place triangular products rely on.  abort: if non-null and
+// *abort != 0 at kernel start, the kernel does nothing.
+template <typename T>
+cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
+                    int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
+                    const int32_t *abort);
+
+// Solve X * op(Ltri) = alpha * X in place for an M x w strip (w <= 64);
+// op = transpose when transL != 0.  Rows are independent.
+template <typename T>
+cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int w, int transL,
+                       T alpha, const int32_t *abort);
+
+// In-place Cholesky of one w x w lower tile (w <= 64).  On a pivot <= 0 or
+// NaN at local column j, sets *info = base + j + 1 (when *info was 0).
+template <typename T>
+cudaError_t potrf_tile(cudaStream_t st, View<T> A, int w, int32_t *info, int64_t base);
+
+// In-place inverse of one w x w lower-triangular tile.
+template <typename T>
+cudaError_t trtri_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort);
+
+// In-place lower triangle of W^T W for one w x w lower-triangular tile W.
+template <typename T>
+cudaError_t lauum_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort);
+
+// *info = first j (1-based) with a zero diagonal in T1 then T2, else 0.
+template <typename T>
+cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int64_t n2,
+                       int32_t *info);
+
+// TRTTF / TFTTR copies.
+template <typename T>
+cudaError_t pack_copy(cudaStream_t st, const Layout &L, bool lowerA, T *A, int64_t lda, T *arf,
+                      bool unpack);
+
+// Blocked algorithms on the RFP blocks (Sections 3-5).
+template <typename T>
+cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info);
+template <typename T>
+cudaError_t pftrs_impl(cudaStream_t st, const Layout &L, const T *arf, T *B, int64_t ldb,
+                       int64_t nrhs);
+template <typename T>
+cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info);
+
+}  // namespace rfp

@@ -1,0 +1,439 @@
+// Tile kernels shared by PFTRF, PFTRS and PFTRI.
+//
+// The paper's four-step algorithms (Section 3: POTRF, TRSM, SYRK, POTRF;
+// Section 4: TRSM, GEMM, TRSM; Section 5: TRTRI, TRMM, LAUUM, SYRK) are built
+// here from five kernels:
+//   gemm_nt_kernel    C = alpha A B^T + beta C on strided views, with optional
+//                     triangle masks: the update, SYRK, GEMM and TRMM steps
+//   trsm_right_kernel X op(L) = alpha X for a strip of rows, by substitution
+//   potrf/trtri/lauum_tile_kernel   the diagonal-tile LAPACK steps
+// In FP64 these kernels are bound by the FP64 pipe (sm_103a has no FP64
+// tensor-core MMA), so the GEMM keeps 4x4 register tiles and double-buffered
+// shared memory, which keeps one DFMA in flight per thread per cycle of
+// shared-memory traffic; memory traffic is far below the HBM roofline.
+#include <cfloat>
+#include <climits>
+
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+template <typename T>
+struct GemmCfg;
+template <>
+struct GemmCfg<double> {
+    static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, PAD = 2;
+};
+template <>
+struct GemmCfg<float> {
+    static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8, PAD = 4;
+};
+
+template <typename T>
+struct GemmArgs {
+    View<T> C, A, B;
+    int64_t M, N, K;
+    T alpha, beta;
+    int cmode, amask, bmask;
+    const int32_t *abort;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_vec(T *dst, const T *src, int n)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < n) dst[i] = src[i];
+}
+
+constexpr int kGemmThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(GemmArgs<T> g)
+{
+    using Cfg = GemmCfg<T>;
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, TM = Cfg::TM, TN = Cfg::TN;
+    constexpr int LDA_S = BM + Cfg::PAD, LDB_S = BN + Cfg::PAD;
+    constexpr int A_PER = BM * BK / kGemmThreads, B_PER = BN * BK / kGemmThreads;
+    __shared__ __align__(16) T As[2][BK][LDA_S];
+    __shared__ __align__(16) T Bs[2][BK][LDB_S];
+
+    if (g.abort && *g.abort) return;
+    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+    if (g.cmode == MASK_LOWER && m0 + BM - 1 < n0) return;   // tile strictly above diagonal
+
+    // K range that can hold non-zero products for this tile.
+    int64_t kbeg = 0, kend = g.K;
+    if (g.amask == MASK_LOWER) kend = min(kend, m0 + BM);
+    if (g.amask == MASK_UPPER) kbeg = max(kbeg, m0);
+    if (g.bmask == MASK_LOWER) kend = min(kend, n0 + BN);
+    if (g.bmask == MASK_UPPER) kbeg = max(kbeg, n0);
+    const int64_t ntiles = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const bool a_mfast = (g.A.rs == 1), b_nfast = (g.B.rs == 1);
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = T(0);
+
+    T ra[A_PER], rb[B_PER];
+    auto a_coord = [&](int q, int &mm, int &kk) {
+        if (a_mfast) { mm = tid % BM; kk = tid / BM + q * (kGemmThreads / BM); }
+        else { kk = tid % BK; mm = tid / BK + q * (kGemmThreads / BK); }
+    };
+    auto b_coord = [&](int q, int &nn, int &kk) {
+        if (b_nfast) { nn = tid % BN; kk = tid / BN + q * (kGemmThreads / BN); }
+        else { kk = tid % BK; nn = tid / BK + q * (kGemmThreads / BK); }
+    };
+    auto load_regs = [&](int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < A_PER; ++q) {
+            int mm, kk;
+            a_coord(q, mm, kk);
+            const int64_t gm = m0 + mm, gk = k0 + kk;
+            bool ok = gm < g.M && gk < kend;
+            if (g.amask == MASK_LOWER) ok = ok && gm >= gk;
+            else if (g.amask == MASK_UPPER) ok = ok && gm <= gk;
+            ra[q] = ok ? g.A.p[gm * g.A.rs + gk * g.A.cs] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < B_PER; ++q) {
+            int nn, kk;
+            b_coord(q, nn, kk);
+            const int64_t gn = n0 + nn, gk = k0 + kk;
+            bool ok = gn < g.N && gk < kend;
+            if (g.bmask == MASK_LOWER) ok = ok && gn >= gk;
+            else if (g.bmask == MASK_UPPER) ok = ok && gn <= gk;
+            rb[q] = ok ? g.B.p[gn * g.B.rs + gk * g.B.cs] : T(0);
+        }
+    };
+    auto store_smem = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < A_PER; ++q) {
+            int mm, kk;
+            a_coord(q, mm, kk);
+            As[buf][kk][mm] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < B_PER; ++q) {
+            int nn, kk;
+            b_coord(q, nn, kk);
+            Bs[buf][kk][nn] = rb[q];
+        }
+    };
+
+    if (ntiles > 0) {
+        load_regs(kbeg);
+        store_smem(0);
+        __syncthreads();
+        for (int64_t t = 0; t < ntiles; ++t) {
+            const int buf = (int)(t & 1);
+            if (t + 1 < ntiles) load_regs(kbeg + (t + 1) * BK);
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T a[TM], b[TN];
+                load_vec(a, &As[buf][kk][ty * TM], TM);
+                load_vec(b, &Bs[buf][kk][tx * TN], TN);
+#pragma unroll
+                for (int r = 0; r < TM; ++r)
+#pragma unroll
+                    for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+            }
+            if (t + 1 < ntiles) store_smem(buf ^ 1);
+            __syncthreads();
+        }
+    }
+
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+        const int64_t i = m0 + ty * TM + r;
+        if (i >= g.M) continue;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int64_t j = n0 + tx * TN + c;
+            if (j >= g.N) continue;
+            if (g.cmode == MASK_LOWER && j > i) continue;
+            T *pc = g.C.p + i * g.C.rs + j * g.C.cs;
+            T v = g.alpha * acc[r][c];
+            if (g.beta != T(0)) v = fma(g.beta, *pc, v);
+            *pc = v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
+                    int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
+                    const int32_t *abort)
+{
+    using Cfg = GemmCfg<T>;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K <= 0 && beta == T(1)) return cudaSuccess;
+    GemmArgs<T> g{C, A, B, M, N, K, alpha, beta, cmode, amask, bmask, abort};
+    dim3 grid((unsigned)((N + Cfg::BN - 1) / Cfg::BN), (unsigned)((M + Cfg::BM - 1) / Cfg::BM));
+    gemm_nt_kernel<T><<<grid, kGemmThreads, 0, st>>>(g);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Strip triangular solve: X op(L) = alpha X, 64 rows per CTA, w <= 64.
+
+constexpr int kTileMax = 64, kTileLd = 65, kStripRows = 64;
+
+template <typename T>
+struct TrsmArgs {
+    View<T> X, L;
+    int64_t M;
+    int w, transL;
+    T alpha;
+    const int32_t *abort;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ls = reinterpret_cast<T *>(smem_raw);
+    T *Xs = Ls + kTileMax * kTileLd;
+    if (a.abort && *a.abort) return;
+    const int tid = threadIdx.x, w = a.w;
+    const int64_t r0 = (int64_t)blockIdx.x * kStripRows;
+
+    for (int e = tid; e < w * w; e += 256) {
+        int i, j;
+        if (a.L.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
+        Ls[i * kTileLd + j] = (i >= j) ? a.L(i, j) : T(0);
+    }
+    const bool xrow = (a.X.rs == 1);
+    for (int e = tid; e < kStripRows * w; e += 256) {
+        int rr, cc;
+        if (xrow) { rr = e % kStripRows; cc = e / kStripRows; } else { cc = e % w; rr = e / w; }
+        const int64_t gr = r0 + rr;
+        Xs[rr * kTileLd + cc] = gr < a.M ? a.alpha * a.X(gr, cc) : T(0);
+    }
+    __syncthreads();
+
+    const int row = tid % kStripRows, grp = tid / kStripRows;   // 4 column groups
+    T *xr = Xs + row * kTileLd;
+    if (a.transL) {                  // X L^T = B: columns in increasing order
+        for (int j = 0; j < w; ++j) {
+            if (grp == 0) xr[j] = xr[j] / Ls[j * kTileLd + j];
+            __syncthreads();
+            const T xj = xr[j];
+            for (int c = j + 1 + grp; c < w; c += 4) xr[c] -= xj * Ls[c * kTileLd + j];
+            __syncthreads();
+        }
+    } else {                         // X L = B: columns in decreasing order
+        for (int j = w - 1; j >= 0; --j) {
+            if (grp == 0) xr[j] = xr[j] / Ls[j * kTileLd + j];
+            __syncthreads();
+            const T xj = xr[j];
+            for (int c = grp; c < j; c += 4) xr[c] -= xj * Ls[j * kTileLd + c];
+            __syncthreads();
+        }
+    }
+
+    for (int e = tid; e < kStripRows * w; e += 256) {
+        int rr, cc;
+        if (xrow) { rr = e % kStripRows; cc = e / kStripRows; } else { cc = e % w; rr = e / w; }
+        const int64_t gr = r0 + rr;
+        if (gr < a.M) a.X(gr, cc) = Xs[rr * kTileLd + cc];
+    }
+}
+
+template <typename T>
+static cudaError_t set_smem_once(const void *fn, int bytes)
+{
+    // The opt-in above 48 KB is a per-function, per-device attribute; setting
+    // it again is harmless, so no cache is kept.
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T>
+cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int w, int transL,
+                       T alpha, const int32_t *abort)
+{
+    if (M <= 0 || w <= 0) return cudaSuccess;
+    const int smem = 2 * kTileMax * kTileLd * (int)sizeof(T);
+    cudaError_t e = set_smem_once<T>((const void *)trsm_right_kernel<T>, smem);
+    if (e != cudaSuccess) return e;
+    TrsmArgs<T> a{X, Ltri, M, w, transL, alpha, abort};
+    const unsigned grid = (unsigned)((M + kStripRows - 1) / kStripRows);
+    trsm_right_kernel<T><<<grid, 256, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal tiles (one CTA each).
+
+template <typename T>
+__device__ __forceinline__ void load_lower_tile(T *S, View<T> A, int w)
+{
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i, j;
+        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
+        S[i * kTileLd + j] = (i >= j) ? A(i, j) : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_lower_tile(View<T> A, const T *S, int w)
+{
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i, j;
+        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
+        if (i >= j) A(i, j) = S[i * kTileLd + j];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32_t *info,
+                                                         int64_t base)
+{
+    __shared__ __align__(16) T S[kTileMax * kTileLd];
+    __shared__ int fail;
+    if (*info != 0) return;
+    load_lower_tile(S, A, w);
+    if (threadIdx.x == 0) fail = -1;
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        if (threadIdx.x == 0) {
+            const T d = S[j * kTileLd + j];
+            if (!(d > T(0))) fail = j;
+            else S[j * kTileLd + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail >= 0) break;
+        const T djj = S[j * kTileLd + j];
+        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) S[i * kTileLd + j] /= djj;
+        __syncthreads();
+        const int rem = w - j - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+            if (k <= i) S[i * kTileLd + k] -= S[i * kTileLd + j] * S[k * kTileLd + j];
+        }
+        __syncthreads();
+    }
+    if (fail >= 0) {
+        if (threadIdx.x == 0) *info = (int32_t)(base + fail + 1);
+        return;
+    }
+    store_lower_tile(A, S, w);
+}
+
+template <typename T>
+cudaError_t potrf_tile(cudaStream_t st, View<T> A, int w, int32_t *info, int64_t base)
+{
+    if (w <= 0) return cudaSuccess;
+    potrf_tile_kernel<T><<<1, 256, 0, st>>>(A, w, info, base);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) trtri_tile_kernel(View<T> A, int w, const int32_t *abort)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ls = reinterpret_cast<T *>(smem_raw);
+    T *Ws = Ls + kTileMax * kTileLd;
+    if (abort && *abort) return;
+    load_lower_tile(Ls, A, w);
+    __syncthreads();
+    const int c = threadIdx.x;      // one column of W = L^{-1} per thread
+    if (c < w) {
+        Ws[c * kTileLd + c] = T(1) / Ls[c * kTileLd + c];
+        for (int i = c + 1; i < w; ++i) {
+            T s = T(0);
+            for (int p = c; p < i; ++p) s += Ls[i * kTileLd + p] * Ws[p * kTileLd + c];
+            Ws[i * kTileLd + c] = -s / Ls[i * kTileLd + i];
+        }
+    }
+    __syncthreads();
+    store_lower_tile(A, Ws, w);
+}
+
+template <typename T>
+cudaError_t trtri_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort)
+{
+    if (w <= 0) return cudaSuccess;
+    const int smem = 2 * kTileMax * kTileLd * (int)sizeof(T);
+    cudaError_t e = set_smem_once<T>((const void *)trtri_tile_kernel<T>, smem);
+    if (e != cudaSuccess) return e;
+    trtri_tile_kernel<T><<<1, 256, smem, st>>>(A, w, abort);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lauum_tile_kernel(View<T> A, int w, const int32_t *abort)
+{
+    __shared__ __align__(16) T Ws[kTileMax * kTileLd];
+    if (abort && *abort) return;
+    load_lower_tile(Ws, A, w);
+    __syncthreads();
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i, j;
+        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
+        if (i < j) continue;
+        T s = T(0);
+        for (int k = i; k < w; ++k) s += Ws[k * kTileLd + i] * Ws[k * kTileLd + j];
+        A(i, j) = s;
+    }
+}
+
+template <typename T>
+cudaError_t lauum_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort)
+{
+    if (w <= 0) return cudaSuccess;
+    lauum_tile_kernel<T><<<1, 256, 0, st>>>(A, w, abort);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) check_diag_kernel(View<T> t1, int64_t n1, View<T> t2,
+                                                          int64_t n2, int32_t *info)
+{
+    __shared__ unsigned long long best;
+    if (threadIdx.x == 0) best = ULLONG_MAX;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+        const T d = i < n1 ? t1(i, i) : t2(i - n1, i - n1);
+        if (d == T(0)) {
+            atomicMin(&best, (unsigned long long)i);
+            break;   // later indices of this thread are larger
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *info = best == ULLONG_MAX ? 0 : (int32_t)(best + 1);
+}
+
+template <typename T>
+cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int64_t n2,
+                       int32_t *info)
+{
+    check_diag_kernel<T><<<1, 1024, 0, st>>>(t1, n1, t2, n2, info);
+    note_launch();
+    return cudaGetLastError();
+}
+
+#define RFP_INSTANTIATE(T)                                                                    \
+    template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
+                                    int64_t, T, T, int, int, int, const int32_t *);           \
+    template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,  \
+                                       const int32_t *);                                      \
+    template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);       \
+    template cudaError_t trtri_tile<T>(cudaStream_t, View<T>, int, const int32_t *);          \
+    template cudaError_t lauum_tile<T>(cudaStream_t, View<T>, int, const int32_t *);          \
+    template cudaError_t check_diag<T>(cudaStream_t, View<T>, int64_t, View<T>, int64_t,      \
+                                       int32_t *);
+RFP_INSTANTIATE(double)
+RFP_INSTANTIATE(float)
+#undef RFP_INSTANTIATE
+
+}  // namespace rfp

@@ -1,0 +1,308 @@
+// CPU emulation of the library's kernel launchers (tile_kernels.cu, pack.cu),
+// used ONLY by tests/test_host_orchestration.py to check the host-side
+// orchestration (chol.cu, api.cu) without a GPU.
+//
+// Each launcher is emulated with the same CTA decomposition as its kernel.
+// Within one launch every CTA computes from the memory state before the
+// launch and its writes are applied afterwards; every address a CTA touches is
+// recorded, and a launch fails (illegal-address / race error) if
+//   - any access falls outside the buffers registered with emu_register, or
+//   - an element written by one CTA is read or written by another CTA.
+// A launch free of such conflicts gives the same result in any CTA order, so
+// the emulated result equals the GPU result up to floating-point rounding.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "../../paper_0901_1696_gb300/csrc/rfp_internal.cuh"
+
+namespace {
+
+struct Region { uintptr_t lo, hi; };
+std::vector<Region> g_regions;
+int g_violations = 0;
+char g_msg[512] = "";
+long g_launches = 0;
+
+bool in_bounds(const void *p, size_t sz)
+{
+    uintptr_t a = (uintptr_t)p;
+    for (auto &r : g_regions)
+        if (a >= r.lo && a + sz <= r.hi) return true;
+    return false;
+}
+
+void violation(const char *what, const void *p)
+{
+    if (g_violations++ == 0) snprintf(g_msg, sizeof g_msg, "%s at %p", what, p);
+}
+
+// Access log of one launch: address -> (first CTA id, written?)
+struct Launch {
+    std::unordered_map<uintptr_t, int> writer;               // addr -> cta
+    std::unordered_map<uintptr_t, std::vector<int>> readers;  // addr -> ctas
+    std::vector<std::pair<void *, double>> pend_d;
+    std::vector<std::pair<void *, float>> pend_f;
+    int cta = 0;
+    template <typename T>
+    T rd(const T *p)
+    {
+        if (!in_bounds(p, sizeof(T))) { violation("out-of-bounds read", p); return T(0); }
+        auto &v = readers[(uintptr_t)p];
+        if (v.empty() || v.back() != cta) v.push_back(cta);
+        return *p;
+    }
+    void wr(double *p, double x) { wr_any(p, sizeof(double)); pend_d.push_back({p, x}); }
+    void wr(float *p, float x) { wr_any(p, sizeof(float)); pend_f.push_back({p, x}); }
+    void wr_any(void *p, size_t sz)
+    {
+        if (!in_bounds(p, sz)) { violation("out-of-bounds write", p); return; }
+        auto it = writer.find((uintptr_t)p);
+        if (it != writer.end() && it->second != cta) violation("two CTAs write one element", p);
+        writer[(uintptr_t)p] = cta;
+    }
+    cudaError_t commit()
+    {
+        ++g_launches;
+        for (auto &kv : writer) {
+            auto it = readers.find(kv.first);
+            if (it == readers.end()) continue;
+            for (int c : it->second)
+                if (c != kv.second) { violation("element written by one CTA and read by another", (void *)kv.first); break; }
+        }
+        for (auto &w : pend_d) *(double *)w.first = w.second;
+        for (auto &w : pend_f) *(float *)w.first = w.second;
+        return g_violations ? cudaErrorIllegalAddress : cudaSuccess;
+    }
+};
+
+template <typename T> struct Cfg;
+template <> struct Cfg<double> { static constexpr int BM = 64, BN = 64; };
+template <> struct Cfg<float> { static constexpr int BM = 128, BN = 128; };
+
+bool aborted(Launch &L, const int32_t *abort) { return abort && L.rd(abort) != 0; }
+
+}  // namespace
+
+extern "C" {
+void emu_reset() { g_regions.clear(); g_violations = 0; g_msg[0] = 0; g_launches = 0; }
+void emu_register(void *p, size_t bytes) { g_regions.push_back({(uintptr_t)p, (uintptr_t)p + bytes}); }
+int emu_violations() { return g_violations; }
+const char *emu_message() { return g_msg; }
+long emu_launches() { return g_launches; }
+}
+
+cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t)
+{
+    if (!in_bounds(p, n)) { violation("out-of-bounds memset", p); return cudaErrorIllegalAddress; }
+    memset(p, v, n);
+    return cudaSuccess;
+}
+const char *cudaGetErrorName(cudaError_t e) { return e ? "emulated error" : "cudaSuccess"; }
+cudaError_t cudaEventCreate(cudaEvent_t *e) { *e = nullptr; return cudaSuccess; }
+cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t, cudaEvent_t) { *ms = 0.f; return cudaSuccess; }
+
+namespace rfp {
+
+template <typename T>
+cudaError_t gemm_nt(cudaStream_t, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N, int64_t K,
+                    T alpha, T beta, int cmode, int amask, int bmask, const int32_t *abort)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K <= 0 && beta == T(1)) return cudaSuccess;
+    const int BM = Cfg<T>::BM, BN = Cfg<T>::BN;
+    Launch L;
+    const int64_t gy = (M + BM - 1) / BM, gx = (N + BN - 1) / BN;
+    for (int64_t by = 0; by < gy; ++by)
+        for (int64_t bx = 0; bx < gx; ++bx) {
+            L.cta = (int)(by * gx + bx);
+            if (aborted(L, abort)) continue;
+            const int64_t m0 = by * BM, n0 = bx * BN;
+            if (cmode == MASK_LOWER && m0 + BM - 1 < n0) continue;
+            int64_t kbeg = 0, kend = K;
+            if (amask == MASK_LOWER) kend = std::min(kend, m0 + BM);
+            if (amask == MASK_UPPER) kbeg = std::max(kbeg, m0);
+            if (bmask == MASK_LOWER) kend = std::min(kend, n0 + BN);
+            if (bmask == MASK_UPPER) kbeg = std::max(kbeg, n0);
+            for (int64_t i = m0; i < std::min(M, m0 + BM); ++i)
+                for (int64_t j = n0; j < std::min(N, n0 + BN); ++j) {
+                    T acc = T(0);
+                    for (int64_t k = kbeg; k < kend; ++k) {
+                        bool aok = amask == MASK_LOWER ? i >= k : amask == MASK_UPPER ? i <= k : true;
+                        bool bok = bmask == MASK_LOWER ? j >= k : bmask == MASK_UPPER ? j <= k : true;
+                        T a = aok ? L.rd(&A(i, k)) : T(0);
+                        T b = bok ? L.rd(&B(j, k)) : T(0);
+                        acc += a * b;
+                    }
+                    if (cmode == MASK_LOWER && j > i) continue;
+                    T v = alpha * acc;
+                    if (beta != T(0)) v += beta * L.rd(&C(i, j));
+                    L.wr(&C(i, j), v);
+                }
+        }
+    return L.commit();
+}
+
+template <typename T>
+cudaError_t trsm_strip(cudaStream_t, View<T> X, View<T> Lt, int64_t M, int w, int transL, T alpha,
+                       const int32_t *abort)
+{
+    if (M <= 0 || w <= 0) return cudaSuccess;
+    if (w > 64) { violation("trsm tile wider than 64", nullptr); return cudaErrorInvalidValue; }
+    Launch L;
+    for (int64_t r0 = 0, cta = 0; r0 < M; r0 += 64, ++cta) {
+        L.cta = (int)cta;
+        if (aborted(L, abort)) continue;
+        std::vector<T> l(w * w), x;
+        for (int i = 0; i < w; ++i)
+            for (int j = 0; j <= i; ++j) l[i * w + j] = L.rd(&Lt(i, j));
+        for (int64_t r = r0; r < std::min(M, r0 + 64); ++r) {
+            x.assign(w, T(0));
+            for (int c = 0; c < w; ++c) x[c] = alpha * L.rd(&X(r, c));
+            if (transL) {
+                for (int j = 0; j < w; ++j) {
+                    x[j] /= l[j * w + j];
+                    for (int c = j + 1; c < w; ++c) x[c] -= x[j] * l[c * w + j];
+                }
+            } else {
+                for (int j = w - 1; j >= 0; --j) {
+                    x[j] /= l[j * w + j];
+                    for (int c = 0; c < j; ++c) x[c] -= x[j] * l[j * w + c];
+                }
+            }
+            for (int c = 0; c < w; ++c) L.wr(&X(r, c), x[c]);
+        }
+    }
+    return L.commit();
+}
+
+template <typename T>
+cudaError_t potrf_tile(cudaStream_t, View<T> A, int w, int32_t *info, int64_t base)
+{
+    if (w <= 0) return cudaSuccess;
+    Launch L;
+    if (L.rd(info) != 0) return L.commit();
+    std::vector<T> s(w * w, T(0));
+    for (int i = 0; i < w; ++i)
+        for (int j = 0; j <= i; ++j) s[i * w + j] = L.rd(&A(i, j));
+    for (int j = 0; j < w; ++j) {
+        T d = s[j * w + j];
+        if (!(d > T(0))) {
+            int32_t v = (int32_t)(base + j + 1);
+            L.wr_any(info, 4);
+            L.commit();
+            *info = v;
+            return g_violations ? cudaErrorIllegalAddress : cudaSuccess;
+        }
+        s[j * w + j] = std::sqrt(d);
+        for (int i = j + 1; i < w; ++i) s[i * w + j] /= s[j * w + j];
+        for (int i = j + 1; i < w; ++i)
+            for (int k = j + 1; k <= i; ++k) s[i * w + k] -= s[i * w + j] * s[k * w + j];
+    }
+    for (int i = 0; i < w; ++i)
+        for (int j = 0; j <= i; ++j) L.wr(&A(i, j), s[i * w + j]);
+    return L.commit();
+}
+
+template <typename T>
+cudaError_t trtri_tile(cudaStream_t, View<T> A, int w, const int32_t *abort)
+{
+    if (w <= 0) return cudaSuccess;
+    Launch L;
+    if (aborted(L, abort)) return L.commit();
+    std::vector<T> l(w * w, T(0)), x(w * w, T(0));
+    for (int i = 0; i < w; ++i)
+        for (int j = 0; j <= i; ++j) l[i * w + j] = L.rd(&A(i, j));
+    for (int c = 0; c < w; ++c) {
+        x[c * w + c] = T(1) / l[c * w + c];
+        for (int i = c + 1; i < w; ++i) {
+            T s = T(0);
+            for (int p = c; p < i; ++p) s += l[i * w + p] * x[p * w + c];
+            x[i * w + c] = -s / l[i * w + i];
+        }
+    }
+    for (int i = 0; i < w; ++i)
+        for (int j = 0; j <= i; ++j) L.wr(&A(i, j), x[i * w + j]);
+    return L.commit();
+}
+
+template <typename T>
+cudaError_t lauum_tile(cudaStream_t, View<T> A, int w, const int32_t *abort)
+{
+    if (w <= 0) return cudaSuccess;
+    Launch L;
+    if (aborted(L, abort)) return L.commit();
+    std::vector<T> x(w * w, T(0));
+    for (int i = 0; i < w; ++i)
+        for (int j = 0; j <= i; ++j) x[i * w + j] = L.rd(&A(i, j));
+    for (int i = 0; i < w; ++i)
+        for (int j = 0; j <= i; ++j) {
+            T s = T(0);
+            for (int k = i; k < w; ++k) s += x[k * w + i] * x[k * w + j];
+            L.wr(&A(i, j), s);
+        }
+    return L.commit();
+}
+
+template <typename T>
+cudaError_t check_diag(cudaStream_t, View<T> t1, int64_t n1, View<T> t2, int64_t n2, int32_t *info)
+{
+    Launch L;
+    int32_t v = 0;
+    for (int64_t i = 0; i < n1 + n2; ++i) {
+        T d = i < n1 ? L.rd(&t1(i, i)) : L.rd(&t2(i - n1, i - n1));
+        if (d == T(0)) { v = (int32_t)(i + 1); break; }
+    }
+    L.wr_any(info, 4);
+    cudaError_t e = L.commit();
+    *info = v;
+    return e;
+}
+
+template <typename T>
+cudaError_t pack_copy(cudaStream_t, const Layout &Ly, bool lowerA, T *A, int64_t lda, T *arf, bool unpack)
+{
+    const int TILE = 64;
+    Launch L;
+    struct Blk { int64_t rows, cols, roff, coff; Block b; bool tri; };
+    Blk blks[3] = {{Ly.n1, Ly.n1, 0, 0, Ly.t1, true}, {Ly.n2, Ly.n1, Ly.n1, 0, Ly.s, false},
+                   {Ly.n2, Ly.n2, Ly.n1, Ly.n1, Ly.t2, true}};
+    int cta = 0;
+    for (auto &bk : blks)
+        for (int64_t bi0 = 0; bi0 < bk.rows; bi0 += TILE)
+            for (int64_t bj0 = 0; bj0 < bk.cols; bj0 += TILE) {
+                if (bk.tri && bj0 > bi0) continue;
+                L.cta = cta++;
+                for (int64_t bi = bi0; bi < std::min(bk.rows, bi0 + TILE); ++bi)
+                    for (int64_t bj = bj0; bj < std::min(bk.cols, bj0 + TILE); ++bj) {
+                        if (bk.tri && bi < bj) continue;
+                        int64_t gi = bk.roff + bi, gj = bk.coff + bj;
+                        T *pa = lowerA ? &A[gi + gj * lda] : &A[gj + gi * lda];
+                        T *pr = bk.b.trans ? &arf[bk.b.off + bj + bi * Ly.ld] : &arf[bk.b.off + bi + bj * Ly.ld];
+                        if (unpack) L.wr(pa, L.rd(pr));
+                        else L.wr(pr, L.rd(pa));
+                    }
+            }
+    return L.commit();
+}
+
+#define EMU_INST(T)                                                                                  \
+    template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \
+                                    T, T, int, int, int, const int32_t *);                           \
+    template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,         \
+                                       const int32_t *);                                             \
+    template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);              \
+    template cudaError_t trtri_tile<T>(cudaStream_t, View<T>, int, const int32_t *);                 \
+    template cudaError_t lauum_tile<T>(cudaStream_t, View<T>, int, const int32_t *);                 \
+    template cudaError_t check_diag<T>(cudaStream_t, View<T>, int64_t, View<T>, int64_t, int32_t *); \
+    template cudaError_t pack_copy<T>(cudaStream_t, const Layout &, bool, T *, int64_t, T *, bool);
+EMU_INST(double)
+EMU_INST(float)
+
+}  // namespace rfp

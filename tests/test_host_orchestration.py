@@ -1,0 +1,206 @@
+"""Host-side orchestration of the CUDA library, checked on the CPU.
+
+The library's host code (``csrc/chol.cu``: the blocked PFTRF / PFTRS /
+PFTRI launch sequences, ``csrc/api.cu``: argument checks and the layout
+descriptors) is compiled with g++ against ``tests/host_emu``, an emulation of
+each kernel launcher with the kernel's own CTA decomposition.  The emulator
+fails a launch on any out-of-bounds access and on any element that one CTA
+writes while another CTA of the same launch reads or writes it.  So these
+tests show, without a GPU, that every launch the library issues stays inside
+the caller's buffers, that the in-place steps are race-free, and that the
+launch sequences compute what the oracle computes.  The kernels themselves
+are tested on the GPU (tests/test_gpu_*.py).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import rfp_inputs as gen
+from paper_0901_1696_gb300.binding import Library, RfpError
+from rfp_inputs import LAYOUTS
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+EMU_DIR = os.path.join(ROOT, "tests", "host_emu")
+CSRC = os.path.join(ROOT, "paper_0901_1696_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("emu") / "librfp_emu.so")
+    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-I", EMU_DIR, "-x", "c++",
+           os.path.join(CSRC, "chol.cu"), os.path.join(CSRC, "api.cu"), "-x", "none",
+           os.path.join(EMU_DIR, "emu_kernels.cpp"), "-o", so]
+    subprocess.run(cmd, check=True)
+    lib = Library(so)
+    raw = lib.lib
+    raw.emu_register.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    raw.emu_message.restype = ctypes.c_char_p
+    raw.emu_launches.restype = ctypes.c_long
+    return lib
+
+
+def _register(emu, *arrays):
+    raw = emu.lib
+    raw.emu_reset()
+    for a in arrays:
+        raw.emu_register(a.ctypes.data, a.nbytes)
+
+
+def _ok(emu):
+    raw = emu.lib
+    assert raw.emu_violations() == 0, raw.emu_message().decode()
+
+
+def _full_from_factor(transr, uplo, n, arf):
+    F = oracle.unpack(transr, uplo, n, arf)
+    return np.tril(F) if uplo == "L" else np.triu(F).T
+
+
+SIZES = [1, 2, 3, 5, 63, 64, 65, 127, 128, 129, 200, 257]
+
+
+@pytest.mark.parametrize("transr,uplo", LAYOUTS)
+@pytest.mark.parametrize("n", SIZES)
+def test_emulated_path_matches_oracle(emu, transr, uplo, n):
+    A, rng = gen.spd_bbt(n, seed=n + 7, return_rng=True)
+    nrhs = 3 if n % 2 else 70
+    B = gen.rhs(n, nrhs, rng)
+    lda = n + 3
+    Afull = np.zeros((lda, n), order="F")
+    Afull[:n] = A
+    arf = np.zeros(n * (n + 1) // 2)
+    info = np.zeros(1, dtype=np.int32)
+    ldb = n + 1
+    Bw = np.zeros((ldb, nrhs), order="F")
+    Bw[:n] = B
+    _register(emu, Afull, arf, info, Bw)
+
+    emu.rfp_dpack(transr, uplo, n, Afull, lda, arf, 0)
+    _ok(emu)
+    np.testing.assert_array_equal(arf, oracle.pack(transr, uplo, A))
+
+    ref_f, ref_info = oracle.pftrf(transr, uplo, n, arf)
+    emu.rfp_dpftrf(transr, uplo, n, arf, info, 0)
+    _ok(emu)
+    assert info[0] == ref_info == 0
+    assert np.max(np.abs(arf - ref_f)) <= 1e-13 * max(1.0, np.max(np.abs(ref_f)))
+
+    X = oracle.pftrs(transr, uplo, n, arf, B)
+    emu.rfp_dpftrs(transr, uplo, n, nrhs, arf, Bw, ldb, 0)
+    _ok(emu)
+    assert np.max(np.abs(Bw[:n] - X)) <= 1e-12 * max(1.0, np.max(np.abs(X)))
+
+    ref_i, _ = oracle.pftri(transr, uplo, n, arf)
+    emu.rfp_dpftri(transr, uplo, n, arf, info, 0)
+    _ok(emu)
+    assert info[0] == 0
+    assert np.max(np.abs(arf - ref_i)) <= 1e-12 * max(1.0, np.max(np.abs(ref_i)))
+
+    # unpack writes the UPLO triangle only
+    Aout = np.full((lda, n), 7.0, order="F")
+    _register(emu, Aout, arf)
+    emu.rfp_dunpack(transr, uplo, n, arf, Aout, lda, 0)
+    _ok(emu)
+    want = oracle.unpack(transr, uplo, n, arf, np.full((n, n), 7.0))
+    np.testing.assert_array_equal(Aout[:n], want)
+    assert np.all(Aout[n:] == 7.0)
+
+
+@pytest.mark.parametrize("transr,uplo", LAYOUTS)
+@pytest.mark.parametrize("n", [7, 130])
+def test_emulated_single_precision(emu, transr, uplo, n):
+    A, rng = gen.spd_bbt(n, seed=3, return_rng=True)
+    B = gen.rhs(n, 5, rng)
+    A32 = np.asfortranarray(A.astype(np.float32))
+    arf = np.zeros(n * (n + 1) // 2, dtype=np.float32)
+    info = np.zeros(1, dtype=np.int32)
+    B32 = np.asfortranarray(B.astype(np.float32))
+    _register(emu, A32, arf, info, B32)
+    emu.rfp_spack(transr, uplo, n, A32, n, arf, 0)
+    np.testing.assert_array_equal(arf, oracle.pack(transr, uplo, A32.astype(np.float64)))
+    emu.rfp_spftrf(transr, uplo, n, arf, info, 0)
+    emu.rfp_spftrs(transr, uplo, n, 5, arf, B32, n, 0)
+    _ok(emu)
+    assert info[0] == 0
+    assert oracle.solve_backward_error(A, B32.astype(np.float64), B) <= 64 * n * 6e-8
+
+
+@pytest.mark.parametrize("transr,uplo", LAYOUTS)
+@pytest.mark.parametrize("n,k", [(70, 3), (70, 40), (130, 64), (130, 100)])
+def test_emulated_info_on_failure(emu, transr, uplo, n, k):
+    A, L0 = gen.spd_integer_factor(n, seed=5)
+    A = A.copy()
+    A[k, k] -= L0[k, k] ** 2 + 1.0
+    arf = oracle.pack(transr, uplo, A)
+    info = np.zeros(1, dtype=np.int32)
+    _register(emu, arf, info)
+    emu.rfp_dpftrf(transr, uplo, n, arf, info, 0)
+    _ok(emu)
+    assert info[0] == k + 1
+
+
+def test_emulated_pftri_zero_diagonal(emu):
+    n = 90
+    arf = oracle.pack("N", "L", np.diag(np.r_[np.ones(70), 0.0, np.ones(19)]))
+    info = np.zeros(1, dtype=np.int32)
+    _register(emu, arf, info)
+    emu.rfp_dpftri("N", "L", n, arf, info, 0)
+    _ok(emu)
+    assert info[0] == 71
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 6, 7, 100, 1001])
+@pytest.mark.parametrize("transr,uplo", LAYOUTS)
+def test_layout_descriptor_matches_oracle_placement(emu, transr, uplo, n):
+    """rfp_layout's block descriptors place every element where the oracle's
+    block assembly (Figs. 4-6) puts it: bit-exact index work."""
+    d = emu.rfp_layout(transr, uplo, n)
+    n1, n2, ld = d["n1"], d["n2"], d["ld"]
+    assert (n1, n2) == oracle.split(uplo, n)
+    code = np.zeros((n, n), order="F")
+    for j in range(n):
+        for i in range(n):
+            code[i, j] = 1 + i + j * n
+    arf = oracle.pack(transr, uplo, code)
+    for (off, tr, rows, cols, r0, c0, tri) in [
+            (d["t1_off"], d["t1_trans"], n1, n1, 0, 0, True),
+            (d["s_off"], d["s_trans"], n2, n1, n1, 0, False),
+            (d["t2_off"], d["t2_trans"], n2, n2, n1, n1, True)]:
+        for i in range(rows):
+            for j in range(i + 1 if tri else cols):
+                pos = off + (j + i * ld if tr else i + j * ld)
+                gi, gj = r0 + i, c0 + j          # logical lower element
+                a = code[gi, gj] if uplo == "L" else code[gj, gi]
+                assert arf[pos] == a
+
+
+def test_argument_checks(emu):
+    arf = np.zeros(10)
+    info = np.zeros(1, dtype=np.int32)
+    B = np.zeros((4, 2), order="F")
+    cases = [
+        (lambda: emu.rfp_dpftrf("X", "L", 4, arf, info, 0), -1),
+        (lambda: emu.rfp_dpftrf("N", "C", 4, arf, info, 0), -2),
+        (lambda: emu.rfp_dpftrf("N", "L", -1, arf, info, 0), -3),
+        (lambda: emu.rfp_dpftrf("N", "L", 4, 0, info, 0), -4),
+        (lambda: emu.rfp_dpftrf("N", "L", 4, arf, 0, 0), -5),
+        (lambda: emu.rfp_dpftrf("N", "L", 4, arf.ctypes.data + 1, info, 0), -4),
+        (lambda: emu.rfp_dpftrs("N", "L", 4, -2, arf, B, 4, 0), -4),
+        (lambda: emu.rfp_dpftrs("N", "L", 4, 2, 0, B, 4, 0), -5),
+        (lambda: emu.rfp_dpftrs("N", "L", 4, 2, arf, B, 3, 0), -7),
+        (lambda: emu.rfp_dpack("T", "U", 4, B, 3, arf, 0), -5),
+        (lambda: emu.rfp_dunpack("T", "U", 4, arf, B, 2, 0), -6),
+        (lambda: emu.rfp_dpftri("c", "L", 4, arf, info, 0), -1),
+    ]
+    for call, code in cases:
+        with pytest.raises(RfpError) as e:
+            call()
+        assert e.value.status == code
+    # quick returns
+    assert emu.rfp_dpftrs("N", "L", 0, 5, 0, 0, 1, 0) == 0
+    assert emu.rfp_dpftrs("N", "L", 4, 0, 0, 0, 4, 0) == 0
+    assert emu.rfp_dpack("N", "L", 0, 0, 1, 0, 0) == 0
