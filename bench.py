@@ -1,8 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark of the RFPF Cholesky hot path on GB300.
 
-One step = one pass of the whole path over one synthetic SPD matrix of order
-n = 16384 held in one of the eight RFPF layouts (step s uses layout s mod 8):
+One step = one pass of the whole path over one synthetic SPD matrix held in
+one of the eight RFPF layouts: step s uses TRANSR x UPLO pair s mod 4 and
+order n = 16384 (even) for (s div 4) even, n = 16383 (odd, the leading
+principal submatrix) otherwise, so 8 steps cover all eight layouts:
   rfp_dpack (full -> RFPF), rfp_dpftrf, rfp_dpftrs (nrhs = 256),
   rfp_dpftri, rfp_dunpack (RFPF -> full, the inverse).
 A = Q diag(lam) Q^T, Q Haar-random orthogonal, lam log-uniform on [1, 1e4]
@@ -10,10 +12,11 @@ A = Q diag(lam) Q^T, Q Haar-random orthogonal, lam log-uniform on [1, 1e4]
 HBM before the timed region and larger than L2 (the RFP array alone is
 1.07 GB), so no L2 flush is needed.
 
-Reported metric (the benchmark spec): PFTRF+PFTRS TFLOP/s = (n^3/3 + 2 n^2 nrhs)
+Reported metric: PFTRF+PFTRS TFLOP/s = (n^3/3 + 2 n^2 nrhs)
 summed over the timed steps / the device time of those two calls (CUDA
 events on the launching stream).  The other rows of the step are reported in
-"breakdown".  --impl reference times the CPU oracle instead.
+"breakdown".  --impl reference times the plain CPU oracle on the host cores
+instead (a bounded sample of the same workload per step).
 """
 from __future__ import annotations
 
@@ -33,6 +36,12 @@ METRIC = "PFTRF+PFTRS TFLOP/s & % peak; served solves/s, p50/p99 at ≤1e-12 bwd
 LAYOUTS = [(t, u) for t in "NT" for u in "LU"]
 
 
+def step_layout(s: int, n: int):
+    """(transr, uplo, order) of step s: 4 TRANSR x UPLO pairs x 2 parities."""
+    transr, uplo = LAYOUTS[s % 4]
+    return transr, uplo, (n if (s // 4) % 2 == 0 else n - 1)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -43,7 +52,9 @@ def parse():
     p.add_argument("--nrhs", type=int, default=256)
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--cpu-n", type=int, default=4096, help="oracle sample size (CPU legs)")
+    p.add_argument("--cpu-n", type=int, default=0,
+                   help="oracle sample order (default 10240 for cpu_baseline, 6144 per "
+                        "reference step)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -120,6 +131,7 @@ def oracle_sample(n: int, nrhs: int, kappa: float, seed: int = 0):
 def run_reference(args, rank: int):
     if rank != 0:
         return
+    args.cpu_n = args.cpu_n or 6144
     nrhs = max(1, args.nrhs * args.cpu_n // args.n)
     times, rates = [], []
     for s in range(args.warmup + args.steps):
@@ -188,20 +200,20 @@ def run_ours(args, rank: int, world: int):
     rows = ["pack", "pftrf", "pftrs", "pftri", "unpack"]
 
     def step(s, evs=None):
-        transr, uplo = LAYOUTS[s % len(LAYOUTS)]
+        transr, uplo, m = step_layout(s, n)      # A(0:m, 0:m), leading dimension n
         rec = (lambda i: evs[i].record(stream)) if evs else (lambda i: None)
         rec(0)
-        lib.rfp_dpack(transr, uplo, n, A, n, arf, stream)
+        lib.rfp_dpack(transr, uplo, m, A, n, arf, stream)
         rec(1)
-        lib.rfp_dpftrf(transr, uplo, n, arf, infos[s, 0:1], stream)
+        lib.rfp_dpftrf(transr, uplo, m, arf, infos[s, 0:1], stream)
         rec(2)
         X.copy_(B0)
         rec(3)
-        lib.rfp_dpftrs(transr, uplo, n, nrhs, arf, X, n, stream)
+        lib.rfp_dpftrs(transr, uplo, m, nrhs, arf, X, n, stream)
         rec(4)
-        lib.rfp_dpftri(transr, uplo, n, arf, infos[s, 1:2], stream)
+        lib.rfp_dpftri(transr, uplo, m, arf, infos[s, 1:2], stream)
         rec(5)
-        lib.rfp_dunpack(transr, uplo, n, arf, Ainv, n, stream)
+        lib.rfp_dunpack(transr, uplo, m, arf, Ainv, n, stream)
         rec(6)
 
     for s in range(args.warmup):
@@ -239,8 +251,9 @@ def run_ours(args, rank: int, world: int):
         per_row["pftri"] += ev[4].elapsed_time(ev[5])
         per_row["unpack"] += ev[5].elapsed_time(ev[6])
     K = args.steps
+    orders = [step_layout(args.warmup + k, n)[2] for k in range(K)]
     metric_ms = per_row["pftrf"] + per_row["pftrs"]
-    metric_flops = K * (pftrf_flops(n) + pftrs_flops(n, nrhs))
+    metric_flops = sum(pftrf_flops(m) + pftrs_flops(m, nrhs) for m in orders)
     if dist:
         t = torch.tensor([metric_ms, total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -252,10 +265,14 @@ def run_ours(args, rank: int, world: int):
     agg = {}
     for name, ms in stages:
         agg[name] = agg.get(name, 0.0) + ms
-    n1 = (n + 1) // 2
+    # algorithmic flops of step 3 (lower triangle of T2 incl. its diagonal:
+    # n2 (n2 + 1) / 2 dot products of length n1, 2 flops each) per step
     syrk_ms = agg.get("pftrf.syrk_t2", 0.0) / K
-    # per layout n1/n2 differ by one for odd n; at even n both are n/2
-    syrk_flops = n1 * (n - n1) * (n - n1 + 1)
+    syrk_flops = 0.0
+    for k, m in enumerate(orders):
+        uplo = step_layout(args.warmup + k, n)[1]
+        n1 = (m + 1) // 2 if uplo == "L" else m // 2
+        syrk_flops += n1 * (m - n1) * (m - n1 + 1) / K
     peak = fp64_peak_tflops(clocks["sm_mhz"])
     achieved = syrk_flops / (syrk_ms * 1e-3) / 1e12 if syrk_ms else None
     pf = [agg.get(k, 0.0) for k in ("pftrf.potrf_t1", "pftrf.trsm_s", "pftrf.syrk_t2",
@@ -264,8 +281,9 @@ def run_ours(args, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"FP64 SPD n={n} RFPF, 8 layouts cycled per step; pack + PFTRF + "
-                               f"PFTRS(nrhs={nrhs}) + PFTRI + unpack", "n": n, "nrhs": nrhs,
+        "config": {"workload": f"FP64 SPD n={n}/{n - 1} RFPF, all 8 layouts cycled over the steps; "
+                               f"pack + PFTRF + PFTRS(nrhs={nrhs}) + PFTRI + unpack",
+                   "n": [n, n - 1], "nrhs": nrhs,
                    "kappa": args.kappa, "matrix": "Q diag(lam) Q^T, Haar Q, log-uniform lam",
                    "l2": "inputs larger than L2 (RFP 1.07 GB); no flush",
                    "parallelism": f"replicas x{world}"},
@@ -275,11 +293,11 @@ def run_ours(args, rank: int, world: int):
                      "peak_source": "FP64 FMA pipe: 152 SMs x units x 2 x median SM clock"},
         "breakdown": {
             **{f"{r}_ms": per_row[r] / K for r in rows},
-            "pftrf_tflops": pftrf_flops(n) * K / (per_row["pftrf"] * 1e-3) / 1e12,
-            "pftrs_tflops": pftrs_flops(n, nrhs) * K / (per_row["pftrs"] * 1e-3) / 1e12,
-            "pftri_tflops": pftri_flops(n) * K / (per_row["pftri"] * 1e-3) / 1e12,
-            "pack_gbs": pack_bytes(n) * K / (per_row["pack"] * 1e-3) / 1e9,
-            "unpack_gbs": pack_bytes(n) * K / (per_row["unpack"] * 1e-3) / 1e9,
+            "pftrf_tflops": sum(map(pftrf_flops, orders)) / (per_row["pftrf"] * 1e-3) / 1e12,
+            "pftrs_tflops": sum(pftrs_flops(m, nrhs) for m in orders) / (per_row["pftrs"] * 1e-3) / 1e12,
+            "pftri_tflops": sum(map(pftri_flops, orders)) / (per_row["pftri"] * 1e-3) / 1e12,
+            "pack_gbs": sum(map(pack_bytes, orders)) / (per_row["pack"] * 1e-3) / 1e9,
+            "unpack_gbs": sum(map(pack_bytes, orders)) / (per_row["unpack"] * 1e-3) / 1e9,
             "pftrf_step_split": [round(x / sum(pf), 4) for x in pf] if sum(pf) else None,
             "pftri_steps_ms": {k: v / K for k, v in agg.items() if k.startswith("pftri.")},
         },
@@ -290,6 +308,7 @@ def run_ours(args, rank: int, world: int):
     if not args.no_e2e:
         line["e2e"] = e2e_leg(args, lib, A, B0, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
+        args.cpu_n = args.cpu_n or 10240
         rate, dt, threads = oracle_sample(args.cpu_n, max(1, nrhs * args.cpu_n // n), args.kappa)
         line["cpu_baseline"] = {
             "value": rate, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",

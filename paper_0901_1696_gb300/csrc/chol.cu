@@ -125,13 +125,13 @@ static cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const in
         RFP_TRY(trtri_tile(st, V.sub(k0, k0), (int)w, abort));
         if (k0 > 0)
             RFP_TRY(gemm_nt(st, V.sub(k0, 0), V.sub(k0, k0), V.sub(k0, 0).t(), w, k0, w, T(1),
-                            T(0), MASK_NONE, MASK_LOWER, MASK_NONE, abort));
+                            T(0), MASK_NONE, MASK_LOWER, MASK_NONE, abort, true));
         if (k1 < m) {
             if (k0 > 0)
                 RFP_TRY(gemm_nt(st, V.sub(k1, 0), V.sub(k1, k0), V.sub(k0, 0).t(), m - k1, k0, w,
                                 T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
             RFP_TRY(gemm_nt(st, V.sub(k1, k0), V.sub(k1, k0), V.sub(k0, k0).t(), m - k1, w, w,
-                            T(-1), T(0), MASK_NONE, MASK_NONE, MASK_UPPER, abort));
+                            T(-1), T(0), MASK_NONE, MASK_NONE, MASK_UPPER, abort, true));
         }
     }
     return cudaSuccess;
@@ -149,7 +149,7 @@ static cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const in
             RFP_TRY(gemm_nt(st, V, V.sub(k0, 0).t(), V.sub(k0, 0).t(), k0, k0, w, T(1), T(1),
                             MASK_LOWER, MASK_NONE, MASK_NONE, abort));
             RFP_TRY(gemm_nt(st, V.sub(k0, 0), V.sub(k0, k0).t(), V.sub(k0, 0).t(), w, k0, w,
-                            T(1), T(0), MASK_NONE, MASK_UPPER, MASK_NONE, abort));
+                            T(1), T(0), MASK_NONE, MASK_UPPER, MASK_NONE, abort, true));
         }
         RFP_TRY(lauum_tile(st, V.sub(k0, k0), (int)w, abort));
     }

@@ -28,6 +28,9 @@ struct PackArgs {
     int unpack;
 };
 
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+
 // Row/column of the t-th tile of a lower-triangular tile grid (row-major).
 __device__ __forceinline__ void tri_tile(int64_t t, int64_t &ti, int64_t &tj)
 {
@@ -39,7 +42,7 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t &ti, int64_t &tj)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(PackArgs<T> a)
+__global__ void __launch_bounds__(kPackThreads, 3) pack_kernel(PackArgs<T> a)
 {
     __shared__ T tile[kPackTile][kPackTile + 1];
     const int64_t t = blockIdx.x;
@@ -70,32 +73,68 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(PackArgs<T> a)
     const View<T> src = a.unpack ? vR : vA;
     const View<T> dst = a.unpack ? vA : vR;
 
+    // Thread (fast, slow): `fast` runs along the array's unit-stride index.
     const int fast = threadIdx.x % kPackTile, slow0 = threadIdx.x / kPackTile;
-    auto valid = [&](int bi, int bj) {
-        return bi < h && bj < wd && (!tri || bi0 + bi >= bj0 + bj);
+    constexpr int kSlowStep = kPackThreads / kPackTile;
+    const bool src_rows = (src.rs == 1), dst_rows = (dst.rs == 1);
+
+    // Valid elements: bi < h, bj < wd and, on a diagonal tile, bi0+bi >= bj0+bj.
+    // For a thread whose fast index is bi (rows) or bj (columns) this is a
+    // range [lo, hi) of its slow index.
+    auto slow_range = [&](bool rows_fast, int &lo, int &hi) {
+        const int f = fast;
+        const int64_t d = bi0 - bj0;   // diagonal offset of the tile
+        if (rows_fast) {               // bi = f, bj = slow
+            hi = (f < h) ? wd : 0;
+            if (tri) hi = (int)imin64(hi, imax64(0, d + f + 1));
+            lo = 0;
+        } else {                       // bj = f, bi = slow
+            hi = (f < wd) ? h : 0;
+            lo = tri ? (int)imax64(0, imin64(h, f - d)) : 0;
+        }
     };
+    int slo, shi;
+    slow_range(src_rows, slo, shi);
+    const int64_t sstride = src_rows ? src.cs : src.rs;
+    const T *sp = src.p + fast + (int64_t)slow0 * sstride;
 
     T v[kPackPer];
-    const bool src_rows = (src.rs == 1);
 #pragma unroll
     for (int q = 0; q < kPackPer; ++q) {
-        const int s = slow0 + q * (kPackThreads / kPackTile);
-        const int bi = src_rows ? fast : s, bj = src_rows ? s : fast;
-        if (valid(bi, bj)) v[q] = src(bi, bj);
+        const int sl = slow0 + q * kSlowStep;
+        if (sl >= slo && sl < shi) v[q] = sp[(int64_t)q * kSlowStep * sstride];
     }
+    if (src_rows == dst_rows) {
+        // Both arrays are contiguous along the same index: store straight
+        // from registers (same (fast, slow) ownership, same validity).
+        const int64_t dstride = dst_rows ? dst.cs : dst.rs;
+        T *dp = dst.p + fast + (int64_t)slow0 * dstride;
+#pragma unroll
+        for (int q = 0; q < kPackPer; ++q) {
+            const int sl = slow0 + q * kSlowStep;
+            if (sl >= slo && sl < shi) dp[(int64_t)q * kSlowStep * dstride] = v[q];
+        }
+        return;
+    }
+    // Transposed block: through shared memory, tile[bi][bj].
 #pragma unroll
     for (int q = 0; q < kPackPer; ++q) {
-        const int s = slow0 + q * (kPackThreads / kPackTile);
-        const int bi = src_rows ? fast : s, bj = src_rows ? s : fast;
-        if (valid(bi, bj)) tile[bi][bj] = v[q];
+        const int sl = slow0 + q * kSlowStep;
+        if (sl >= slo && sl < shi) {
+            if (src_rows) tile[fast][sl] = v[q];
+            else tile[sl][fast] = v[q];
+        }
     }
     __syncthreads();
-    const bool dst_rows = (dst.rs == 1);
+    int dlo, dhi;
+    slow_range(dst_rows, dlo, dhi);
+    const int64_t dstride = dst_rows ? dst.cs : dst.rs;
+    T *dp = dst.p + fast + (int64_t)slow0 * dstride;
 #pragma unroll
     for (int q = 0; q < kPackPer; ++q) {
-        const int s = slow0 + q * (kPackThreads / kPackTile);
-        const int bi = dst_rows ? fast : s, bj = dst_rows ? s : fast;
-        if (valid(bi, bj)) dst(bi, bj) = tile[bi][bj];
+        const int sl = slow0 + q * kSlowStep;
+        if (sl >= dlo && sl < dhi)
+            dp[(int64_t)q * kSlowStep * dstride] = dst_rows ? tile[fast][sl] : tile[sl][fast];
     }
 }
 

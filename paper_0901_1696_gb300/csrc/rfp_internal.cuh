@@ -52,6 +52,35 @@ void stage_mark(cudaStream_t st, const char *name);   // end of one of its steps
 
 // ---- launchers (all enqueue on `st`, return cudaSuccess or the launch error)
 
+// Tile shape of one gemm_nt launch.  The large tile (64 x 64 FP64, 128 x 128
+// FP32, 256 threads) is used unless the launch would put fewer than two CTAs
+// on each SM, in which case the small tile (32 x 32 FP64 with 64 threads,
+// 64 x 64 FP32 with 256 threads) quadruples the CTA count.  In-place calls
+// (A or B aliasing C) always take the large tile, whose width covers the
+// 64-wide diagonal blocks the in-place products work on.
+struct GemmTileChoice {
+    int bm, bn;
+    bool small;
+};
+inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, bool inplace,
+                                       int elem_size, int num_sms)
+{
+    const int big = elem_size == 8 ? 64 : 128, sml = elem_size == 8 ? 32 : 64;
+    auto ctas = [&](int64_t t) {
+        const int64_t gm = (M + t - 1) / t, gn = (N + t - 1) / t;
+        if (cmode != MASK_LOWER) return gm * gn;
+        int64_t c = 0;   // tiles with some i >= j
+        for (int64_t by = 0; by < gm; ++by) {
+            const int64_t last_n = (by * t + t - 1) / t;   // column tiles 0..last_n
+            c += (last_n + 1 < gn ? last_n + 1 : gn);
+        }
+        return c;
+    };
+    if (!inplace && ctas(big) < 2 * (int64_t)num_sms) return {sml, sml, true};
+    return {big, big, false};
+}
+int device_sm_count();   // SMs of the current device (cached per device)
+
 // C(M x N) = alpha * A(M x K) * B(N x K)^T + beta * C.  cmode MASK_LOWER
 // writes only i >= j.  amask / bmask treat an operand as triangular (entries
 // outside the triangle read as zero and are never loaded).  A may alias C
@@ -61,7 +90,7 @@ void stage_mark(cudaStream_t st, const char *name);   // end of one of its steps
 template <typename T>
 cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
                     int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
-                    const int32_t *abort);
+                    const int32_t *abort, bool inplace = false);
 
 // Solve X * op(Ltri) = alpha * X in place for an M x w strip (w <= 64);
 // op = transpose when transL != 0.  Rows are independent.

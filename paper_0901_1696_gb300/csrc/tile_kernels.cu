@@ -18,16 +18,20 @@
 
 namespace rfp {
 
-template <typename T>
-struct GemmCfg;
-template <>
-struct GemmCfg<double> {
-    static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, PAD = 2;
+// Tile configurations: BM x BN C tile, TM x TN per thread, BK-deep K steps.
+template <typename T, int BM_, int BN_, int TM_, int TN_>
+struct GemmCfg {
+    static constexpr int BM = BM_, BN = BN_, BK = 16, TM = TM_, TN = TN_;
+    static constexpr int TX = BN / TN, NT = (BM / TM) * (BN / TN);
+    static constexpr int PAD = 16 / (int)sizeof(T);
+    static_assert(NT % BM == 0 && NT % BN == 0 && NT % BK == 0, "loader mapping");
 };
-template <>
-struct GemmCfg<float> {
-    static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8, PAD = 4;
-};
+template <typename T> struct GemmBig;
+template <typename T> struct GemmSmall;
+template <> struct GemmBig<double> { using C = GemmCfg<double, 64, 64, 4, 4>; };
+template <> struct GemmSmall<double> { using C = GemmCfg<double, 32, 32, 4, 4>; };
+template <> struct GemmBig<float> { using C = GemmCfg<float, 128, 128, 8, 8>; };
+template <> struct GemmSmall<float> { using C = GemmCfg<float, 64, 64, 4, 4>; };
 
 template <typename T>
 struct GemmArgs {
@@ -46,13 +50,11 @@ __device__ __forceinline__ void load_vec(T *dst, const T *src, int n)
         if (i < n) dst[i] = src[i];
 }
 
-constexpr int kGemmThreads = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(GemmArgs<T> g)
+template <typename T, typename Cfg>
+__global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
 {
-    using Cfg = GemmCfg<T>;
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, TM = Cfg::TM, TN = Cfg::TN;
+    constexpr int kGemmThreads = Cfg::NT;
     constexpr int LDA_S = BM + Cfg::PAD, LDB_S = BN + Cfg::PAD;
     constexpr int A_PER = BM * BK / kGemmThreads, B_PER = BN * BK / kGemmThreads;
     __shared__ __align__(16) T As[2][BK][LDA_S];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(GemmArgs<T> g)
     if (g.bmask == MASK_UPPER) kbeg = max(kbeg, n0);
     const int64_t ntiles = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
 
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int tid = threadIdx.x, tx = tid % Cfg::TX, ty = tid / Cfg::TX;
     const bool a_mfast = (g.A.rs == 1), b_nfast = (g.B.rs == 1);
 
     T acc[TM][TN];
@@ -164,19 +166,41 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(GemmArgs<T> g)
     }
 }
 
+template <typename T, typename Cfg>
+static void launch_gemm(cudaStream_t st, const GemmArgs<T> &g)
+{
+    dim3 grid((unsigned)((g.N + Cfg::BN - 1) / Cfg::BN), (unsigned)((g.M + Cfg::BM - 1) / Cfg::BM));
+    gemm_nt_kernel<T, Cfg><<<grid, Cfg::NT, 0, st>>>(g);
+}
+
 template <typename T>
 cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
                     int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
-                    const int32_t *abort)
+                    const int32_t *abort, bool inplace)
 {
-    using Cfg = GemmCfg<T>;
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 && beta == T(1)) return cudaSuccess;
     GemmArgs<T> g{C, A, B, M, N, K, alpha, beta, cmode, amask, bmask, abort};
-    dim3 grid((unsigned)((N + Cfg::BN - 1) / Cfg::BN), (unsigned)((M + Cfg::BM - 1) / Cfg::BM));
-    gemm_nt_kernel<T><<<grid, kGemmThreads, 0, st>>>(g);
+    const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, inplace, (int)sizeof(T),
+                                               device_sm_count());
+    if (tc.small) launch_gemm<T, typename GemmSmall<T>::C>(st, g);
+    else launch_gemm<T, typename GemmBig<T>::C>(st, g);
     note_launch();
     return cudaGetLastError();
+}
+
+int device_sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            return 152;
+        cache[dev] = sms;
+    }
+    return cache[dev];
 }
 
 // ---------------------------------------------------------------------------
@@ -424,7 +448,7 @@ cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int6
 
 #define RFP_INSTANTIATE(T)                                                                    \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
-                                    int64_t, T, T, int, int, int, const int32_t *);           \
+                                    int64_t, T, T, int, int, int, const int32_t *, bool);     \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,  \
                                        const int32_t *);                                      \
     template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);       \

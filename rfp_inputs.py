@@ -49,11 +49,22 @@ def spectrum(n: int, kappa: float, rng) -> np.ndarray:
     return lam
 
 
+def _preload_torch_linalg(torch):
+    """torch loads its CUDA linear-algebra library lazily by file name; under
+    a profiler's injection that lookup can fail, so load it by full path."""
+    import ctypes
+    import os
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
 def spd_spectrum(n: int, seed: int = 0, kappa: float = 1e4, device=None):
     """A = Q diag(lam) Q^T, Haar Q.  Returns numpy (CPU) unless ``device`` is a
     torch CUDA device, in which case a torch FP64 tensor on that device."""
     if device is not None:
         import torch
+        _preload_torch_linalg(torch)
         g = torch.Generator(device=device)
         g.manual_seed(seed)
         G = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)

@@ -80,9 +80,6 @@ struct Launch {
     }
 };
 
-template <typename T> struct Cfg;
-template <> struct Cfg<double> { static constexpr int BM = 64, BN = 64; };
-template <> struct Cfg<float> { static constexpr int BM = 128, BN = 128; };
 
 bool aborted(Launch &L, const int32_t *abort) { return abort && L.rd(abort) != 0; }
 
@@ -94,6 +91,7 @@ void emu_register(void *p, size_t bytes) { g_regions.push_back({(uintptr_t)p, (u
 int emu_violations() { return g_violations; }
 const char *emu_message() { return g_msg; }
 long emu_launches() { return g_launches; }
+void emu_set_sms(int);
 }
 
 cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t)
@@ -110,13 +108,19 @@ cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t, cudaEvent_t) { *ms = 0.
 
 namespace rfp {
 
+// The emulated device has the SM count given by emu_set_sms (default 152).
+static int g_emu_sms = 152;
+int device_sm_count() { return g_emu_sms; }
+
 template <typename T>
 cudaError_t gemm_nt(cudaStream_t, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N, int64_t K,
-                    T alpha, T beta, int cmode, int amask, int bmask, const int32_t *abort)
+                    T alpha, T beta, int cmode, int amask, int bmask, const int32_t *abort,
+                    bool inplace)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 && beta == T(1)) return cudaSuccess;
-    const int BM = Cfg<T>::BM, BN = Cfg<T>::BN;
+    const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, inplace, (int)sizeof(T), device_sm_count());
+    const int BM = tc.bm, BN = tc.bn;
     Launch L;
     const int64_t gy = (M + BM - 1) / BM, gx = (N + BN - 1) / BN;
     for (int64_t by = 0; by < gy; ++by)
@@ -292,9 +296,11 @@ cudaError_t pack_copy(cudaStream_t, const Layout &Ly, bool lowerA, T *A, int64_t
     return L.commit();
 }
 
+extern "C" void emu_set_sms(int s) { g_emu_sms = s; }
+
 #define EMU_INST(T)                                                                                  \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \
-                                    T, T, int, int, int, const int32_t *);                           \
+                                    T, T, int, int, int, const int32_t *, bool);                     \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,         \
                                        const int32_t *);                                             \
     template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);              \

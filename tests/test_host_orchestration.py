@@ -29,7 +29,7 @@ CSRC = os.path.join(ROOT, "paper_0901_1696_gb300", "csrc")
 
 
 @pytest.fixture(scope="module")
-def emu(tmp_path_factory):
+def emu_lib(tmp_path_factory):
     so = str(tmp_path_factory.mktemp("emu") / "librfp_emu.so")
     cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-I", EMU_DIR, "-x", "c++",
            os.path.join(CSRC, "chol.cu"), os.path.join(CSRC, "api.cu"), "-x", "none",
@@ -40,7 +40,17 @@ def emu(tmp_path_factory):
     raw.emu_register.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
     raw.emu_message.restype = ctypes.c_char_p
     raw.emu_launches.restype = ctypes.c_long
+    raw.emu_set_sms.argtypes = [ctypes.c_int]
     return lib
+
+
+@pytest.fixture(params=[152, 1], ids=["sms152", "sms1"])
+def emu(emu_lib, request):
+    """The emulated device's SM count steers gemm_nt's tile choice: with 152
+    SMs the small launches take the small tiles, with 1 SM every launch takes
+    the large tiles, so both CTA decompositions go through the checks."""
+    emu_lib.lib.emu_set_sms(request.param)
+    return emu_lib
 
 
 def _register(emu, *arrays):
