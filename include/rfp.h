@@ -125,6 +125,26 @@ int rfp_dpftri(char transr, char uplo, int64_t n, double *arf, int32_t *info,
 int rfp_spftri(char transr, char uplo, int64_t n, float *arf, int32_t *info,
                void *stream);
 
+/*
+ * rfp_ssyrk_tc: the SYRK of PFTRF step 3 (Fig. 4, T2 <- T2 - S S^T) on the
+ * tcgen05 tensor cores, the building block of the mixed-precision modes.
+ * C (n x n, FP32, column-major, ldc >= max(1,n)) <- alpha * A * A^T + beta * C
+ * on the lower triangle (uplo must be 'L'; the strict upper triangle of C is
+ * not touched).  A is n x k stored K-contiguous (element (i, p) at
+ * A[i*lda + p]) in the precision `prec`: RFP_PREC_BF16 (bfloat16, tensor-core
+ * kind::f16) or RFP_PREC_TF32 (float read as TF32, kind::tf32); products are
+ * accumulated in FP32.  A must be 16-byte aligned and lda * element size a
+ * multiple of 16 bytes.  beta == 0 does not read C.  *d_err (device int32)
+ * is set non-zero if a bounded wait inside the kernel expired (C is then
+ * unspecified); it is not cleared by the call.
+ * Arguments: 1 uplo, 2 n, 3 k, 4 alpha, 5 A, 6 lda, 7 prec, 8 beta, 9 C,
+ * 10 ldc, 11 d_err, 12 stream.
+ */
+#define RFP_PREC_BF16 0
+#define RFP_PREC_TF32 1
+int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, int64_t lda,
+                 int prec, float beta, float *C, int64_t ldc, int32_t *d_err, void *stream);
+
 /* Text for a return code of this library (static storage, never NULL). */
 const char *rfp_status_string(int status);
 

@@ -24,5 +24,8 @@ from .binding import (  # noqa: F401
     rfp_stage_timing,
     rfp_stage_times,
     rfp_sunpack,
+    rfp_ssyrk_tc,
+    RFP_PREC_BF16,
+    RFP_PREC_TF32,
 )
 from .flops import pftrf_flops, pftri_flops, pftrs_flops, pack_bytes  # noqa: F401

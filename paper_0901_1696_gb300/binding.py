@@ -43,7 +43,10 @@ SIGNATURES = {
     "rfp_spftrs": [_c, _c, _i64, _i64, _p, _p, _i64, _p],
     "rfp_dpftri": [_c, _c, _i64, _p, _i32p, _p],
     "rfp_spftri": [_c, _c, _i64, _p, _i32p, _p],
+    "rfp_ssyrk_tc": [_c, _i64, _i64, ctypes.c_float, _p, _i64, ctypes.c_int, ctypes.c_float, _p,
+                     _i64, _i32p, _p],
 }
+RFP_PREC_BF16, RFP_PREC_TF32 = 0, 1
 
 
 def _addr(x) -> int | None:
@@ -167,6 +170,11 @@ class Library:
                                      _stream(stream))
         return self._check(name, rc)
 
+    def rfp_ssyrk_tc(self, uplo, n, k, alpha, A, lda, prec, beta, C, ldc, d_err, stream=None):
+        rc = self.lib.rfp_ssyrk_tc(_ch(uplo), n, k, alpha, _addr(A), lda, prec, beta, _addr(C), ldc,
+                                   _addr(d_err), _stream(stream))
+        return self._check("rfp_ssyrk_tc", rc)
+
     def rfp_dpftrs(self, transr, uplo, n, nrhs, arf, B, ldb, stream=None):
         return self._trs("rfp_dpftrs", transr, uplo, n, nrhs, arf, B, ldb, stream)
 
@@ -203,3 +211,4 @@ rfp_dunpack, rfp_sunpack = _fwd("rfp_dunpack"), _fwd("rfp_sunpack")
 rfp_dpftrf, rfp_spftrf = _fwd("rfp_dpftrf"), _fwd("rfp_spftrf")
 rfp_dpftrs, rfp_spftrs = _fwd("rfp_dpftrs"), _fwd("rfp_spftrs")
 rfp_dpftri, rfp_spftri = _fwd("rfp_dpftri"), _fwd("rfp_spftri")
+rfp_ssyrk_tc = _fwd("rfp_ssyrk_tc")

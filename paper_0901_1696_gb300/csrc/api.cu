@@ -234,6 +234,25 @@ int rfp_spftri(char transr, char uplo, int64_t n, float *arf, int32_t *info, voi
     return pftri_entry<float>(transr, uplo, n, arf, info, stream);
 }
 
+int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, int64_t lda,
+                 int prec, float beta, float *C, int64_t ldc, int32_t *d_err, void *stream)
+{
+    if (uplo != 'L' && uplo != 'l') return -1;
+    if (n < 0 || n > (int64_t(1) << 30)) return -2;
+    if (k < 0 || k > (int64_t(1) << 30)) return -3;
+    if (prec != RFP_PREC_BF16 && prec != RFP_PREC_TF32) return -7;
+    const int esz = prec == RFP_PREC_BF16 ? 2 : 4;
+    if (n == 0) return RFP_OK;
+    if (!A || (reinterpret_cast<uintptr_t>(A) % 16)) return -5;
+    if (lda < (k > 1 ? k : 1) || (lda * esz) % 16) return -6;
+    if (!C || !aligned(C)) return -9;
+    if (ldc < n) return -10;
+    if (!d_err || !aligned(d_err)) return -11;
+    rfp::View<float> Cv{C, 1, ldc};
+    return finish(rfp::tc_gemm_nt((cudaStream_t)stream, prec, A, n, lda, 0, A, n, lda, 0, Cv, n,
+                                  n, k, alpha, beta, rfp::MASK_LOWER, d_err));
+}
+
 const char *rfp_status_string(int status)
 {
     if (status == RFP_OK) return "success";

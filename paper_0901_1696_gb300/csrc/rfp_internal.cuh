@@ -116,6 +116,18 @@ template <typename T>
 cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int64_t n2,
                        int32_t *info);
 
+// Tensor-core GEMM update (tc_gemm.cu): C (FP32 view, M x N) = alpha A B^T +
+// beta C, A / B K-contiguous low-precision matrices (kind 0: BF16, kind 1:
+// FP32 read as TF32) with a_rows / b_rows rows `pitch` elements apart (pitch
+// * element size a multiple of 16 bytes, base 16-byte aligned); rows
+// a_row0.. / b_row0.. are used.  cmode MASK_LOWER with M == N launches only
+// the lower-triangular tiles.  *err receives a non-zero code if a bounded
+// wait inside the kernel expires.
+cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows,
+                       int64_t a_pitch_elems, int a_row0, const void *B, int64_t b_rows,
+                       int64_t b_pitch_elems, int b_row0, View<float> C, int64_t M, int64_t N,
+                       int64_t K, float alpha, float beta, int cmode, int *err);
+
 // TRTTF / TFTTR copies.
 template <typename T>
 cudaError_t pack_copy(cudaStream_t st, const Layout &L, bool lowerA, T *A, int64_t lda, T *arf,

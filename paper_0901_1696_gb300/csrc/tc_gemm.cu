@@ -1,0 +1,387 @@
+// Tensor-core (tcgen05) low-precision GEMM update for the mixed-precision
+// factorization: C (FP32, strided view) = alpha * A * B^T + beta * C, with A
+// (M x K) and B (N x K) stored K-contiguous in BF16 (kind::f16) or FP32 read
+// as TF32 (kind::tf32), accumulated in FP32 in tensor memory.
+//
+// This is the SYRK / GEMM of the paper's step 3 (Fig. 4, T2 <- T2 - S S^T)
+// and of the trailing updates inside the Cholesky of a triangle, run on the
+// 5th-generation tensor cores:
+//   * one 128 x 128 output tile per CTA (TMEM: 128 lanes x 128 FP32 columns),
+//   * warp 4 issues TMA loads (cp.async.bulk.tensor.2d, 128-byte swizzle) of
+//     128-byte K slices of A and B into a 4-stage shared-memory ring,
+//   * warp 5 (one thread) issues tcgen05.mma (K = 32 bytes per instruction)
+//     and tcgen05.commit to release each stage and finally the accumulator,
+//   * warps 0-3 read the accumulator with tcgen05.ld (one TMEM lane per
+//     thread = one C row) and apply the masked epilogue to C.
+// Every mbarrier wait is bounded by time; on expiry the kernel records an
+// error code in *err, stops issuing work, waits (bounded) for its in-flight
+// copies and MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+namespace tc {
+
+constexpr int kBM = 128, kBN = 128, kStages = 4;
+constexpr int kRowBytes = 128;                    // one K slice per row (swizzle span)
+constexpr int kTileBytes = kBM * kRowBytes;       // 16 KB per operand per stage
+constexpr int kThreads = 192;                     // 4 epilogue warps + TMA warp + MMA warp
+constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s bound on any single wait
+constexpr int kSmemBytes = 1024 /*align*/ + 2 * kStages * kTileBytes + 256;
+
+struct Args {
+    float *C;
+    int64_t crs, ccs;       // C element (i, j) at C[i*crs + j*ccs]
+    int64_t M, N, K;        // K in elements
+    int a_row0, b_row0;     // first row of A / B inside their tensor maps
+    float alpha, beta;
+    int cmode;              // MASK_LOWER: write only i >= j (C-local)
+    int tiles_n;            // column tiles
+    int lower_tiles;        // 1: blockIdx.x enumerates the lower-triangular tile set
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier; false (and *err set) on
+// expiry or when another role already failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code)
+{
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255) {
+            if (*(volatile int *)err != 0) return false;
+            if (globaltimer() - t0 > kWaitNs) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)(16u >> 4) << 16;                   // leading byte offset (unused, SW128 K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: 8-row group pitch
+    d |= (uint64_t)1 << 46;                            // fixed field 0b001
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format, both K-major, N, M.
+template <int KIND>
+__host__ __device__ constexpr uint32_t instr_desc()
+{
+    return (1u << 4)                                    // D = F32
+           | ((KIND == 0 ? 1u : 2u) << 7)               // A = BF16 (f16 kind) / TF32
+           | ((KIND == 0 ? 1u : 2u) << 10)              // B = BF16 / TF32
+           | ((uint32_t)(kBN >> 3) << 17)               // N / 8
+           | ((uint32_t)(kBM >> 4) << 24);              // M / 16
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                    uint32_t accumulate)
+{
+    constexpr uint32_t idesc = instr_desc<KIND>();
+    if (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   Args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + kStages * kTileBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kStages * kTileBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *accf = empty + kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    // Tile coordinates.
+    int64_t tm, tn;
+    if (a.lower_tiles) {   // row-major lower-triangular tile list
+        const int64_t t = blockIdx.x;
+        int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+        while (r * (r + 1) / 2 > t) --r;
+        tm = r;
+        tn = t - r * (r + 1) / 2;
+    } else {
+        tm = blockIdx.x / a.tiles_n;
+        tn = blockIdx.x % a.tiles_n;
+    }
+    const int64_t m0 = tm * kBM, n0 = tn * kBN;
+    const int bk = kRowBytes / (KIND == 0 ? 2 : 4);                 // K elements per stage
+    const int nk = (int)((a.K + bk - 1) / bk);
+
+    if (warp == 0) {   // one warp allocates the accumulator columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;     // stages loaded by the producer (producer thread only)
+    if (warp == 4 && lane == 0) {
+        // ---- TMA producer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kStages, r = kt / kStages;
+            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, a.err, 1)) break;
+            mbar_expect_tx(&full[s], 2 * kTileBytes);
+            tma_load_2d(sA + s * kTileBytes, &tmA, &full[s], kt * bk, a.a_row0 + (int)m0);
+            tma_load_2d(sB + s * kTileBytes, &tmB, &full[s], kt * bk, a.b_row0 + (int)n0);
+            issued = kt + 1;
+        }
+        // On failure, let the copies already issued land before the CTA exits.
+        if (issued < nk)
+            for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
+                mbar_wait(&full[kt % kStages], (kt / kStages) & 1, a.err, 1);
+    } else if (warp == 5 && lane == 0) {
+        // ---- MMA issuer
+        bool ok = true;
+        int kt = 0;
+        for (; kt < nk; ++kt) {
+            const int s = kt % kStages, r = kt / kStages;
+            if (!mbar_wait(&full[s], r & 1, a.err, 2)) { ok = false; break; }
+            fence_after();
+            const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+#pragma unroll
+            for (int kk = 0; kk < kRowBytes / 32; ++kk)
+                mma<KIND>(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
+                          (kt | kk) != 0 ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(accf);   // arrives once every MMA issued above has completed
+        (void)ok;
+    } else if (warp < 4) {
+        // ---- epilogue: lane = row of the tile
+        // warp-uniform decision: tcgen05.ld is a .sync.aligned warp instruction
+        const bool have = __all_sync(0xffffffffu, nk > 0 && mbar_wait(accf, 0, a.err, 3));
+        fence_after();
+        const int64_t i = m0 + warp * 32 + lane;
+        const bool row_ok = i < a.M && *(volatile int *)a.err == 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+            float v[32];
+            if (have) tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0.f;
+            }
+            if (!row_ok || (nk > 0 && !have)) continue;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int64_t j = n0 + c0 + q;
+                if (j >= a.N || (a.cmode == MASK_LOWER && j > i)) continue;
+                float *pc = a.C + i * a.crs + j * a.ccs;
+                float out = a.alpha * v[q];
+                if (a.beta != 0.f) out = fmaf(a.beta, *pc, out);
+                *pc = out;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN)
+                     : "memory");
+    }
+}
+
+// ---- host side --------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D tensor map over a K-contiguous matrix: `rows` rows of `cols` elements,
+// `pitch_bytes` apart (multiple of 16), box = 128 rows x 128 bytes, 128-byte
+// swizzle, zero fill outside the matrix.
+cudaError_t make_map(CUtensorMap *map, const void *ptr, int kind, int64_t rows, int64_t cols,
+                     int64_t pitch_bytes)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int esz = kind == 0 ? 2 : 4;
+    if ((reinterpret_cast<uintptr_t>(ptr) % 16) || (pitch_bytes % 16)) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace tc
+
+cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows, int64_t a_pitch_elems,
+                       int a_row0, const void *B, int64_t b_rows, int64_t b_pitch_elems, int b_row0,
+                       View<float> C, int64_t M, int64_t N, int64_t K, float alpha, float beta,
+                       int cmode, int *err)
+{
+    using namespace tc;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int esz = kind == 0 ? 2 : 4;
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, A, kind, a_rows, K, a_pitch_elems * esz);
+    if (e != cudaSuccess) return e;
+    e = make_map(&mb, B, kind, b_rows, K, b_pitch_elems * esz);
+    if (e != cudaSuccess) return e;
+    Args args;
+    args.C = C.p; args.crs = C.rs; args.ccs = C.cs;
+    args.M = M; args.N = N; args.K = K;
+    args.a_row0 = a_row0; args.b_row0 = b_row0;
+    args.alpha = alpha; args.beta = beta; args.cmode = cmode;
+    const int64_t tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + kBN - 1) / kBN;
+    args.tiles_n = (int)tiles_n;
+    args.lower_tiles = (cmode == MASK_LOWER && M == N) ? 1 : 0;
+    args.err = err;
+    const int64_t grid = args.lower_tiles ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+    if (kind == 0) {
+        e = cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        tc_gemm_kernel<0><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(ma, mb, args);
+    } else {
+        e = cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        tc_gemm_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(ma, mb, args);
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace rfp

@@ -298,6 +298,53 @@ cudaError_t pack_copy(cudaStream_t, const Layout &Ly, bool lowerA, T *A, int64_t
 
 extern "C" void emu_set_sms(int s) { g_emu_sms = s; }
 
+// Tensor-core GEMM update: 128 x 128 tiles, lower-triangular tile list when
+// cmode is lower and M == N, operands read as BF16 (kind 0) or FP32 (kind 1).
+cudaError_t tc_gemm_nt(cudaStream_t, int kind, const void *A, int64_t a_rows, int64_t a_pitch,
+                       int a_row0, const void *B, int64_t b_rows, int64_t b_pitch, int b_row0,
+                       View<float> C, int64_t M, int64_t N, int64_t K, float alpha, float beta,
+                       int cmode, int *err)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int T = 128, esz = kind == 0 ? 2 : 4;
+    if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || (a_pitch * esz) % 16 || (b_pitch * esz) % 16) {
+        violation("tensor map alignment", A);
+        return cudaErrorInvalidValue;
+    }
+    Launch L;
+    auto load = [&](const void *base, int64_t pitch, int64_t rows, int64_t r, int64_t k) -> float {
+        if (r >= rows || k >= K) return 0.f;   // TMA zero fill outside the matrix
+        if (kind == 0) {
+            const uint16_t *p = (const uint16_t *)base + r * pitch + k;
+            uint32_t bits = (uint32_t)L.rd(p) << 16;
+            float f;
+            memcpy(&f, &bits, 4);
+            return f;
+        }
+        return L.rd((const float *)base + r * pitch + k);
+    };
+    const int64_t gm = (M + T - 1) / T, gn = (N + T - 1) / T;
+    const bool lower_tiles = cmode == MASK_LOWER && M == N;
+    int cta = 0;
+    for (int64_t tm = 0; tm < gm; ++tm)
+        for (int64_t tn = 0; tn < (lower_tiles ? tm + 1 : gn); ++tn, ++cta) {
+            L.cta = cta;
+            for (int64_t i = tm * T; i < std::min(M, tm * T + T); ++i)
+                for (int64_t j = tn * T; j < std::min(N, tn * T + T); ++j) {
+                    double acc = 0;
+                    for (int64_t k = 0; k < K; ++k)
+                        acc += (double)load(A, a_pitch, a_rows, a_row0 + i, k) *
+                               (double)load(B, b_pitch, b_rows, b_row0 + j, k);
+                    if (cmode == MASK_LOWER && j > i) continue;
+                    float v = alpha * (float)acc;
+                    if (beta != 0.f) v = beta * L.rd(&C(i, j)) + v;
+                    L.wr(&C(i, j), v);
+                }
+        }
+    (void)err;
+    return L.commit();
+}
+
 #define EMU_INST(T)                                                                                  \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \
                                     T, T, int, int, int, const int32_t *, bool);                     \
