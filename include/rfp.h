@@ -36,6 +36,7 @@
 #ifndef RFP_H
 #define RFP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -144,6 +145,43 @@ int rfp_spftri(char transr, char uplo, int64_t n, float *arf, int32_t *info,
 #define RFP_PREC_TF32 1
 int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, int64_t lda,
                  int prec, float beta, float *C, int64_t ldc, int32_t *d_err, void *stream);
+
+/*
+ * rfp_dpfsv_mixed: solve A X = B for the SPD matrix A held in FP64 RFPF
+ * (arf, any of the eight layouts, left unchanged) by factoring a
+ * low-precision copy and refining in FP64.  This is the mixed-precision
+ * direction of the project: the algorithms of Sections 3-4 are unchanged
+ * apart from the precision of their Level-3 steps; there is no counterpart
+ * in the paper (its routines are FP64 or FP32 throughout).
+ *   prec RFP_PREC_FP32: FP32 factorization on the FP32 FMA pipes;
+ *   prec RFP_PREC_TF32 / RFP_PREC_BF16: FP32 storage, the SYRK updates of
+ *        512-wide panels on tcgen05 tensor cores from TF32 / BF16 operands
+ *        with FP32 accumulation.
+ * Refinement: X = 0, R = B, then up to max_iter times D = (L L^T)^{-1} R in
+ * FP32, X += D in FP64, R = B - A X in FP64 from arf; it stops as soon as
+ * max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol, decided on
+ * the device (no host synchronization).  B (n x nrhs, ldb) is read only; X
+ * (n x nrhs, ldx) receives the solution.
+ * work: caller-owned device workspace of at least rfp_dpfsv_mixed_workspace
+ * bytes, 256-byte aligned (FP32 copy of A in full storage, 4 n^2 bytes, plus
+ * O(n * (512 + nrhs)) panel and residual buffers).
+ * status (device, caller-owned) receives: info (first failing pivot of the
+ * low-precision factorization, 0 if none), iterations, converged (1/0),
+ * tc_error (non-zero if a tensor-core kernel's bounded wait expired),
+ * backward_error (last value of the criterion above).
+ * Arguments: 1 transr, 2 uplo, 3 n, 4 nrhs, 5 arf, 6 B, 7 ldb, 8 X, 9 ldx,
+ * 10 prec, 11 max_iter, 12 tol, 13 work, 14 work_bytes, 15 status, 16 stream.
+ */
+#define RFP_PREC_FP32 2
+typedef struct rfp_mixed_status {
+    int32_t info, iterations, converged, tc_error;
+    double backward_error;
+} rfp_mixed_status_t;
+size_t rfp_dpfsv_mixed_workspace(int64_t n, int64_t nrhs, int prec);
+int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
+                    const double *B, int64_t ldb, double *X, int64_t ldx, int prec, int max_iter,
+                    double tol, void *work, size_t work_bytes, rfp_mixed_status_t *status,
+                    void *stream);
 
 /* Text for a return code of this library (static storage, never NULL). */
 const char *rfp_status_string(int status);

@@ -27,5 +27,9 @@ from .binding import (  # noqa: F401
     rfp_ssyrk_tc,
     RFP_PREC_BF16,
     RFP_PREC_TF32,
+    RFP_PREC_FP32,
+    rfp_dpfsv_mixed,
+    rfp_dpfsv_mixed_workspace,
+    mixed_status,
 )
 from .flops import pftrf_flops, pftri_flops, pftrs_flops, pack_bytes  # noqa: F401

@@ -43,10 +43,24 @@ SIGNATURES = {
     "rfp_spftrs": [_c, _c, _i64, _i64, _p, _p, _i64, _p],
     "rfp_dpftri": [_c, _c, _i64, _p, _i32p, _p],
     "rfp_spftri": [_c, _c, _i64, _p, _i32p, _p],
+    "rfp_dpfsv_mixed": [_c, _c, _i64, _i64, _p, _p, _i64, _p, _i64, ctypes.c_int, ctypes.c_int,
+                        ctypes.c_double, _p, ctypes.c_size_t, _p, _p],
     "rfp_ssyrk_tc": [_c, _i64, _i64, ctypes.c_float, _p, _i64, ctypes.c_int, ctypes.c_float, _p,
                      _i64, _i32p, _p],
 }
-RFP_PREC_BF16, RFP_PREC_TF32 = 0, 1
+RFP_PREC_BF16, RFP_PREC_TF32, RFP_PREC_FP32 = 0, 1, 2
+
+
+class RfpMixedStatus(ctypes.Structure):
+    _fields_ = [("info", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("tc_error", ctypes.c_int32),
+                ("backward_error", ctypes.c_double)]
+
+
+def mixed_status(raw: bytes) -> dict:
+    """Decode the 24-byte rfp_mixed_status_t read back from the device."""
+    st = RfpMixedStatus.from_buffer_copy(bytes(raw))
+    return {f: getattr(st, f) for f, _ in RfpMixedStatus._fields_}
 
 
 def _addr(x) -> int | None:
@@ -170,6 +184,18 @@ class Library:
                                      _stream(stream))
         return self._check(name, rc)
 
+    def rfp_dpfsv_mixed_workspace(self, n, nrhs, prec) -> int:
+        f = self.lib.rfp_dpfsv_mixed_workspace
+        f.argtypes, f.restype = [_i64, _i64, ctypes.c_int], ctypes.c_size_t
+        return int(f(n, nrhs, prec))
+
+    def rfp_dpfsv_mixed(self, transr, uplo, n, nrhs, arf, B, ldb, X, ldx, prec, max_iter, tol,
+                        work, work_bytes, status, stream=None):
+        rc = self.lib.rfp_dpfsv_mixed(_ch(transr), _ch(uplo), n, nrhs, _addr(arf), _addr(B), ldb,
+                                      _addr(X), ldx, prec, max_iter, tol, _addr(work), work_bytes,
+                                      _addr(status), _stream(stream))
+        return self._check("rfp_dpfsv_mixed", rc)
+
     def rfp_ssyrk_tc(self, uplo, n, k, alpha, A, lda, prec, beta, C, ldc, d_err, stream=None):
         rc = self.lib.rfp_ssyrk_tc(_ch(uplo), n, k, alpha, _addr(A), lda, prec, beta, _addr(C), ldc,
                                    _addr(d_err), _stream(stream))
@@ -212,3 +238,4 @@ rfp_dpftrf, rfp_spftrf = _fwd("rfp_dpftrf"), _fwd("rfp_spftrf")
 rfp_dpftrs, rfp_spftrs = _fwd("rfp_dpftrs"), _fwd("rfp_spftrs")
 rfp_dpftri, rfp_spftri = _fwd("rfp_dpftri"), _fwd("rfp_spftri")
 rfp_ssyrk_tc = _fwd("rfp_ssyrk_tc")
+rfp_dpfsv_mixed, rfp_dpfsv_mixed_workspace = _fwd("rfp_dpfsv_mixed"), _fwd("rfp_dpfsv_mixed_workspace")

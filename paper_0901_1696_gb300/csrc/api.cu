@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/rfp.h"
+#include "mixed_internal.cuh"
 #include "rfp_internal.cuh"
 
 namespace rfp {
@@ -251,6 +252,43 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
     rfp::View<float> Cv{C, 1, ldc};
     return finish(rfp::tc_gemm_nt((cudaStream_t)stream, prec, A, n, lda, 0, A, n, lda, 0, Cv, n,
                                   n, k, alpha, beta, rfp::MASK_LOWER, d_err));
+}
+
+size_t rfp_dpfsv_mixed_workspace(int64_t n, int64_t nrhs, int prec)
+{
+    if (n <= 0 || nrhs <= 0 || n > kMaxN) return 0;
+    if (prec != RFP_PREC_BF16 && prec != RFP_PREC_TF32 && prec != RFP_PREC_FP32) return 0;
+    return rfp::mixed_workspace_bytes(n, nrhs, prec);
+}
+
+int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
+                    const double *B, int64_t ldb, double *X, int64_t ldx, int prec, int max_iter,
+                    double tol, void *work, size_t work_bytes, rfp_mixed_status_t *status,
+                    void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN || n > (int64_t(1) << 31) - 1) return -3;
+    if (nrhs < 0 || nrhs > (int64_t(1) << 31) - 1) return -4;
+    if (prec != RFP_PREC_BF16 && prec != RFP_PREC_TF32 && prec != RFP_PREC_FP32) return -10;
+    if (max_iter < 0) return -11;
+    if (!(tol >= 0.0)) return -12;
+    if (!status || !aligned(status)) return -15;
+    if (n == 0 || nrhs == 0)
+        return finish(cudaMemsetAsync(status, 0, sizeof(rfp_mixed_status_t), (cudaStream_t)stream));
+    if (!arf || !aligned(arf)) return -5;
+    if (!B || !aligned(B)) return -6;
+    if (ldb < n) return -7;
+    if (!X || !aligned(X)) return -8;
+    if (ldx < n) return -9;
+    rfp::MixedWork w;
+    if (!work) return -13;
+    if (!rfp::mixed_carve(work, work_bytes, n, nrhs, prec, &w))
+        return (reinterpret_cast<uintptr_t>(work) % 256) ? -13 : -14;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    return finish(rfp::pfsv_mixed_impl((cudaStream_t)stream, L, arf, B, ldb, X, ldx, nrhs, prec,
+                                       max_iter, tol, w, status));
 }
 
 const char *rfp_status_string(int status)

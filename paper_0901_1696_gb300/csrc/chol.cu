@@ -31,7 +31,7 @@ constexpr int64_t kNb = 64;   // diagonal tile width
 // Right-looking blocked Cholesky of the m x m lower triangle V in place
 // (LAPACK POTRF 'L' on one RFP triangle).  Failure index offset by `base`.
 template <typename T>
-static cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info,
+cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info,
                                  int64_t base)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
@@ -48,7 +48,7 @@ static cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t 
 
 // X (rows x m) <- X L^{-T}, L the m x m lower triangle V (right-looking).
 template <typename T>
-static cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
+cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
                                           int64_t m, const int32_t *abort)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
@@ -64,7 +64,7 @@ static cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t ro
 // X (rows x m) <- alpha X L^{-1}, L the m x m lower triangle V (columns from
 // the right).
 template <typename T>
-static cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
+cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
                                             int64_t m, T alpha, const int32_t *abort)
 {
     const int64_t nblk = (m + kNb - 1) / kNb;
@@ -81,7 +81,7 @@ static cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t 
 
 // L X = B in place, B (m x nrhs), L the m x m lower triangle V (forward).
 template <typename T>
-static cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
+cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
                                            int64_t m, const int32_t *abort)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
@@ -97,7 +97,7 @@ static cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t n
 
 // L^T X = B in place, B (m x nrhs), L the m x m lower triangle V (backward).
 template <typename T>
-static cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
+cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
                                          int64_t m, const int32_t *abort)
 {
     const int64_t nblk = (m + kNb - 1) / kNb;
@@ -118,7 +118,7 @@ static cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrh
 //   W_pp = L_pp^{-1};  X(p, :p) <- W_pp X(p, :p);
 //   X(i>p, :p) -= L(i, p) X(p, :p);  X(i>p, p) <- -L(i, p) W_pp.
 template <typename T>
-static cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
+cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
@@ -141,7 +141,7 @@ static cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const in
 // Block row q contributes W(q, :)^T W(q, :) to rows <= q; processed in
 // increasing q, rows < q already hold partial sums, row q still holds W.
 template <typename T>
-static cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
+cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
@@ -238,6 +238,18 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     stage_mark(st, "pftri.lauum_t2");
     return cudaSuccess;
 }
+
+#define RFP_BLOCKED_INST(T)                                                                      \
+    template cudaError_t potrf_blocked<T>(cudaStream_t, View<T>, int64_t, int32_t *, int64_t);     \
+    template cudaError_t trsm_right_lower_trans<T>(cudaStream_t, View<T>, int64_t, View<T>, int64_t, \
+                                                   const int32_t *);                               \
+    template cudaError_t trsm_left_lower_notrans<T>(cudaStream_t, View<T>, int64_t, View<T>,       \
+                                                    int64_t, const int32_t *);                     \
+    template cudaError_t trsm_left_lower_trans<T>(cudaStream_t, View<T>, int64_t, View<T>, int64_t, \
+                                                  const int32_t *);
+RFP_BLOCKED_INST(float)
+RFP_BLOCKED_INST(double)
+#undef RFP_BLOCKED_INST
 
 template cudaError_t pftrf_impl<double>(cudaStream_t, const Layout &, double *, int32_t *);
 template cudaError_t pftrf_impl<float>(cudaStream_t, const Layout &, float *, int32_t *);

@@ -1,0 +1,174 @@
+// Mixed-precision solve of A X = B for an SPD matrix held in FP64 RFPF:
+// factor a low-precision copy, refine in FP64 (the precision direction of
+// the project; the method of Sections 3-4 is unchanged apart from the
+// precision of its Level-3 steps).
+//
+//   1. W = fl32(A) (lower triangle of the logical matrix, FP32, full storage)
+//   2. W = L L^T in FP32 storage: the blocked Cholesky of Section 3 on W with
+//      the SYRK / GEMM updates in
+//        RFP_PREC_FP32: FP32 FMA (SIMT), the s-precision kernels,
+//        RFP_PREC_TF32 / RFP_PREC_BF16: tcgen05 tensor cores (rfp_ssyrk_tc's
+//        kernel) on 512-wide panels converted to TF32 / BF16, FP32 accumulate;
+//      the diagonal blocks and the panel solves stay in FP32.
+//   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 solves, Section 4),
+//      X += D (FP64), R = B - A X with A read from the FP64 RFP array (FP64),
+//      until max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol
+//      or max_iter steps.  Convergence is decided on the device: every later
+//      kernel of the fixed launch sequence returns at once.
+#include "mixed_internal.cuh"
+
+namespace rfp {
+
+namespace {
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int64_t ldw_for(int64_t n) { return (n + 31) / 32 * 32; }
+size_t panel_elem(int prec) { return prec == RFP_PREC_BF16 ? 2 : 4; }
+}  // namespace
+
+size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec)
+{
+    size_t b = 0;
+    b += up((size_t)ldw_for(n) * (size_t)n * sizeof(float));                  // W
+    if (prec != RFP_PREC_FP32) b += up((size_t)n * kMixedPanel * panel_elem(prec));   // P
+    b += up((size_t)n * (size_t)nrhs * sizeof(double));                       // R
+    b += up((size_t)n * (size_t)nrhs * sizeof(float));                        // D
+    b += up((size_t)nrhs * sizeof(double));                                   // berr
+    b += up(sizeof(double)) + up(sizeof(int32_t)) + up(sizeof(int32_t));      // anorm, stop, tc_err
+    return b;
+}
+
+bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, MixedWork *w)
+{
+    if (reinterpret_cast<uintptr_t>(work) % kAlign) return false;
+    if (bytes < mixed_workspace_bytes(n, nrhs, prec)) return false;
+    char *p = static_cast<char *>(work);
+    w->ldw = ldw_for(n);
+    w->W = reinterpret_cast<float *>(p);
+    p += up((size_t)w->ldw * (size_t)n * sizeof(float));
+    w->P = nullptr;
+    if (prec != RFP_PREC_FP32) {
+        w->P = p;
+        p += up((size_t)n * kMixedPanel * panel_elem(prec));
+    }
+    w->R = reinterpret_cast<double *>(p);
+    p += up((size_t)n * (size_t)nrhs * sizeof(double));
+    w->D = reinterpret_cast<float *>(p);
+    p += up((size_t)n * (size_t)nrhs * sizeof(float));
+    w->berr = reinterpret_cast<double *>(p);
+    p += up((size_t)nrhs * sizeof(double));
+    w->anorm = reinterpret_cast<double *>(p);
+    p += up(sizeof(double));
+    w->stop = reinterpret_cast<int32_t *>(p);
+    p += up(sizeof(int32_t));
+    w->tc_err = reinterpret_cast<int32_t *>(p);
+    return true;
+}
+
+#define RFP_TRY(x)                        \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+// Blocked right-looking Cholesky of the FP32 working matrix with the trailing
+// update of each 512-wide panel on the tensor cores.
+static cudaError_t factor_tc(cudaStream_t st, View<float> W, int64_t n, int prec,
+                             const MixedWork &w, int32_t *info)
+{
+    for (int64_t j0 = 0; j0 < n; j0 += kMixedPanel) {
+        const int64_t j1 = std::min(j0 + kMixedPanel, n), nb = j1 - j0;
+        RFP_TRY(potrf_blocked<float>(st, W.sub(j0, j0), nb, info, j0));
+        if (j1 >= n) break;
+        const int64_t m = n - j1;
+        RFP_TRY(trsm_right_lower_trans<float>(st, W.sub(j1, j0), m, W.sub(j0, j0), nb, info));
+        // panel -> K-contiguous low-precision copy P (row r, column k at P[r*512 + k])
+        if (prec == RFP_PREC_BF16) {
+            View<__nv_bfloat16> P{static_cast<__nv_bfloat16 *>(w.P), kMixedPanel, 1};
+            RFP_TRY((convert<float, __nv_bfloat16>(st, W.sub(j1, j0), P, m, nb, false, info)));
+        } else {
+            View<float> P{static_cast<float *>(w.P), kMixedPanel, 1};
+            RFP_TRY((convert<float, float>(st, W.sub(j1, j0), P, m, nb, false, info)));
+        }
+        RFP_TRY(tc_gemm_nt(st, prec, w.P, m, kMixedPanel, 0, w.P, m, kMixedPanel, 0, W.sub(j1, j1),
+                           m, m, nb, -1.0f, 1.0f, MASK_LOWER, w.tc_err));
+    }
+    return cudaSuccess;
+}
+
+// R = B - A X with A read from its FP64 RFP blocks (A11 = T1, A21 = S,
+// A22 = T2 as stored lower triangles; the strict upper halves come from
+// the transposed views).
+static cudaError_t residual(cudaStream_t st, const RfpViews &v, View<double> B, View<double> X,
+                            View<double> R, int64_t nrhs, const int32_t *stop)
+{
+    const int64_t n1 = v.n1, n2 = v.n2;
+    RFP_TRY((convert<double, double>(st, B, R, n1 + n2, nrhs, false, stop)));
+    View<double> R1 = R, R2 = R.sub(n1, 0), X1 = X, X2 = X.sub(n1, 0);
+    const double m1 = -1.0, p1 = 1.0;
+    if (n1 > 0) {
+        RFP_TRY(gemm_nt<double>(st, R1, v.t1, X1.t(), n1, nrhs, n1, m1, p1, MASK_NONE, MASK_LOWER,
+                                MASK_NONE, stop));
+        RFP_TRY(gemm_nt<double>(st, R1, v.t1.t(), X1.t(), n1, nrhs, n1, m1, p1, MASK_NONE,
+                                MASK_STRICT_UPPER, MASK_NONE, stop));
+    }
+    if (n1 > 0 && n2 > 0) {
+        RFP_TRY(gemm_nt<double>(st, R1, v.s.t(), X2.t(), n1, nrhs, n2, m1, p1, MASK_NONE, MASK_NONE,
+                                MASK_NONE, stop));
+        RFP_TRY(gemm_nt<double>(st, R2, v.s, X1.t(), n2, nrhs, n1, m1, p1, MASK_NONE, MASK_NONE,
+                                MASK_NONE, stop));
+    }
+    if (n2 > 0) {
+        RFP_TRY(gemm_nt<double>(st, R2, v.t2, X2.t(), n2, nrhs, n2, m1, p1, MASK_NONE, MASK_LOWER,
+                                MASK_NONE, stop));
+        RFP_TRY(gemm_nt<double>(st, R2, v.t2.t(), X2.t(), n2, nrhs, n2, m1, p1, MASK_NONE,
+                                MASK_STRICT_UPPER, MASK_NONE, stop));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_c, const double *Bp,
+                            int64_t ldb, double *Xp, int64_t ldx, int64_t nrhs, int prec,
+                            int max_iter, double tol, const MixedWork &w,
+                            rfp_mixed_status_t *status)
+{
+    double *arf = const_cast<double *>(arf_c);     // read only
+    RfpViews v{block_view(arf, L, L.t1), block_view(arf, L, L.s), block_view(arf, L, L.t2), L.n1,
+               L.n2};
+    const int64_t n = L.n;
+    View<float> W{w.W, 1, w.ldw};
+    View<double> B{const_cast<double *>(Bp), 1, ldb}, X{Xp, 1, ldx}, R{w.R, 1, n};
+    View<float> D{w.D, 1, n};
+
+    RFP_TRY(cudaMemsetAsync(status, 0, sizeof(rfp_mixed_status_t), st));
+    RFP_TRY(cudaMemsetAsync(w.stop, 0, sizeof(int32_t), st));
+    RFP_TRY(cudaMemsetAsync(w.tc_err, 0, sizeof(int32_t), st));
+    stage_begin(st);
+    RFP_TRY(anorm_inf(st, v, n, w.anorm));
+    // 1. W = fl32(A), logical lower triangle
+    RFP_TRY((convert<double, float>(st, v.t1, W, L.n1, L.n1, true, nullptr)));
+    RFP_TRY((convert<double, float>(st, v.s, W.sub(L.n1, 0), L.n2, L.n1, false, nullptr)));
+    RFP_TRY((convert<double, float>(st, v.t2, W.sub(L.n1, L.n1), L.n2, L.n2, true, nullptr)));
+    stage_mark(st, "mixed.convert");
+    // 2. factor
+    int32_t *info = &status->info;
+    if (prec == RFP_PREC_FP32) RFP_TRY(potrf_blocked<float>(st, W, n, info, 0));
+    else RFP_TRY(factor_tc(st, W, n, prec, w, info));
+    RFP_TRY(stop_on_failure(st, status, w.tc_err, w.stop));
+    stage_mark(st, "mixed.factor");
+    // 3. refinement
+    RFP_TRY(fill(st, X, n, nrhs, 0.0));
+    RFP_TRY((convert<double, double>(st, B, R, n, nrhs, false, w.stop)));
+    for (int it = 0; it < max_iter; ++it) {
+        RFP_TRY((convert<double, float>(st, R, D, n, nrhs, false, w.stop)));
+        RFP_TRY(trsm_left_lower_notrans<float>(st, D, nrhs, W, n, w.stop));
+        RFP_TRY(trsm_left_lower_trans<float>(st, D, nrhs, W, n, w.stop));
+        RFP_TRY(add_correction(st, X, D, n, nrhs, w.stop));
+        RFP_TRY(residual(st, v, B, X, R, nrhs, w.stop));
+        RFP_TRY(backward_error(st, R, X, B, n, nrhs, w.anorm, w.berr, tol, status, w.stop));
+    }
+    stage_mark(st, "mixed.refine");
+    return cudaSuccess;
+}
+
+}  // namespace rfp

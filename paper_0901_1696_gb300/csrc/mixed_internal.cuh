@@ -1,0 +1,55 @@
+// Internal declarations of the mixed-precision solve (mixed.cu,
+// mixed_kernels.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "../../include/rfp.h"
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+// The three logical-lower blocks of an FP64 RFP array.
+struct RfpViews {
+    View<double> t1, s, t2;
+    int64_t n1, n2;
+};
+
+template <typename Ts, typename Td>
+cudaError_t convert(cudaStream_t st, View<Ts> src, View<Td> dst, int64_t rows, int64_t cols,
+                    bool tri, const int32_t *stop);
+cudaError_t add_correction(cudaStream_t st, View<double> X, View<float> D, int64_t n, int64_t nrhs,
+                           const int32_t *stop);
+cudaError_t fill(cudaStream_t st, View<double> X, int64_t n, int64_t nrhs, double v);
+cudaError_t anorm_inf(cudaStream_t st, const RfpViews &v, int64_t n, double *out);
+cudaError_t backward_error(cudaStream_t st, View<double> R, View<double> X, View<double> B,
+                           int64_t n, int64_t nrhs, const double *anorm, double *berr_col,
+                           double tol, rfp_mixed_status_t *status, int32_t *stop);
+cudaError_t stop_on_failure(cudaStream_t st, rfp_mixed_status_t *status, const int32_t *tc_err,
+                            int32_t *stop);
+
+// Workspace carve-up of the mixed-precision solve (mixed.cu).
+struct MixedWork {
+    float *W;          // FP32 working matrix / factor, ldw x n column-major (lower used)
+    int64_t ldw;
+    void *P;           // low-precision panel, n x kPanel, K-contiguous
+    double *R;         // FP64 residual, n x nrhs
+    float *D;          // FP32 correction, n x nrhs
+    double *berr;      // per-column backward errors (nrhs)
+    double *anorm;     // ||A||_inf
+    int32_t *stop;     // refinement stop word
+    int32_t *tc_err;   // tensor-core kernel error word
+};
+
+constexpr int64_t kMixedPanel = 512;   // panel width of the tensor-core factorization
+
+size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec);
+bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, MixedWork *w);
+cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf, const double *B,
+                            int64_t ldb, double *X, int64_t ldx, int64_t nrhs, int prec,
+                            int max_iter, double tol, const MixedWork &w,
+                            rfp_mixed_status_t *status);
+
+}  // namespace rfp

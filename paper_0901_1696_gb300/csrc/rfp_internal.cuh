@@ -43,7 +43,21 @@ inline View<T> block_view(T *arf, const Layout &L, const Block &b)
 }
 
 // Operand / output triangle masks used by the tile GEMM.
-enum Mask : int { MASK_NONE = 0, MASK_LOWER = 1, MASK_UPPER = 2 };
+// STRICT variants exclude the diagonal (operands only).
+enum Mask : int { MASK_NONE = 0, MASK_LOWER = 1, MASK_UPPER = 2, MASK_STRICT_LOWER = 3,
+                  MASK_STRICT_UPPER = 4 };
+
+// Does a triangle mask keep operand element (r, c)?
+__host__ __device__ inline bool mask_keeps(int mask, int64_t r, int64_t c)
+{
+    switch (mask) {
+    case MASK_LOWER: return r >= c;
+    case MASK_UPPER: return r <= c;
+    case MASK_STRICT_LOWER: return r > c;
+    case MASK_STRICT_UPPER: return r < c;
+    default: return true;
+    }
+}
 
 // ---- instrumentation (api.cu): launch counter and optional step timing ----
 void note_launch();                                   // one kernel enqueued
@@ -132,6 +146,20 @@ cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows,
 template <typename T>
 cudaError_t pack_copy(cudaStream_t st, const Layout &L, bool lowerA, T *A, int64_t lda, T *arf,
                       bool unpack);
+
+// Blocked triangle building blocks (chol.cu), instantiated for float and
+// double.  V is an m x m lower triangle; `abort` / `info` as for the kernels.
+template <typename T>
+cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info, int64_t base);
+template <typename T>   // X (rows x m) <- X L^{-T}
+cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, View<T> V, int64_t m,
+                                   const int32_t *abort);
+template <typename T>   // L X = B, B m x nrhs
+cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
+                                    const int32_t *abort);
+template <typename T>   // L^T X = B
+cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
+                                  const int32_t *abort);
 
 // Blocked algorithms on the RFP blocks (Sections 3-5).
 template <typename T>

@@ -288,14 +288,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int q = 0; q < 32; ++q) v[q] = 0.f;
             }
             if (!row_ok || (nk > 0 && !have)) continue;
+            // All loads of the chunk are issued before any store (the stores
+            // could alias the loads as far as the compiler knows).
+            float cv[32];
+            float *prow = a.C + i * a.crs + (n0 + c0) * a.ccs;
+            const int64_t jmax = (a.cmode == MASK_LOWER && i < a.N - 1) ? i : a.N - 1;
+            const int cnt = (int)(jmax - (n0 + c0) + 1 < 32 ? jmax - (n0 + c0) + 1 : 32);
+            if (a.beta != 0.f) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
+            }
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                const int64_t j = n0 + c0 + q;
-                if (j >= a.N || (a.cmode == MASK_LOWER && j > i)) continue;
-                float *pc = a.C + i * a.crs + j * a.ccs;
+                if (q >= cnt) continue;
                 float out = a.alpha * v[q];
-                if (a.beta != 0.f) out = fmaf(a.beta, *pc, out);
-                *pc = out;
+                if (a.beta != 0.f) out = fmaf(a.beta, cv[q], out);
+                prow[q * a.ccs] = out;
             }
         }
     }

@@ -66,10 +66,10 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
 
     // K range that can hold non-zero products for this tile.
     int64_t kbeg = 0, kend = g.K;
-    if (g.amask == MASK_LOWER) kend = min(kend, m0 + BM);
-    if (g.amask == MASK_UPPER) kbeg = max(kbeg, m0);
-    if (g.bmask == MASK_LOWER) kend = min(kend, n0 + BN);
-    if (g.bmask == MASK_UPPER) kbeg = max(kbeg, n0);
+    if (g.amask == MASK_LOWER || g.amask == MASK_STRICT_LOWER) kend = min(kend, m0 + BM);
+    if (g.amask == MASK_UPPER || g.amask == MASK_STRICT_UPPER) kbeg = max(kbeg, m0);
+    if (g.bmask == MASK_LOWER || g.bmask == MASK_STRICT_LOWER) kend = min(kend, n0 + BN);
+    if (g.bmask == MASK_UPPER || g.bmask == MASK_STRICT_UPPER) kbeg = max(kbeg, n0);
     const int64_t ntiles = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
 
     const int tid = threadIdx.x, tx = tid % Cfg::TX, ty = tid / Cfg::TX;
@@ -96,9 +96,7 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
             int mm, kk;
             a_coord(q, mm, kk);
             const int64_t gm = m0 + mm, gk = k0 + kk;
-            bool ok = gm < g.M && gk < kend;
-            if (g.amask == MASK_LOWER) ok = ok && gm >= gk;
-            else if (g.amask == MASK_UPPER) ok = ok && gm <= gk;
+            const bool ok = gm < g.M && gk < kend && mask_keeps(g.amask, gm, gk);
             ra[q] = ok ? g.A.p[gm * g.A.rs + gk * g.A.cs] : T(0);
         }
 #pragma unroll
@@ -106,9 +104,7 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
             int nn, kk;
             b_coord(q, nn, kk);
             const int64_t gn = n0 + nn, gk = k0 + kk;
-            bool ok = gn < g.N && gk < kend;
-            if (g.bmask == MASK_LOWER) ok = ok && gn >= gk;
-            else if (g.bmask == MASK_UPPER) ok = ok && gn <= gk;
+            const bool ok = gn < g.N && gk < kend && mask_keeps(g.bmask, gn, gk);
             rb[q] = ok ? g.B.p[gn * g.B.rs + gk * g.B.cs] : T(0);
         }
     };
@@ -149,6 +145,19 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
         }
     }
 
+    // Epilogue: every C load is issued before the first store (stores may
+    // alias the loads as far as the compiler can tell), then C is written.
+    T cin[TM][TN];
+    if (g.beta != T(0)) {
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int64_t i = m0 + ty * TM + r, j = n0 + tx * TN + c;
+                const bool ok = i < g.M && j < g.N && !(g.cmode == MASK_LOWER && j > i);
+                cin[r][c] = ok ? g.C.p[i * g.C.rs + j * g.C.cs] : T(0);
+            }
+    }
 #pragma unroll
     for (int r = 0; r < TM; ++r) {
         const int64_t i = m0 + ty * TM + r;
@@ -158,10 +167,9 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
             const int64_t j = n0 + tx * TN + c;
             if (j >= g.N) continue;
             if (g.cmode == MASK_LOWER && j > i) continue;
-            T *pc = g.C.p + i * g.C.rs + j * g.C.cs;
             T v = g.alpha * acc[r][c];
-            if (g.beta != T(0)) v = fma(g.beta, *pc, v);
-            *pc = v;
+            if (g.beta != T(0)) v = fma(g.beta, cin[r][c], v);
+            g.C.p[i * g.C.rs + j * g.C.cs] = v;
         }
     }
 }

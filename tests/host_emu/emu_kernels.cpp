@@ -18,6 +18,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "../../paper_0901_1696_gb300/csrc/mixed_internal.cuh"
 #include "../../paper_0901_1696_gb300/csrc/rfp_internal.cuh"
 
 namespace {
@@ -47,6 +48,7 @@ struct Launch {
     std::unordered_map<uintptr_t, std::vector<int>> readers;  // addr -> ctas
     std::vector<std::pair<void *, double>> pend_d;
     std::vector<std::pair<void *, float>> pend_f;
+    std::vector<std::pair<void *, uint16_t>> pend_b;
     int cta = 0;
     template <typename T>
     T rd(const T *p)
@@ -76,6 +78,7 @@ struct Launch {
         }
         for (auto &w : pend_d) *(double *)w.first = w.second;
         for (auto &w : pend_f) *(float *)w.first = w.second;
+        for (auto &w : pend_b) *(uint16_t *)w.first = w.second;
         return g_violations ? cudaErrorIllegalAddress : cudaSuccess;
     }
 };
@@ -130,16 +133,16 @@ cudaError_t gemm_nt(cudaStream_t, View<T> C, View<T> A, View<T> B, int64_t M, in
             const int64_t m0 = by * BM, n0 = bx * BN;
             if (cmode == MASK_LOWER && m0 + BM - 1 < n0) continue;
             int64_t kbeg = 0, kend = K;
-            if (amask == MASK_LOWER) kend = std::min(kend, m0 + BM);
-            if (amask == MASK_UPPER) kbeg = std::max(kbeg, m0);
-            if (bmask == MASK_LOWER) kend = std::min(kend, n0 + BN);
-            if (bmask == MASK_UPPER) kbeg = std::max(kbeg, n0);
+            if (amask == MASK_LOWER || amask == MASK_STRICT_LOWER) kend = std::min(kend, m0 + BM);
+            if (amask == MASK_UPPER || amask == MASK_STRICT_UPPER) kbeg = std::max(kbeg, m0);
+            if (bmask == MASK_LOWER || bmask == MASK_STRICT_LOWER) kend = std::min(kend, n0 + BN);
+            if (bmask == MASK_UPPER || bmask == MASK_STRICT_UPPER) kbeg = std::max(kbeg, n0);
             for (int64_t i = m0; i < std::min(M, m0 + BM); ++i)
                 for (int64_t j = n0; j < std::min(N, n0 + BN); ++j) {
                     T acc = T(0);
                     for (int64_t k = kbeg; k < kend; ++k) {
-                        bool aok = amask == MASK_LOWER ? i >= k : amask == MASK_UPPER ? i <= k : true;
-                        bool bok = bmask == MASK_LOWER ? j >= k : bmask == MASK_UPPER ? j <= k : true;
+                        bool aok = mask_keeps(amask, i, k);
+                        bool bok = mask_keeps(bmask, j, k);
                         T a = aok ? L.rd(&A(i, k)) : T(0);
                         T b = bok ? L.rd(&B(j, k)) : T(0);
                         acc += a * b;
@@ -344,6 +347,138 @@ cudaError_t tc_gemm_nt(cudaStream_t, int kind, const void *A, int64_t a_rows, in
     (void)err;
     return L.commit();
 }
+
+// ---- mixed-precision kernels -----------------------------------------------------
+
+static float bf16_round(float x, uint16_t *bits_out)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;                    // round to nearest even
+    *bits_out = (uint16_t)(u >> 16);
+    uint32_t back = (uint32_t)(*bits_out) << 16;
+    float f;
+    memcpy(&f, &back, 4);
+    return f;
+}
+template <typename Td, typename Ts> static void put(Launch &L, Td *p, Ts v) { L.wr(p, (Td)v); }
+static void put(Launch &L, __nv_bfloat16 *p, float v)
+{
+    uint16_t bits;
+    bf16_round(v, &bits);
+    L.wr_any(p, 2);
+    // bf16 stores are applied immediately after the launch's checks
+    static_cast<void>(bits);
+    L.pend_b.push_back({p, bits});
+}
+
+template <typename Ts, typename Td>
+cudaError_t convert(cudaStream_t, View<Ts> src, View<Td> dst, int64_t rows, int64_t cols, bool tri,
+                    const int32_t *stop)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    Launch L;
+    const int T = 32;
+    int cta = 0;
+    for (int64_t r0 = 0; r0 < rows; r0 += T)
+        for (int64_t c0 = 0; c0 < cols; c0 += T, ++cta) {
+            L.cta = cta;
+            if (stop && L.rd(stop)) continue;
+            if (tri && r0 + T - 1 < c0) continue;
+            for (int64_t i = r0; i < std::min(rows, r0 + T); ++i)
+                for (int64_t j = c0; j < std::min(cols, c0 + T); ++j) {
+                    if (tri && i < j) continue;
+                    put(L, &dst(i, j), L.rd(&src(i, j)));
+                }
+        }
+    return L.commit();
+}
+
+cudaError_t add_correction(cudaStream_t, View<double> X, View<float> D, int64_t n, int64_t nrhs,
+                           const int32_t *stop)
+{
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    Launch L;
+    if (L.rd(stop)) return L.commit();
+    for (int64_t j = 0; j < nrhs; ++j)
+        for (int64_t i = 0; i < n; ++i) L.wr(&X(i, j), L.rd(&X(i, j)) + (double)L.rd(&D(i, j)));
+    return L.commit();
+}
+
+cudaError_t fill(cudaStream_t, View<double> X, int64_t n, int64_t nrhs, double v)
+{
+    Launch L;
+    for (int64_t j = 0; j < nrhs; ++j)
+        for (int64_t i = 0; i < n; ++i) L.wr(&X(i, j), v);
+    return L.commit();
+}
+
+cudaError_t anorm_inf(cudaStream_t, const RfpViews &v, int64_t n, double *out)
+{
+    Launch L;
+    auto lower = [&](int64_t i, int64_t j) {
+        if (j >= v.n1) return L.rd(&v.t2(i - v.n1, j - v.n1));
+        if (i >= v.n1) return L.rd(&v.s(i - v.n1, j));
+        return L.rd(&v.t1(i, j));
+    };
+    double m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0;
+        for (int64_t j = 0; j <= i; ++j) s += std::fabs(lower(i, j));
+        for (int64_t k = i + 1; k < n; ++k) s += std::fabs(lower(k, i));
+        m = std::max(m, s);
+    }
+    L.wr(out, m);
+    return L.commit();
+}
+
+cudaError_t backward_error(cudaStream_t, View<double> R, View<double> X, View<double> B, int64_t n,
+                           int64_t nrhs, const double *anorm, double *berr_col, double tol,
+                           rfp_mixed_status_t *status, int32_t *stop)
+{
+    Launch L;
+    if (L.rd(stop)) return L.commit();
+    double m = 0;
+    for (int64_t j = 0; j < nrhs; ++j) {
+        double r = 0, x = 0, b = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            r = std::max(r, std::fabs(L.rd(&R(i, j))));
+            x = std::max(x, std::fabs(L.rd(&X(i, j))));
+            b = std::max(b, std::fabs(L.rd(&B(i, j))));
+        }
+        const double den = L.rd(anorm) * x + b, e = den > 0 ? r / den : r;
+        L.wr(&berr_col[j], e);
+        m = std::max(m, e);
+    }
+    L.wr(&status->backward_error, m);
+    L.wr_any(&status->iterations, 4);
+    const int32_t iters = L.rd(&status->iterations) + 1;
+    cudaError_t e = L.commit();
+    status->iterations = iters;
+    if (m <= tol) { status->converged = 1; *stop = 1; }
+    return e;
+}
+
+cudaError_t stop_on_failure(cudaStream_t, rfp_mixed_status_t *status, const int32_t *tc_err,
+                            int32_t *stop)
+{
+    Launch L;
+    const int32_t te = L.rd(tc_err), info = L.rd(&status->info);
+    cudaError_t e = L.commit();
+    status->tc_error = te;
+    if (info != 0 || te != 0) *stop = 1;
+    return e;
+}
+
+template cudaError_t convert<double, float>(cudaStream_t, View<double>, View<float>, int64_t, int64_t,
+                                            bool, const int32_t *);
+template cudaError_t convert<double, double>(cudaStream_t, View<double>, View<double>, int64_t,
+                                             int64_t, bool, const int32_t *);
+template cudaError_t convert<float, float>(cudaStream_t, View<float>, View<float>, int64_t, int64_t,
+                                           bool, const int32_t *);
+template cudaError_t convert<float, __nv_bfloat16>(cudaStream_t, View<float>, View<__nv_bfloat16>,
+                                                   int64_t, int64_t, bool, const int32_t *);
 
 #define EMU_INST(T)                                                                                  \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \

@@ -1,0 +1,91 @@
+"""GPU tests of the mixed-precision solve (rfp_dpfsv_mixed) through the C ABI.
+
+The target: a normwise backward error max_j ||b_j - A x_j||_inf /
+(||A||_inf ||x_j||_inf + ||b_j||_inf) <= 1e-14, checked both by the device's
+own figure and independently by the oracle's compensated residual, and a
+solution within the forward-error bound kappa * 1e-14 of the oracle's FP64
+solve.  Refinement from a factor of unit roundoff u_f converges when
+kappa * u_f < 1: FP32 up to kappa = 1e6, TF32 and BF16 only for small
+kappa; where it cannot converge the status must say so (converged = 0 or a
+reported factorization failure), never claim convergence.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import rfp_inputs as gen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+rfp = pytest.importorskip("paper_0901_1696_gb300.binding")
+
+PRECS = {"fp32": 2, "tf32": 1, "bf16": 0}
+
+
+def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
+    n, nrhs = B.shape
+    arf = torch.from_numpy(oracle.pack(transr, uplo, A)).cuda()
+    arf0 = arf.clone()
+    dB = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()          # column-major
+    ldx = n + 1
+    dX = torch.full((nrhs, ldx), np.nan, dtype=torch.float64, device="cuda")
+    wb = rfp.rfp_dpfsv_mixed_workspace(n, nrhs, prec)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    status = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    rfp.rfp_dpfsv_mixed(transr, uplo, n, nrhs, arf, dB, n, dX, ldx, prec, max_iter, tol, work, wb,
+                        status)
+    st = rfp.mixed_status(status.cpu().numpy().tobytes())
+    X = np.asfortranarray(dX.cpu().numpy()[:, :n].T)
+    assert torch.equal(arf, arf0), "A must not be modified"
+    return X, st
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("transr,uplo,n", [("N", "L", 100), ("T", "U", 513), ("N", "U", 1300),
+                                           ("T", "L", 2100)])
+def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
+    A, rng = gen.spd_bbt(n, seed=n, return_rng=True)
+    B = gen.rhs(n, 16, rng)
+    X, st = solve_mixed(transr, uplo, A, B, PRECS[prec])
+    assert st["info"] == 0 and st["tc_error"] == 0
+    assert st["converged"] == 1, st
+    assert st["backward_error"] <= 1e-15
+    assert oracle.solve_backward_error(A, X, B) <= 1e-14
+    ref = oracle.pftrs(transr, uplo, n, oracle.pftrf(transr, uplo, n, oracle.pack(transr, uplo, A))[0], B)
+    assert np.max(np.abs(X - ref)) <= 10 * 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_mixed_conditioning(prec, kappa):
+    n = 1200
+    A = gen.spd_spectrum(n, seed=7, kappa=kappa)
+    B = gen.rhs(n, 8, seed=8)
+    X, st = solve_mixed("N", "L", A, B, PRECS[prec], max_iter=40)
+    assert st["tc_error"] == 0
+    bwd = oracle.solve_backward_error(A, X, B) if st["info"] == 0 else np.inf
+    u_f = {"fp32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
+    if st["converged"]:
+        assert st["backward_error"] <= 1e-15 and bwd <= 1e-14, (st, bwd)
+    if kappa * u_f * 100 < 1:         # well inside the convergence condition
+        assert st["info"] == 0 and st["converged"] == 1, st
+
+
+def test_mixed_argument_checks():
+    n, nrhs = 64, 2
+    arf = torch.zeros(n * (n + 1) // 2, dtype=torch.float64, device="cuda")
+    B = torch.zeros(nrhs, n, dtype=torch.float64, device="cuda")
+    X = torch.zeros_like(B)
+    wb = rfp.rfp_dpfsv_mixed_workspace(n, nrhs, 2)
+    work = torch.empty(wb + 512, dtype=torch.uint8, device="cuda")
+    status = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    bad = [((n, nrhs, arf, B, n, X, n, 7, 5, 1e-14, work, wb), -10),
+           ((n, nrhs, arf, B, n - 1, X, n, 2, 5, 1e-14, work, wb), -7),
+           ((n, nrhs, arf, B, n, X, n, 2, 5, 1e-14, work, wb - 8), -14),
+           ((n, nrhs, arf, B, n, X, n, 2, 5, 1e-14, work.data_ptr() + 8, wb), -13),
+           ((n, nrhs, arf, B, n, X, n, 2, -1, 1e-14, work, wb), -11)]
+    for args, code in bad:
+        with pytest.raises(rfp.RfpError) as e:
+            rfp.rfp_dpfsv_mixed("N", "L", *args, status)
+        assert e.value.status == code
+    assert rfp.rfp_dpfsv_mixed_workspace(n, nrhs, 9) == 0

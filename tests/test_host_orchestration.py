@@ -32,7 +32,8 @@ CSRC = os.path.join(ROOT, "paper_0901_1696_gb300", "csrc")
 def emu_lib(tmp_path_factory):
     so = str(tmp_path_factory.mktemp("emu") / "librfp_emu.so")
     cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-I", EMU_DIR, "-x", "c++",
-           os.path.join(CSRC, "chol.cu"), os.path.join(CSRC, "api.cu"), "-x", "none",
+           os.path.join(CSRC, "chol.cu"), os.path.join(CSRC, "api.cu"),
+           os.path.join(CSRC, "mixed.cu"), "-x", "none",
            os.path.join(EMU_DIR, "emu_kernels.cpp"), "-o", so]
     subprocess.run(cmd, check=True)
     lib = Library(so)
@@ -214,3 +215,41 @@ def test_argument_checks(emu):
     assert emu.rfp_dpftrs("N", "L", 0, 5, 0, 0, 1, 0) == 0
     assert emu.rfp_dpftrs("N", "L", 4, 0, 0, 0, 4, 0) == 0
     assert emu.rfp_dpack("N", "L", 0, 0, 1, 0, 0) == 0
+
+
+def _aligned_bytes(nbytes, align=256):
+    raw = np.zeros(nbytes + align, dtype=np.uint8)
+    off = (-raw.ctypes.data) % align
+    return raw[off:off + nbytes]
+
+
+@pytest.mark.parametrize("prec", [2, 1, 0], ids=["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("transr,uplo,n", [("N", "L", 5), ("T", "U", 70), ("N", "U", 600),
+                                           ("T", "L", 600)])
+def test_emulated_mixed_precision_solve(emu_lib, prec, transr, uplo, n):
+    """The refinement loop's launch sequence, in bounds and race-free, reaches
+    an FP64-accurate solution (n = 600 runs one 512-wide panel and one
+    tensor-core SYRK update)."""
+    from paper_0901_1696_gb300.binding import mixed_status
+    emu = emu_lib
+    emu.lib.emu_set_sms(152)
+    if n == 600 and prec == 2 and transr == "T":
+        pytest.skip("the FP32 path has no panel split; one 600 case is enough")
+    A, rng = gen.spd_bbt(n, seed=n, return_rng=True)
+    nrhs = 3
+    B = gen.rhs(n, nrhs, rng)
+    arf = oracle.pack(transr, uplo, A)
+    X = np.zeros((n + 2, nrhs), order="F")
+    wbytes = emu.rfp_dpfsv_mixed_workspace(n, nrhs, prec)
+    work = _aligned_bytes(wbytes)
+    status = _aligned_bytes(24, 8)
+    Bc = np.asfortranarray(B)
+    _register(emu, arf, Bc, X, work, status)
+    emu.rfp_dpfsv_mixed(transr, uplo, n, nrhs, arf, Bc, n, X, n + 2, prec, 10, 1e-15, work,
+                        wbytes, status, 0)
+    _ok(emu)
+    st = mixed_status(status.tobytes())
+    assert st["info"] == 0 and st["tc_error"] == 0
+    assert st["converged"] == 1 and 1 <= st["iterations"] <= 6, st
+    assert oracle.solve_backward_error(A, X[:n], B) <= 1e-15
+    np.testing.assert_array_equal(arf, oracle.pack(transr, uplo, A))   # A untouched
