@@ -183,6 +183,31 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
                     double tol, void *work, size_t work_bytes, rfp_mixed_status_t *status,
                     void *stream);
 
+/*
+ * rfp_dpfsv_mixed_noalloc: rfp_dpfsv_mixed for callers that cannot allocate
+ * device memory (code running inside a memory pool it does not own, plugins
+ * whose host application forbids device allocations after start-up, loops
+ * that must not block or fail on an allocation).  The paper has no
+ * counterpart; this is an interface variant of rfp_dpfsv_mixed.
+ * The workspace is a fixed 32 MiB array inside the library (every GPU that
+ * loads the library holds it until the process exits); nothing is allocated.
+ * Same arguments and results as rfp_dpfsv_mixed without work / work_bytes:
+ * 1 transr, 2 uplo, 3 n, 4 nrhs, 5 arf, 6 B, 7 ldb, 8 X, 9 ldx, 10 prec,
+ * 11 max_iter, 12 tol, 13 status, 14 stream.  Problems whose
+ * rfp_dpfsv_mixed_workspace exceeds rfp_dpfsv_mixed_noalloc_capacity() are
+ * rejected: -3 if n does not fit even with nrhs = 1, else -4 (for example
+ * n = 2048 with nrhs <= 256 fits in every precision).
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it; serialize them.  The array keeps
+ * the previous call's contents; the solve itself clears what must start at
+ * zero.  The first call on each device looks up the array's device address
+ * (set-up, once per device); make it before any stream capture.
+ */
+size_t rfp_dpfsv_mixed_noalloc_capacity(void);
+int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
+                            const double *B, int64_t ldb, double *X, int64_t ldx, int prec,
+                            int max_iter, double tol, rfp_mixed_status_t *status, void *stream);
+
 /* Text for a return code of this library (static storage, never NULL). */
 const char *rfp_status_string(int status);
 

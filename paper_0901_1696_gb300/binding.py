@@ -196,6 +196,21 @@ class Library:
                                       _addr(status), _stream(stream))
         return self._check("rfp_dpfsv_mixed", rc)
 
+    def rfp_dpfsv_mixed_noalloc_capacity(self) -> int:
+        f = self.lib.rfp_dpfsv_mixed_noalloc_capacity
+        f.argtypes, f.restype = [], ctypes.c_size_t
+        return int(f())
+
+    def rfp_dpfsv_mixed_noalloc(self, transr, uplo, n, nrhs, arf, B, ldb, X, ldx, prec, max_iter,
+                                tol, status, stream=None):
+        f = self.lib.rfp_dpfsv_mixed_noalloc
+        f.argtypes = [_c, _c, _i64, _i64, _p, _p, _i64, _p, _i64, ctypes.c_int, ctypes.c_int,
+                      ctypes.c_double, _p, _p]
+        f.restype = ctypes.c_int
+        rc = f(_ch(transr), _ch(uplo), n, nrhs, _addr(arf), _addr(B), ldb, _addr(X), ldx, prec,
+               max_iter, tol, _addr(status), _stream(stream))
+        return self._check("rfp_dpfsv_mixed_noalloc", rc)
+
     def rfp_ssyrk_tc(self, uplo, n, k, alpha, A, lda, prec, beta, C, ldc, d_err, stream=None):
         rc = self.lib.rfp_ssyrk_tc(_ch(uplo), n, k, alpha, _addr(A), lda, prec, beta, _addr(C), ldc,
                                    _addr(d_err), _stream(stream))
@@ -239,3 +254,5 @@ rfp_dpftrs, rfp_spftrs = _fwd("rfp_dpftrs"), _fwd("rfp_spftrs")
 rfp_dpftri, rfp_spftri = _fwd("rfp_dpftri"), _fwd("rfp_spftri")
 rfp_ssyrk_tc = _fwd("rfp_ssyrk_tc")
 rfp_dpfsv_mixed, rfp_dpfsv_mixed_workspace = _fwd("rfp_dpfsv_mixed"), _fwd("rfp_dpfsv_mixed_workspace")
+rfp_dpfsv_mixed_noalloc = _fwd("rfp_dpfsv_mixed_noalloc")
+rfp_dpfsv_mixed_noalloc_capacity = _fwd("rfp_dpfsv_mixed_noalloc_capacity")
