@@ -57,6 +57,13 @@ def parse():
                         "reference step)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--mode", choices=["fp64", "mixed"], default="fp64",
+                   help="fp64: the FP64 hot path (default line); mixed: the mixed-precision "
+                        "solve at n = 32768 against the FP64 path (its own line)")
+    p.add_argument("--mixed-n", type=int, default=32768)
+    p.add_argument("--mixed-nrhs", type=int, default=64)
+    p.add_argument("--kappas", default="1e2,1e4,1e6")
+    p.add_argument("--precs", default="fp32,tf32,bf16")
     return p.parse_args()
 
 
@@ -356,8 +363,103 @@ def e2e_leg(args, lib, A, B0, dev, stream):
             "d2h_bytes_per_step": n * nrhs * 8, "ms_per_step": ms}
 
 
+def run_mixed(args):
+    """Mixed-precision solve (low-precision factor + FP64 refinement) of an
+    n = 32768 FP64 RFPF system with nrhs = 64, for each condition number and
+    precision, against FP64 PFTRF + PFTRS on the same GPU.  Errors: the
+    device's backward error, the oracle's compensated backward error on 4
+    sampled columns, and the max-norm distance to the FP64 solution."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import rfp_inputs as gen
+    from paper_0901_1696_gb300 import binding as rfp
+    from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    stream = torch.cuda.current_stream(dev)
+    n, nrhs = args.mixed_n, args.mixed_nrhs
+    precs = {"fp32": rfp.RFP_PREC_FP32, "tf32": rfp.RFP_PREC_TF32, "bf16": rfp.RFP_PREC_BF16}
+    results, fp64 = [], []
+    Bh = gen.rhs(n, nrhs, seed=3)
+    dB = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev)
+    X = torch.empty_like(dB)
+    status = torch.zeros(24, dtype=torch.uint8, device=dev)
+    sample = [0, nrhs // 3, 2 * nrhs // 3, nrhs - 1]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for kappa in [float(k) for k in args.kappas.split(",")]:
+        A = gen.spd_butterfly(n, seed=0, kappa=kappa, device=dev) if n & (n - 1) == 0 else \
+            gen.spd_spectrum(n, seed=0, kappa=kappa, device=dev)
+        arf = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
+        lib.rfp_dpack("N", "L", n, A, n, arf, stream)
+        Ah = A.cpu().numpy()
+        del A
+        # FP64 reference path on a copy
+        fac = arf.clone()
+        X64 = dB.clone()
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        lib.rfp_dpftrf("N", "L", n, fac, info, stream)
+        lib.rfp_dpftrs("N", "L", n, nrhs, fac, X64, n, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = ev[0].elapsed_time(ev[1])
+        X64h = X64.cpu().numpy().T
+        fp64.append({"kappa": kappa, "ms": ms64, "info": int(info.item()),
+                     "tflops": (pftrf_flops(n) + pftrs_flops(n, nrhs)) / (ms64 * 1e-3) / 1e12,
+                     "oracle_bwd_sampled": oracle.solve_backward_error(Ah, X64h[:, sample],
+                                                                       Bh[:, sample])})
+        del fac, X64
+        for name in args.precs.split(","):
+            prec = precs[name]
+            wb = lib.rfp_dpfsv_mixed_workspace(n, nrhs, prec)
+            work = torch.empty(wb, dtype=torch.uint8, device=dev)
+            for rep in range(2):            # first call warms up, second is timed
+                torch.cuda.synchronize(dev)
+                lib.rfp_stage_timing(True)
+                ev[0].record(stream)
+                lib.rfp_dpfsv_mixed("N", "L", n, nrhs, arf, dB, n, X, n, prec, 30, 1e-15, work,
+                                    wb, status, stream)
+                ev[1].record(stream)
+                torch.cuda.synchronize(dev)
+                stages = dict(lib.rfp_stage_times())
+                lib.rfp_stage_timing(False)
+            ms = ev[0].elapsed_time(ev[1])
+            st = rfp.mixed_status(status.cpu().numpy().tobytes())
+            Xh = X.cpu().numpy().T
+            fwd = float(np.max(np.abs(Xh - X64h)) / np.max(np.abs(X64h)))
+            results.append({
+                "kappa": kappa, "prec": name, "ms": ms, "speedup_vs_fp64": ms64 / ms,
+                "steps_ms": {k.split(".")[1]: v for k, v in stages.items()},
+                "iterations": st["iterations"], "converged": st["converged"],
+                "info": st["info"], "tc_error": st["tc_error"],
+                "backward_error": st["backward_error"],
+                "oracle_bwd_sampled": oracle.solve_backward_error(Ah, Xh[:, sample], Bh[:, sample])
+                if st["info"] == 0 else None,
+                "fwd_vs_fp64": fwd,
+                "factor_tflops": pftrf_flops(n) / (stages.get("mixed.factor", 0) * 1e-3) / 1e12
+                if stages.get("mixed.factor") else None})
+            del work
+        del arf, Ah
+        torch.cuda.empty_cache()
+    line = {"mode": "mixed", "metric": "mixed-precision RFPF solve: time and backward error "
+                                        "vs FP64 PFTRF+PFTRS",
+            "unit": "ms", "higher_is_better": False, "n": n, "nrhs": nrhs, "dtype": "f64 in/out",
+            "data": "synthetic: A = Q diag(lam) Q^T, Q random butterfly (n power of two) else "
+                    "Haar, lam log-uniform on [1, kappa] with endpoints pinned",
+            "tol": 1e-15, "fp64": fp64, "results": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "mixed":
+        run_mixed(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
     if args.impl == "reference":

@@ -15,6 +15,12 @@ benchmark configurations describe):
   lam_n = kappa and the others 10^U(0, log10 kappa): the 2-norm condition
   number is exactly kappa.  For n > 4096 the same recipe runs on a CUDA device
   with torch in FP64 (device RNG) when one is present.
+* ``spd_butterfly(n, seed, kappa, device)``: A = Q diag(lam) Q^T with the
+  same spectrum recipe and Q a random butterfly transform: log2(n) levels of
+  Givens rotations with i.i.d. uniform angles pairing i and i + 2^l, so every
+  eigenvector is spread over all coordinates (n must be a power of two).
+  O(n^2 log n) work: the stand-in for a Haar Q at n = 32768, where the QR of
+  a Gaussian matrix would cost ~1e14 FP64 flops.
 * ``spd_integer_factor(n, seed)``: A = L0 L0^T with L0 unit lower triangular
   with small integer entries; the exact Cholesky factor is L0.
 * ``pascal(n)``: P_ij = C(i+j, i); its Cholesky factor is L_ij = C(i, j).
@@ -84,6 +90,40 @@ def spd_spectrum(n: int, seed: int = 0, kappa: float = 1e4, device=None):
     lam = spectrum(n, kappa, rng)
     A = (Q * lam[None, :]) @ Q.T
     return np.asfortranarray(0.5 * (A + A.T))
+
+
+def spd_butterfly(n: int, seed: int = 0, kappa: float = 1e4, device=None):
+    """A = Q diag(lam) Q^T, Q a random butterfly transform (torch FP64 on
+    ``device``, returned as a torch tensor; symmetric, so row- and
+    column-major storage agree)."""
+    import torch
+    if n & (n - 1):
+        raise ValueError("the butterfly generator needs n a power of two")
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = torch.rand(n, dtype=torch.float64, device=device, generator=g)
+    lam = 10.0 ** (u * np.log10(kappa))
+    lam[0], lam[-1] = 1.0, float(kappa)
+    A = torch.diag(lam)
+    h = 1
+    while h < n:
+        theta = 2 * np.pi * torch.rand(n // 2, dtype=torch.float64, device=device, generator=g)
+        c, s = torch.cos(theta), torch.sin(theta)
+        # rotation on coordinate pairs (i, i + h) inside blocks of 2h: A <- G A G^T
+        for dim in (0, 1):
+            V = A.view(n // (2 * h), 2, h, n) if dim == 0 else A.view(n, n // (2 * h), 2, h)
+            if dim == 0:
+                x, y = V[:, 0].clone(), V[:, 1]
+                cc, ss = c.view(n // (2 * h), h, 1), s.view(n // (2 * h), h, 1)
+                V[:, 0] = cc * x - ss * y
+                V[:, 1] = ss * x + cc * y
+            else:
+                x, y = V[:, :, 0].clone(), V[:, :, 1]
+                cc, ss = c.view(1, n // (2 * h), h), s.view(1, n // (2 * h), h)
+                V[:, :, 0] = cc * x - ss * y
+                V[:, :, 1] = ss * x + cc * y
+        h *= 2
+    return 0.5 * (A + A.T)
 
 
 def spd_integer_factor(n: int, seed: int = 0, lo: int = -2, hi: int = 2):
