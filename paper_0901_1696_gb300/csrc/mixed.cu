@@ -78,10 +78,10 @@ static cudaError_t factor_tc(cudaStream_t st, View<float> W, int64_t n, int prec
 {
     for (int64_t j0 = 0; j0 < n; j0 += kMixedPanel) {
         const int64_t j1 = std::min(j0 + kMixedPanel, n), nb = j1 - j0;
-        RFP_TRY(potrf_blocked<float>(st, W.sub(j0, j0), nb, info, j0));
+        RFP_TRY(potrf_rec<float>(st, W.sub(j0, j0), nb, info, j0));
         if (j1 >= n) break;
         const int64_t m = n - j1;
-        RFP_TRY(trsm_right_lower_trans<float>(st, W.sub(j1, j0), m, W.sub(j0, j0), nb, info));
+        RFP_TRY(trsm_right_lower_trans_rec<float>(st, W.sub(j1, j0), m, W.sub(j0, j0), nb, info));
         // panel -> K-contiguous low-precision copy P (row r, column k at P[r*512 + k])
         if (prec == RFP_PREC_BF16) {
             View<__nv_bfloat16> P{static_cast<__nv_bfloat16 *>(w.P), kMixedPanel, 1};
@@ -152,22 +152,24 @@ cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_
     stage_mark(st, "mixed.convert");
     // 2. factor
     int32_t *info = &status->info;
-    if (prec == RFP_PREC_FP32) RFP_TRY(potrf_blocked<float>(st, W, n, info, 0));
+    if (prec == RFP_PREC_FP32) RFP_TRY(potrf_rec<float>(st, W, n, info, 0));
     else RFP_TRY(factor_tc(st, W, n, prec, w, info));
     RFP_TRY(stop_on_failure(st, status, w.tc_err, w.stop));
     stage_mark(st, "mixed.factor");
-    // 3. refinement
+    // 3. refinement (step marks: "mixed.solve", "mixed.residual" per iteration)
     RFP_TRY(fill(st, X, n, nrhs, 0.0));
     RFP_TRY((convert<double, double>(st, B, R, n, nrhs, false, w.stop)));
+    stage_mark(st, "mixed.setup");
     for (int it = 0; it < max_iter; ++it) {
         RFP_TRY((convert<double, float>(st, R, D, n, nrhs, false, w.stop)));
-        RFP_TRY(trsm_left_lower_notrans<float>(st, D, nrhs, W, n, w.stop));
-        RFP_TRY(trsm_left_lower_trans<float>(st, D, nrhs, W, n, w.stop));
+        RFP_TRY(trsm_left_lower_notrans_rec<float>(st, D, nrhs, W, n, w.stop));
+        RFP_TRY(trsm_left_lower_trans_rec<float>(st, D, nrhs, W, n, w.stop));
         RFP_TRY(add_correction(st, X, D, n, nrhs, w.stop));
+        stage_mark(st, "mixed.solve");
         RFP_TRY(residual(st, v, B, X, R, nrhs, w.stop));
         RFP_TRY(backward_error(st, R, X, B, n, nrhs, w.anorm, w.berr, tol, status, w.stop));
+        stage_mark(st, "mixed.residual");
     }
-    stage_mark(st, "mixed.refine");
     return cudaSuccess;
 }
 

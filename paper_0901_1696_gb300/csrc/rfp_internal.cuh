@@ -161,6 +161,20 @@ template <typename T>   // L^T X = B
 cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
                                   const int32_t *abort);
 
+// Recursive forms (split at a multiple of 64 near m/2, one long-K product per
+// level); same contracts as the blocked forms above.
+template <typename T>
+cudaError_t potrf_rec(cudaStream_t st, View<T> V, int64_t m, int32_t *info, int64_t base);
+template <typename T>
+cudaError_t trsm_right_lower_trans_rec(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
+                                       int64_t m, const int32_t *abort);
+template <typename T>
+cudaError_t trsm_left_lower_notrans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
+                                        int64_t m, const int32_t *abort);
+template <typename T>
+cudaError_t trsm_left_lower_trans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
+                                      int64_t m, const int32_t *abort);
+
 // Blocked algorithms on the RFP blocks (Sections 3-5).
 template <typename T>
 cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info);
