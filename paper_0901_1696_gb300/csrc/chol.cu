@@ -5,7 +5,6 @@
 // caller's array).  The full-format LAPACK / Level-3 BLAS calls of Fig. 4
 // are replaced by tiled kernels with 64-wide diagonal tiles:
 //   PFTRF: POTRF(T1); S <- S L11^{-T}; T2 <- T2 - S S^T; POTRF(T2)
-//          (the POTRFs and the TRSM themselves split recursively, below)
 //   PFTRS: L11 Y1 = B1; B2 -= L21 Y1; L22 Y2 = B2;
 //          L22^T X2 = Y2; Y1 -= L21^T X2; L11^T X1 = Y1
 //   PFTRI: W21 = -L22^{-1} L21 L11^{-1}; T1 <- W11^T W11 + W21^T W21;
@@ -117,8 +116,12 @@ cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View
 //
 // Splitting a triangle at m1 (a multiple of 64 near m/2) turns each routine
 // into two half-size calls plus one GEMM / SYRK whose K is m1: half of all the
-// flops run in the top-level product with long K and a full grid, instead of
-// n/64 products with K = 64.  Base case: one 64-wide diagonal tile.
+// flops run in the top-level product with long K, instead of n/64 products
+// with K = 64.  That pays where the K = 64 updates are bound by their C
+// traffic (the FP32 factorization of the mixed-precision solve); the FP64
+// routines keep the blocked forms, whose every update fills the GPU (the
+// deep levels of the recursion launch too few CTAs for the FP64 pipe).
+// Base case: one 64-wide diagonal tile.
 
 static int64_t split_point(int64_t m) { return std::max<int64_t>(kNb, (m / 2 + kNb - 1) / kNb * kNb); }
 
@@ -231,11 +234,11 @@ cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     stage_begin(st);
     RFP_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
     // step 1: L11 L11^T = A11
-    RFP_TRY(potrf_rec(st, t1, L.n1, info, 0));
+    RFP_TRY(potrf_blocked(st, t1, L.n1, info, 0));
     stage_mark(st, "pftrf.potrf_t1");
     if (L.n2 > 0 && L.n1 > 0) {
         // step 2: L21 L11^T = A21
-        RFP_TRY(trsm_right_lower_trans_rec(st, s, L.n2, t1, L.n1, info));
+        RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
         stage_mark(st, "pftrf.trsm_s");
         // step 3: A22 <- A22 - L21 L21^T (lower triangle of T2)
         RFP_TRY(gemm_nt(st, t2, s, s, L.n2, L.n2, L.n1, T(-1), T(1), MASK_LOWER, MASK_NONE,
@@ -243,7 +246,7 @@ cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
         stage_mark(st, "pftrf.syrk_t2");
     }
     // step 4: L22 L22^T = A22
-    RFP_TRY(potrf_rec(st, t2, L.n2, info, L.n1));
+    RFP_TRY(potrf_blocked(st, t2, L.n2, info, L.n1));
     stage_mark(st, "pftrf.potrf_t2");
     return cudaSuccess;
 }
@@ -258,16 +261,16 @@ cudaError_t pftrs_impl(cudaStream_t st, const Layout &L, const T *arf_c, T *Bp, 
     View<T> B1 = B, B2 = B.sub(L.n1, 0);
     stage_begin(st);
     // L Y = B
-    RFP_TRY(trsm_left_lower_notrans_rec(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
+    RFP_TRY(trsm_left_lower_notrans(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
     RFP_TRY(gemm_nt(st, B2, s, B1.t(), L.n2, nrhs, L.n1, T(-1), T(1), MASK_NONE, MASK_NONE,
                     MASK_NONE, (const int32_t *)nullptr));
-    RFP_TRY(trsm_left_lower_notrans_rec(st, B2, nrhs, t2, L.n2, (const int32_t *)nullptr));
+    RFP_TRY(trsm_left_lower_notrans(st, B2, nrhs, t2, L.n2, (const int32_t *)nullptr));
     stage_mark(st, "pftrs.forward");
     // L^T X = Y
-    RFP_TRY(trsm_left_lower_trans_rec(st, B2, nrhs, t2, L.n2, (const int32_t *)nullptr));
+    RFP_TRY(trsm_left_lower_trans(st, B2, nrhs, t2, L.n2, (const int32_t *)nullptr));
     RFP_TRY(gemm_nt(st, B1, s.t(), B2.t(), L.n1, nrhs, L.n2, T(-1), T(1), MASK_NONE, MASK_NONE,
                     MASK_NONE, (const int32_t *)nullptr));
-    RFP_TRY(trsm_left_lower_trans_rec(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
+    RFP_TRY(trsm_left_lower_trans(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
     stage_mark(st, "pftrs.backward");
     return cudaSuccess;
 }
@@ -281,7 +284,7 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     if (L.n1 > 0 && L.n2 > 0) {
         // W21 = -L22^{-1} L21 L11^{-1}: two in-place solves with the factor
         RFP_TRY(trsm_right_lower_notrans(st, s, L.n2, t1, L.n1, T(-1), info));
-        RFP_TRY(trsm_left_lower_notrans_rec(st, s, L.n1, t2, L.n2, info));
+        RFP_TRY(trsm_left_lower_notrans(st, s, L.n1, t2, L.n2, info));
     }
     stage_mark(st, "pftri.w21");
     // T1 <- W11^T W11 + W21^T W21
@@ -294,7 +297,7 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
                         MASK_NONE, MASK_NONE, info));
         stage_mark(st, "pftri.syrk_t1");
         // S <- W22^T W21 = L22^{-T} W21 (T2 still holds L22)
-        RFP_TRY(trsm_left_lower_trans_rec(st, s, L.n1, t2, L.n2, info));
+        RFP_TRY(trsm_left_lower_trans(st, s, L.n1, t2, L.n2, info));
         stage_mark(st, "pftri.trmm_s");
     }
     // T2 <- W22^T W22

@@ -66,18 +66,19 @@ void stage_mark(cudaStream_t st, const char *name);   // end of one of its steps
 
 // ---- launchers (all enqueue on `st`, return cudaSuccess or the launch error)
 
-// Tile shape of one gemm_nt launch.  The large tile (64 x 64 FP64, 128 x 128
-// FP32, 256 threads) is used unless the launch would put fewer than two CTAs
-// on each SM, in which case the small tile (32 x 32 FP64 with 64 threads,
-// 64 x 64 FP32 with 256 threads) quadruples the CTA count.  In-place calls
-// (A or B aliasing C) always take the large tile, whose width covers the
-// 64-wide diagonal blocks the in-place products work on.
+// Tile shape of one gemm_nt launch: the large tile (64 x 64 FP64, 128 x 128
+// FP32) or the small one (32 x 32 FP64, 64 x 64 FP32), whichever has the
+// smaller estimated time: waves x (CTAs per SM) x (tile area), the CTAs of a
+// wave sharing their SM's pipes and each doing work proportional to its tile
+// area.  The small tile must win by 5%.  In-place calls (A or B aliasing C) always take
+// the large tile, whose width covers the 64-wide diagonal blocks the
+// in-place products work on.
 struct GemmTileChoice {
     int bm, bn;
     bool small;
 };
 inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, bool inplace,
-                                       int elem_size, int num_sms)
+                                       int elem_size, int num_sms, int occ_big, int occ_small)
 {
     const int big = elem_size == 8 ? 64 : 128, sml = elem_size == 8 ? 32 : 64;
     auto ctas = [&](int64_t t) {
@@ -90,10 +91,19 @@ inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, bool inp
         }
         return c;
     };
-    if (!inplace && ctas(big) < 2 * (int64_t)num_sms) return {sml, sml, true};
+    auto est = [&](int64_t c, int occ, int t) {
+        occ = occ > 0 ? occ : 1;
+        const int64_t slots = (int64_t)num_sms * occ;
+        return (double)((c + slots - 1) / slots) * occ * (double)t * t;
+    };
+    if (!inplace && est(ctas(sml), occ_small, sml) < 0.95 * est(ctas(big), occ_big, big))
+        return {sml, sml, true};
     return {big, big, false};
 }
 int device_sm_count();   // SMs of the current device (cached per device)
+// Resident CTAs per SM of the large / small gemm_nt configuration for
+// element size elem_size (cached per device).
+void gemm_occupancy(int elem_size, int *occ_big, int *occ_small);
 
 // C(M x N) = alpha * A(M x K) * B(N x K)^T + beta * C.  cmode MASK_LOWER
 // writes only i >= j.  amask / bmask treat an operand as triangular (entries

@@ -189,12 +189,40 @@ cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M,
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 && beta == T(1)) return cudaSuccess;
     GemmArgs<T> g{C, A, B, M, N, K, alpha, beta, cmode, amask, bmask, abort};
+    int occ_big = 1, occ_small = 1;
+    gemm_occupancy((int)sizeof(T), &occ_big, &occ_small);
     const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, inplace, (int)sizeof(T),
-                                               device_sm_count());
+                                               device_sm_count(), occ_big, occ_small);
     if (tc.small) launch_gemm<T, typename GemmSmall<T>::C>(st, g);
     else launch_gemm<T, typename GemmBig<T>::C>(st, g);
     note_launch();
     return cudaGetLastError();
+}
+
+void gemm_occupancy(int elem_size, int *occ_big, int *occ_small)
+{
+    static int cache[64][2][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    const int e = elem_size == 8 ? 0 : 1;
+    if (!cache[dev][e][0]) {
+        int b = 1, sm = 1;
+        if (elem_size == 8) {
+            using Cb = GemmBig<double>::C;
+            using Cs = GemmSmall<double>::C;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gemm_nt_kernel<double, Cb>, Cb::NT, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sm, gemm_nt_kernel<double, Cs>, Cs::NT, 0);
+        } else {
+            using Cb = GemmBig<float>::C;
+            using Cs = GemmSmall<float>::C;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gemm_nt_kernel<float, Cb>, Cb::NT, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sm, gemm_nt_kernel<float, Cs>, Cs::NT, 0);
+        }
+        cache[dev][e][0] = b > 0 ? b : 1;
+        cache[dev][e][1] = sm > 0 ? sm : 1;
+    }
+    *occ_big = cache[dev][e][0];
+    *occ_small = cache[dev][e][1];
 }
 
 int device_sm_count()
@@ -277,6 +305,56 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
     }
 }
 
+// FP32 variant: one thread solves one row of X entirely in registers against
+// the 64 x 64 triangle in shared memory (padded with the identity when w < 64),
+// with no barrier inside the substitution.  In FP32 the per-column barriers
+// of trsm_right_kernel, not the arithmetic, bound a diagonal-block solve;
+// FP64 keeps trsm_right_kernel, whose four threads per row spread the FP64
+// work over more of the SM's pipes.
+constexpr int kRowsPerCta = 128;
+
+template <int TRANSL>
+__global__ void __launch_bounds__(kRowsPerCta) trsm_rows_f32_kernel(TrsmArgs<float> a)
+{
+    __shared__ float Ls[kTileMax][kTileMax + 1];
+    if (a.abort && *a.abort) return;
+    const int w = a.w;
+    for (int e = threadIdx.x; e < kTileMax * kTileMax; e += blockDim.x) {
+        int i, j;
+        if (a.L.rs == 1) { i = e % kTileMax; j = e / kTileMax; } else { j = e % kTileMax; i = e / kTileMax; }
+        float v;
+        if (i < w && j < w) v = (i >= j) ? a.L(i, j) : 0.f;
+        else v = (i == j) ? 1.f : 0.f;
+        Ls[i][j] = v;
+    }
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kRowsPerCta + threadIdx.x;
+    if (r >= a.M) return;
+    float x[kTileMax];
+#pragma unroll
+    for (int c = 0; c < kTileMax; ++c) x[c] = (c < w) ? a.alpha * a.X(r, c) : 0.f;
+    if (TRANSL) {            // X L^T = B: x_j = (b_j - sum_{k<j} L(j,k) x_k) / L(j,j)
+#pragma unroll
+        for (int j = 0; j < kTileMax; ++j) {
+            float s = x[j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= Ls[j][k] * x[k];
+            x[j] = s / Ls[j][j];
+        }
+    } else {                 // X L = B: x_j = (b_j - sum_{k>j} L(k,j) x_k) / L(j,j)
+#pragma unroll
+        for (int j = kTileMax - 1; j >= 0; --j) {
+            float s = x[j];
+#pragma unroll
+            for (int k = j + 1; k < kTileMax; ++k) s -= Ls[k][j] * x[k];
+            x[j] = s / Ls[j][j];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kTileMax; ++c)
+        if (c < w) a.X(r, c) = x[c];
+}
+
 template <typename T>
 static cudaError_t set_smem_once(const void *fn, int bytes)
 {
@@ -290,6 +368,14 @@ cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int 
                        T alpha, const int32_t *abort)
 {
     if (M <= 0 || w <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        TrsmArgs<float> a{X, Ltri, M, w, transL, alpha, abort};
+        const unsigned grid = (unsigned)((M + kRowsPerCta - 1) / kRowsPerCta);
+        if (transL) trsm_rows_f32_kernel<1><<<grid, kRowsPerCta, 0, st>>>(a);
+        else trsm_rows_f32_kernel<0><<<grid, kRowsPerCta, 0, st>>>(a);
+        note_launch();
+        return cudaGetLastError();
+    }
     const int smem = 2 * kTileMax * kTileLd * (int)sizeof(T);
     cudaError_t e = set_smem_once<T>((const void *)trsm_right_kernel<T>, smem);
     if (e != cudaSuccess) return e;

@@ -122,7 +122,9 @@ cudaError_t gemm_nt(cudaStream_t, View<T> C, View<T> A, View<T> B, int64_t M, in
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 && beta == T(1)) return cudaSuccess;
-    const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, inplace, (int)sizeof(T), device_sm_count());
+    // resident CTAs per SM of the GB300 build (large / small): FP64 2 / 5, FP32 1 / 2
+    const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, inplace, (int)sizeof(T), device_sm_count(),
+                                               sizeof(T) == 8 ? 2 : 1, sizeof(T) == 8 ? 5 : 2);
     const int BM = tc.bm, BN = tc.bn;
     Launch L;
     const int64_t gy = (M + BM - 1) / BM, gx = (N + BN - 1) / BN;

@@ -48,7 +48,7 @@ def emu_lib(tmp_path_factory):
 @pytest.fixture(params=[152, 1], ids=["sms152", "sms1"])
 def emu(emu_lib, request):
     """The emulated device's SM count steers gemm_nt's tile choice: with 152
-    SMs the small launches take the small tiles, with 1 SM every launch takes
+    SMs many small launches take the small tiles, with 1 SM most launches take
     the large tiles, so both CTA decompositions go through the checks."""
     emu_lib.lib.emu_set_sms(request.param)
     return emu_lib
