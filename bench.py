@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--mixed-nrhs", type=int, default=64)
     p.add_argument("--kappas", default="1e2,1e4,1e6")
     p.add_argument("--precs", default="fp32,tf32,bf16")
+    p.add_argument("--max-iter", type=int, default=30, help="refinement steps (mixed mode)")
+    p.add_argument("--no-fp64-ref", action="store_true",
+                   help="mixed mode: skip the FP64 PFTRF + PFTRS reference run")
     return p.parse_args()
 
 
@@ -397,23 +400,28 @@ def run_mixed(args):
         lib.rfp_dpack("N", "L", n, A, n, arf, stream)
         Ah = A.cpu().numpy()
         del A
+        X64h = None
+        if args.no_fp64_ref:
+            fp64.append({"kappa": kappa, "skipped": True})
         # FP64 reference path on a copy
-        fac = arf.clone()
-        X64 = dB.clone()
-        info = torch.zeros(1, dtype=torch.int32, device=dev)
-        torch.cuda.synchronize(dev)
-        ev[0].record(stream)
-        lib.rfp_dpftrf("N", "L", n, fac, info, stream)
-        lib.rfp_dpftrs("N", "L", n, nrhs, fac, X64, n, stream)
-        ev[1].record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = ev[0].elapsed_time(ev[1])
-        X64h = X64.cpu().numpy().T
-        fp64.append({"kappa": kappa, "ms": ms64, "info": int(info.item()),
-                     "tflops": (pftrf_flops(n) + pftrs_flops(n, nrhs)) / (ms64 * 1e-3) / 1e12,
-                     "oracle_bwd_sampled": oracle.solve_backward_error(Ah, X64h[:, sample],
-                                                                       Bh[:, sample])})
-        del fac, X64
+        fac = arf.clone() if not args.no_fp64_ref else None
+        ms64 = None
+        if fac is not None:
+            X64 = dB.clone()
+            info = torch.zeros(1, dtype=torch.int32, device=dev)
+            torch.cuda.synchronize(dev)
+            ev[0].record(stream)
+            lib.rfp_dpftrf("N", "L", n, fac, info, stream)
+            lib.rfp_dpftrs("N", "L", n, nrhs, fac, X64, n, stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            ms64 = ev[0].elapsed_time(ev[1])
+            X64h = X64.cpu().numpy().T
+            fp64.append({"kappa": kappa, "ms": ms64, "info": int(info.item()),
+                         "tflops": (pftrf_flops(n) + pftrs_flops(n, nrhs)) / (ms64 * 1e-3) / 1e12,
+                         "oracle_bwd_sampled": oracle.solve_backward_error(Ah, X64h[:, sample],
+                                                                           Bh[:, sample])})
+            del fac, X64
         for name in args.precs.split(","):
             prec = precs[name]
             wb = lib.rfp_dpfsv_mixed_workspace(n, nrhs, prec)
@@ -422,8 +430,8 @@ def run_mixed(args):
                 torch.cuda.synchronize(dev)
                 lib.rfp_stage_timing(True)
                 ev[0].record(stream)
-                lib.rfp_dpfsv_mixed("N", "L", n, nrhs, arf, dB, n, X, n, prec, 30, 1e-15, work,
-                                    wb, status, stream)
+                lib.rfp_dpfsv_mixed("N", "L", n, nrhs, arf, dB, n, X, n, prec, args.max_iter,
+                                    1e-15, work, wb, status, stream)
                 ev[1].record(stream)
                 torch.cuda.synchronize(dev)
                 stages = {}
@@ -433,9 +441,10 @@ def run_mixed(args):
             ms = ev[0].elapsed_time(ev[1])
             st = rfp.mixed_status(status.cpu().numpy().tobytes())
             Xh = X.cpu().numpy().T
-            fwd = float(np.max(np.abs(Xh - X64h)) / np.max(np.abs(X64h)))
+            fwd = float(np.max(np.abs(Xh - X64h)) / np.max(np.abs(X64h))) if X64h is not None else None
             results.append({
-                "kappa": kappa, "prec": name, "ms": ms, "speedup_vs_fp64": ms64 / ms,
+                "kappa": kappa, "prec": name, "ms": ms,
+                "speedup_vs_fp64": ms64 / ms if ms64 else None,
                 "steps_ms": {k.split(".")[1]: v for k, v in stages.items()},
                 "iterations": st["iterations"], "converged": st["converged"],
                 "info": st["info"], "tc_error": st["tc_error"],

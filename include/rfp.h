@@ -208,6 +208,57 @@ int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, con
                             const double *B, int64_t ldb, double *X, int64_t ldx, int prec,
                             int max_iter, double tol, rfp_mixed_status_t *status, void *stream);
 
+/*
+ * Batched PFTRF + PFTRS (the batching direction of the project): many
+ * independent SPD matrices, each of its own order n <= 512 and its own RFPF
+ * layout, factored (Section 3) and solved (Section 4) by ONE persistent
+ * kernel launch.  All RFP arrays live in one caller buffer `arf` and all
+ * right-hand sides in one buffer `B`, at element offsets given per matrix.
+ *
+ * rfp_batch_entry_t, one per matrix:
+ *   n       order, 0 <= n <= 512
+ *   arf     element offset of its RFP array (n(n+1)/2 elements) in arf
+ *   b       element offset of its right-hand sides (column-major, ldb) in B
+ *   nrhs    0 (factor only) to 8; ldb >= max(1, n) when nrhs > 0
+ *   transr, uplo   its layout ('N'/'T', 'L'/'U')
+ *   nb      panel width 16 or 32 (0 = 32), e.g. from the package's autotuner
+ *
+ * rfp_batch_plan (host, not capturable): validates every entry against the
+ * buffer lengths arf_len / b_len (elements), orders the matrices largest
+ * first, and copies the resulting table into d_plan (device, caller-owned,
+ * rfp_batch_plan_bytes(batch) bytes, 256-byte aligned); it synchronizes
+ * `stream`.  Returns 0, -2 if an entry is invalid (its index is written to
+ * *bad_entry when bad_entry is not NULL), -5 / -6 for a bad d_plan /
+ * plan_bytes, or RFP_ERR_CUDA.  A plan can be reused for any number of runs
+ * with the same entries, in FP64 or FP32.
+ * Arguments: 1 batch, 2 h_entries, 3 arf_len, 4 b_len, 5 d_plan, 6 plan_bytes,
+ * 7 bad_entry, 8 stream.
+ *
+ * rfp_dpfsv_batched / rfp_spfsv_batched: one memset of the plan's work
+ * counter and one kernel launch on `stream` (so the call can be captured in a
+ * CUDA graph and replayed); each matrix is overwritten by its factor, its
+ * right-hand sides by the solutions, and d_info[k] (device, one int32 per
+ * entry, in entry order) receives 0 or the 1-based index of the first
+ * failing pivot (the solve of that matrix is then skipped).  Runs that share
+ * a plan must not overlap on the GPU (they share its counter).
+ * Arguments: 1 batch, 2 d_plan, 3 arf, 4 B, 5 d_info, 6 stream.
+ */
+typedef struct rfp_batch_entry {
+    int64_t n, arf, b;
+    int32_t nrhs, ldb;
+    char transr, uplo;
+    int16_t nb;
+    int32_t reserved;
+} rfp_batch_entry_t;
+size_t rfp_batch_plan_bytes(int64_t batch);
+int rfp_batch_plan(int64_t batch, const rfp_batch_entry_t *h_entries, int64_t arf_len,
+                   int64_t b_len, void *d_plan, size_t plan_bytes, int64_t *bad_entry,
+                   void *stream);
+int rfp_dpfsv_batched(int64_t batch, const void *d_plan, double *arf, double *B, int32_t *d_info,
+                      void *stream);
+int rfp_spfsv_batched(int64_t batch, const void *d_plan, float *arf, float *B, int32_t *d_info,
+                      void *stream);
+
 /* Text for a return code of this library (static storage, never NULL). */
 const char *rfp_status_string(int status);
 

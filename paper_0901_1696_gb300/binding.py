@@ -57,6 +57,13 @@ class RfpMixedStatus(ctypes.Structure):
                 ("backward_error", ctypes.c_double)]
 
 
+def batch_entry_dtype():
+    """numpy dtype with the layout of rfp_batch_entry_t (40 bytes)."""
+    import numpy as np
+    return np.dtype([("n", "<i8"), ("arf", "<i8"), ("b", "<i8"), ("nrhs", "<i4"), ("ldb", "<i4"),
+                     ("transr", "S1"), ("uplo", "S1"), ("nb", "<i2"), ("reserved", "<i4")])
+
+
 def mixed_status(raw: bytes) -> dict:
     """Decode the 24-byte rfp_mixed_status_t read back from the device."""
     st = RfpMixedStatus.from_buffer_copy(bytes(raw))
@@ -211,6 +218,37 @@ class Library:
                max_iter, tol, _addr(status), _stream(stream))
         return self._check("rfp_dpfsv_mixed_noalloc", rc)
 
+    def rfp_batch_plan_bytes(self, batch) -> int:
+        f = self.lib.rfp_batch_plan_bytes
+        f.argtypes, f.restype = [_i64], ctypes.c_size_t
+        return int(f(batch))
+
+    def rfp_batch_plan(self, batch, entries, arf_len, b_len, d_plan, plan_bytes, stream=None):
+        """entries: numpy array of batch_entry_dtype(); returns the bad entry
+        index (-1 if none) when the plan is rejected with -2 (raises)."""
+        f = self.lib.rfp_batch_plan
+        f.argtypes = [_i64, _p, _i64, _i64, _p, ctypes.c_size_t, _p, _p]
+        f.restype = ctypes.c_int
+        bad = ctypes.c_int64(-1)
+        rc = f(batch, _addr(entries), arf_len, b_len, _addr(d_plan), plan_bytes,
+               ctypes.addressof(bad), _stream(stream))
+        if rc == -2:
+            raise RfpError("rfp_batch_plan", rc, f"entry {bad.value} is invalid")
+        return self._check("rfp_batch_plan", rc)
+
+    def _batched(self, name, batch, d_plan, arf, B, d_info, stream):
+        f = getattr(self.lib, name)
+        f.argtypes = [_i64, _p, _p, _p, _p, _p]
+        f.restype = ctypes.c_int
+        return self._check(name, f(batch, _addr(d_plan), _addr(arf), _addr(B), _addr(d_info),
+                                   _stream(stream)))
+
+    def rfp_dpfsv_batched(self, batch, d_plan, arf, B, d_info, stream=None):
+        return self._batched("rfp_dpfsv_batched", batch, d_plan, arf, B, d_info, stream)
+
+    def rfp_spfsv_batched(self, batch, d_plan, arf, B, d_info, stream=None):
+        return self._batched("rfp_spfsv_batched", batch, d_plan, arf, B, d_info, stream)
+
     def rfp_ssyrk_tc(self, uplo, n, k, alpha, A, lda, prec, beta, C, ldc, d_err, stream=None):
         rc = self.lib.rfp_ssyrk_tc(_ch(uplo), n, k, alpha, _addr(A), lda, prec, beta, _addr(C), ldc,
                                    _addr(d_err), _stream(stream))
@@ -255,4 +293,6 @@ rfp_dpftri, rfp_spftri = _fwd("rfp_dpftri"), _fwd("rfp_spftri")
 rfp_ssyrk_tc = _fwd("rfp_ssyrk_tc")
 rfp_dpfsv_mixed, rfp_dpfsv_mixed_workspace = _fwd("rfp_dpfsv_mixed"), _fwd("rfp_dpfsv_mixed_workspace")
 rfp_dpfsv_mixed_noalloc = _fwd("rfp_dpfsv_mixed_noalloc")
+rfp_batch_plan_bytes, rfp_batch_plan = _fwd("rfp_batch_plan_bytes"), _fwd("rfp_batch_plan")
+rfp_dpfsv_batched, rfp_spfsv_batched = _fwd("rfp_dpfsv_batched"), _fwd("rfp_spfsv_batched")
 rfp_dpfsv_mixed_noalloc_capacity = _fwd("rfp_dpfsv_mixed_noalloc_capacity")

@@ -169,6 +169,18 @@ int pftri_entry(char transr, char uplo, int64_t n, T *arf, int32_t *info, void *
     return finish(rfp::pftri_impl<T>((cudaStream_t)stream, L, arf, info));
 }
 
+template <typename T>
+int batched_entry(int64_t batch, const void *d_plan, T *arf, T *B, int32_t *d_info, void *stream)
+{
+    if (batch < 0 || batch > (int64_t(1) << 31) - 1) return -1;
+    if (batch == 0) return RFP_OK;
+    if (!d_plan || (reinterpret_cast<uintptr_t>(d_plan) % 256)) return -2;
+    if (!arf || !aligned(arf)) return -3;
+    if (B && !aligned(B)) return -4;
+    if (!d_info || !aligned(d_info)) return -5;
+    return finish(rfp::batched_run<T>(batch, d_plan, arf, B, d_info, (cudaStream_t)stream));
+}
+
 }  // namespace
 
 extern "C" {
@@ -289,6 +301,35 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
     rfp::make_layout(transr, uplo, n, &L);
     return finish(rfp::pfsv_mixed_impl((cudaStream_t)stream, L, arf, B, ldb, X, ldx, nrhs, prec,
                                        max_iter, tol, w, status));
+}
+
+size_t rfp_batch_plan_bytes(int64_t batch) { return rfp::batch_plan_bytes(batch); }
+
+int rfp_batch_plan(int64_t batch, const rfp_batch_entry_t *h_entries, int64_t arf_len,
+                   int64_t b_len, void *d_plan, size_t plan_bytes, int64_t *bad_entry,
+                   void *stream)
+{
+    if (batch < 0 || batch > (int64_t(1) << 31) - 1) return -1;
+    if (batch > 0 && !h_entries) return -2;
+    if (!d_plan || (reinterpret_cast<uintptr_t>(d_plan) % 256)) return -5;
+    if (plan_bytes < rfp::batch_plan_bytes(batch)) return -6;
+    int64_t bad = -1;
+    const int rc = rfp::batch_plan(batch, h_entries, arf_len, b_len, d_plan, (cudaStream_t)stream, &bad);
+    if (bad_entry) *bad_entry = bad;
+    if (rc >= 1000) return finish((cudaError_t)(rc - 1000));
+    return rc;
+}
+
+int rfp_dpfsv_batched(int64_t batch, const void *d_plan, double *arf, double *B, int32_t *d_info,
+                      void *stream)
+{
+    return batched_entry<double>(batch, d_plan, arf, B, d_info, stream);
+}
+
+int rfp_spfsv_batched(int64_t batch, const void *d_plan, float *arf, float *B, int32_t *d_info,
+                      void *stream)
+{
+    return batched_entry<float>(batch, d_plan, arf, B, d_info, stream);
 }
 
 const char *rfp_status_string(int status)

@@ -152,6 +152,14 @@ cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows,
                        int64_t b_pitch_elems, int b_row0, View<float> C, int64_t M, int64_t N,
                        int64_t K, float alpha, float beta, int cmode, int *err);
 
+// Batched PFTRF + PFTRS (batched.cu).
+size_t batch_plan_bytes(int64_t batch);
+int batch_plan(int64_t batch, const struct rfp_batch_entry *h, int64_t arf_len, int64_t b_len,
+               void *d_plan, cudaStream_t st, int64_t *bad);
+template <typename T>
+cudaError_t batched_run(int64_t batch, const void *d_plan, T *arf, T *B, int32_t *info,
+                        cudaStream_t st);
+
 // TRTTF / TFTTR copies.
 template <typename T>
 cudaError_t pack_copy(cudaStream_t st, const Layout &L, bool lowerA, T *A, int64_t lda, T *arf,

@@ -482,6 +482,25 @@ template cudaError_t convert<float, float>(cudaStream_t, View<float>, View<float
 template cudaError_t convert<float, __nv_bfloat16>(cudaStream_t, View<float>, View<__nv_bfloat16>,
                                                    int64_t, int64_t, bool, const int32_t *);
 
+// The batched kernel runs one whole factorization per CTA and is tested on
+// the GPU; the emulator only links its host entry points.
+size_t batch_plan_bytes(int64_t batch) { return 256 + (size_t)(batch > 0 ? batch : 0) * 104; }
+int batch_plan(int64_t, const struct rfp_batch_entry *, int64_t, int64_t, void *, cudaStream_t,
+               int64_t *bad)
+{
+    *bad = -1;
+    return 1000 + cudaErrorInvalidValue;
+}
+template <typename T>
+cudaError_t batched_run(int64_t, const void *, T *, T *, int32_t *, cudaStream_t)
+{
+    return cudaErrorInvalidValue;
+}
+template cudaError_t batched_run<double>(int64_t, const void *, double *, double *, int32_t *,
+                                         cudaStream_t);
+template cudaError_t batched_run<float>(int64_t, const void *, float *, float *, int32_t *,
+                                        cudaStream_t);
+
 #define EMU_INST(T)                                                                                  \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \
                                     T, T, int, int, int, const int32_t *, bool);                     \
