@@ -274,9 +274,9 @@ int batch_plan(int64_t batch, const rfp_batch_entry_t *h, int64_t arf_len, int64
         bool ok = tr_ok && up_ok && e.n >= 0 && e.n <= kBatchMaxN && e.arf >= 0 &&
                   e.arf + nt <= arf_len && (e.nb == 0 || e.nb == 16 || e.nb == 32) && e.nrhs >= 0 &&
                   e.nrhs <= 8;
-        if (ok && e.nrhs > 0)
-            ok = e.ldb >= std::max<int64_t>(1, e.n) && e.b >= 0 &&
-                 e.b + (int64_t)(e.nrhs - 1) * e.ldb + e.n <= b_len;
+        if (ok && e.nrhs > 0)   // an order-0 matrix reads no right-hand side
+            ok = e.ldb >= std::max<int64_t>(1, e.n) &&
+                 (e.n == 0 || (e.b >= 0 && e.b + (int64_t)(e.nrhs - 1) * e.ldb + e.n <= b_len));
         if (!ok) {
             *bad = k;
             return -2;

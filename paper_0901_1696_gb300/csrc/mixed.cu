@@ -35,6 +35,8 @@ size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec)
     b += up((size_t)n * (size_t)nrhs * sizeof(float));                        // D
     b += up((size_t)nrhs * sizeof(double));                                   // berr
     b += up(sizeof(double)) + up(sizeof(int32_t)) + up(sizeof(int32_t));      // anorm, stop, tc_err
+    if (residual_splits(n) > 1)
+        b += up((size_t)residual_splits(n) * (size_t)n * (size_t)nrhs * sizeof(double));
     return b;
 }
 
@@ -62,6 +64,9 @@ bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, Mi
     w->stop = reinterpret_cast<int32_t *>(p);
     p += up(sizeof(int32_t));
     w->tc_err = reinterpret_cast<int32_t *>(p);
+    p += up(sizeof(int32_t));
+    w->splits = residual_splits(n);
+    w->splitk = w->splits > 1 ? reinterpret_cast<double *>(p) : nullptr;
     return true;
 }
 
@@ -100,29 +105,29 @@ static cudaError_t factor_tc(cudaStream_t st, View<float> W, int64_t n, int prec
 // A22 = T2 as stored lower triangles; the strict upper halves come from
 // the transposed views).
 static cudaError_t residual(cudaStream_t st, const RfpViews &v, View<double> B, View<double> X,
-                            View<double> R, int64_t nrhs, const int32_t *stop)
+                            View<double> R, int64_t nrhs, const int32_t *stop, int splits,
+                            double *work)
 {
+    // the products have nrhs columns and a long K: split K so they fill the GPU
+    auto gemm = [&](View<double> C, View<double> A, View<double> Bop, int64_t M, int64_t K,
+                    int amask) {
+        return gemm_nt_splitk<double>(st, C, A, Bop, M, nrhs, K, -1.0, 1.0, MASK_NONE, amask,
+                                      MASK_NONE, stop, splits, work);
+    };
     const int64_t n1 = v.n1, n2 = v.n2;
     RFP_TRY((convert<double, double>(st, B, R, n1 + n2, nrhs, false, stop)));
     View<double> R1 = R, R2 = R.sub(n1, 0), X1 = X, X2 = X.sub(n1, 0);
-    const double m1 = -1.0, p1 = 1.0;
     if (n1 > 0) {
-        RFP_TRY(gemm_nt<double>(st, R1, v.t1, X1.t(), n1, nrhs, n1, m1, p1, MASK_NONE, MASK_LOWER,
-                                MASK_NONE, stop));
-        RFP_TRY(gemm_nt<double>(st, R1, v.t1.t(), X1.t(), n1, nrhs, n1, m1, p1, MASK_NONE,
-                                MASK_STRICT_UPPER, MASK_NONE, stop));
+        RFP_TRY(gemm(R1, v.t1, X1.t(), n1, n1, MASK_LOWER));
+        RFP_TRY(gemm(R1, v.t1.t(), X1.t(), n1, n1, MASK_STRICT_UPPER));
     }
     if (n1 > 0 && n2 > 0) {
-        RFP_TRY(gemm_nt<double>(st, R1, v.s.t(), X2.t(), n1, nrhs, n2, m1, p1, MASK_NONE, MASK_NONE,
-                                MASK_NONE, stop));
-        RFP_TRY(gemm_nt<double>(st, R2, v.s, X1.t(), n2, nrhs, n1, m1, p1, MASK_NONE, MASK_NONE,
-                                MASK_NONE, stop));
+        RFP_TRY(gemm(R1, v.s.t(), X2.t(), n1, n2, MASK_NONE));
+        RFP_TRY(gemm(R2, v.s, X1.t(), n2, n1, MASK_NONE));
     }
     if (n2 > 0) {
-        RFP_TRY(gemm_nt<double>(st, R2, v.t2, X2.t(), n2, nrhs, n2, m1, p1, MASK_NONE, MASK_LOWER,
-                                MASK_NONE, stop));
-        RFP_TRY(gemm_nt<double>(st, R2, v.t2.t(), X2.t(), n2, nrhs, n2, m1, p1, MASK_NONE,
-                                MASK_STRICT_UPPER, MASK_NONE, stop));
+        RFP_TRY(gemm(R2, v.t2, X2.t(), n2, n2, MASK_LOWER));
+        RFP_TRY(gemm(R2, v.t2.t(), X2.t(), n2, n2, MASK_STRICT_UPPER));
     }
     return cudaSuccess;
 }
@@ -166,7 +171,7 @@ cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_
         RFP_TRY(trsm_left_lower_trans_rec<float>(st, D, nrhs, W, n, w.stop));
         RFP_TRY(add_correction(st, X, D, n, nrhs, w.stop));
         stage_mark(st, "mixed.solve");
-        RFP_TRY(residual(st, v, B, X, R, nrhs, w.stop));
+        RFP_TRY(residual(st, v, B, X, R, nrhs, w.stop, w.splits, w.splitk));
         RFP_TRY(backward_error(st, R, X, B, n, nrhs, w.anorm, w.berr, tol, status, w.stop));
         stage_mark(st, "mixed.residual");
     }

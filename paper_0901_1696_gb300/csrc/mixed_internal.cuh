@@ -41,7 +41,17 @@ struct MixedWork {
     double *anorm;     // ||A||_inf
     int32_t *stop;     // refinement stop word
     int32_t *tc_err;   // tensor-core kernel error word
+    double *splitk;    // split-K slices of the residual products (residual_splits x n x nrhs)
+    int splits;
 };
+
+// K chunks of the residual products: one per 2048 of the larger block's
+// order, at most 8 (1 = no split, no buffer).
+inline int residual_splits(int64_t n)
+{
+    const int64_t k = ((n + 1) / 2) / 2048;
+    return (int)(k < 1 ? 1 : (k > 8 ? 8 : k));
+}
 
 constexpr int64_t kMixedPanel = 512;   // panel width of the tensor-core factorization
 

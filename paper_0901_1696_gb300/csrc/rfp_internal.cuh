@@ -116,6 +116,15 @@ cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M,
                     int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
                     const int32_t *abort, bool inplace = false);
 
+// gemm_nt with K split into `splits` chunks (one launch, grid z = chunk), the
+// chunk products written to work (splits x M x N, dense) and summed into C in
+// a fixed order by a second kernel.  For products with few output tiles and a
+// long K.  splits <= 1 or work == nullptr falls back to gemm_nt.  No in-place.
+template <typename T>
+cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
+                           int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
+                           const int32_t *abort, int splits, T *work);
+
 // Solve X * op(Ltri) = alpha * X in place for an M x w strip (w <= 64);
 // op = transpose when transL != 0.  Rows are independent.
 template <typename T>

@@ -11,6 +11,7 @@
 // tensor-core MMA), so the GEMM keeps 4x4 register tiles and double-buffered
 // shared memory, which keeps one DFMA in flight per thread per cycle of
 // shared-memory traffic; memory traffic is far below the HBM roofline.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -40,6 +41,8 @@ struct GemmArgs {
     T alpha, beta;
     int cmode, amask, bmask;
     const int32_t *abort;
+    int64_t kchunk = 0;     // split-K: blockIdx.z covers K range [z kchunk, (z+1) kchunk)
+    int64_t zstride = 0;    //          and writes C + z * zstride
 };
 
 template <typename T>
@@ -66,6 +69,11 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
 
     // K range that can hold non-zero products for this tile.
     int64_t kbeg = 0, kend = g.K;
+    if (g.kchunk > 0) {
+        kbeg = (int64_t)blockIdx.z * g.kchunk;
+        kend = min(kend, kbeg + g.kchunk);
+        g.C.p += (int64_t)blockIdx.z * g.zstride;
+    }
     if (g.amask == MASK_LOWER || g.amask == MASK_STRICT_LOWER) kend = min(kend, m0 + BM);
     if (g.amask == MASK_UPPER || g.amask == MASK_STRICT_UPPER) kbeg = max(kbeg, m0);
     if (g.bmask == MASK_LOWER || g.bmask == MASK_STRICT_LOWER) kend = min(kend, n0 + BN);
@@ -175,10 +183,52 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
 }
 
 template <typename T, typename Cfg>
-static void launch_gemm(cudaStream_t st, const GemmArgs<T> &g)
+static void launch_gemm(cudaStream_t st, const GemmArgs<T> &g, unsigned splits = 1)
 {
-    dim3 grid((unsigned)((g.N + Cfg::BN - 1) / Cfg::BN), (unsigned)((g.M + Cfg::BM - 1) / Cfg::BM));
+    dim3 grid((unsigned)((g.N + Cfg::BN - 1) / Cfg::BN), (unsigned)((g.M + Cfg::BM - 1) / Cfg::BM),
+              splits);
     gemm_nt_kernel<T, Cfg><<<grid, Cfg::NT, 0, st>>>(g);
+}
+
+// C = beta C + alpha sum_z W_z, W_z dense column-major M x N slices, summed in
+// increasing z (the same order on every run).
+template <typename T>
+__global__ void splitk_reduce_kernel(View<T> C, const T *W, int64_t M, int64_t N, int splits,
+                                     T alpha, T beta, int cmode, const int32_t *abort)
+{
+    if (abort && *abort) return;
+    const int64_t total = M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % M, j = e / M;
+        if (cmode == MASK_LOWER && j > i) continue;
+        T s = T(0);
+        for (int z = 0; z < splits; ++z) s += W[(int64_t)z * total + e];
+        T v = alpha * s;
+        if (beta != T(0)) v = fma(beta, C(i, j), v);
+        C(i, j) = v;
+    }
+}
+
+template <typename T>
+cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
+                           int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
+                           const int32_t *abort, int splits, T *work)
+{
+    if (splits <= 1 || !work) return gemm_nt(st, C, A, B, M, N, K, alpha, beta, cmode, amask, bmask, abort);
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    GemmArgs<T> g{View<T>{work, 1, M}, A, B, M, N, K, T(1), T(0), cmode, amask, bmask, abort};
+    g.kchunk = (K + splits - 1) / splits;
+    g.zstride = M * N;
+    launch_gemm<T, typename GemmBig<T>::C>(st, g, (unsigned)splits);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>((M * N + 255) / 256, 4096);
+    splitk_reduce_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(C, work, M, N, splits, alpha, beta,
+                                                            cmode, abort);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -333,21 +383,23 @@ __global__ void __launch_bounds__(kRowsPerCta) trsm_rows_f32_kernel(TrsmArgs<flo
     float x[kTileMax];
 #pragma unroll
     for (int c = 0; c < kTileMax; ++c) x[c] = (c < w) ? a.alpha * a.X(r, c) : 0.f;
+    // Right-looking order: once x_j is final, its contribution is removed
+    // from every later x_c at once, so each step issues up to 63 independent
+    // FMAs (the per-element summation order is the same ascending order as
+    // the dot-product form).
     if (TRANSL) {            // X L^T = B: x_j = (b_j - sum_{k<j} L(j,k) x_k) / L(j,j)
 #pragma unroll
         for (int j = 0; j < kTileMax; ++j) {
-            float s = x[j];
+            x[j] = x[j] / Ls[j][j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) s -= Ls[j][k] * x[k];
-            x[j] = s / Ls[j][j];
+            for (int c = j + 1; c < kTileMax; ++c) x[c] -= Ls[c][j] * x[j];
         }
     } else {                 // X L = B: x_j = (b_j - sum_{k>j} L(k,j) x_k) / L(j,j)
 #pragma unroll
         for (int j = kTileMax - 1; j >= 0; --j) {
-            float s = x[j];
+            x[j] = x[j] / Ls[j][j];
 #pragma unroll
-            for (int k = j + 1; k < kTileMax; ++k) s -= Ls[k][j] * x[k];
-            x[j] = s / Ls[j][j];
+            for (int c = 0; c < j; ++c) x[c] -= Ls[j][c] * x[j];
         }
     }
 #pragma unroll
@@ -409,31 +461,31 @@ __device__ __forceinline__ void store_lower_tile(View<T> A, const T *S, int w)
     }
 }
 
+// Unblocked right-looking Cholesky of one tile with one barrier per column:
+// at step j every thread reads the (final) pivot S[j][j] and forms
+// l_ij = S[i][j] * (1 / sqrt(pivot)) itself (LAPACK's unblocked Cholesky also
+// scales a column by the reciprocal of its diagonal), updates its share of the
+// trailing triangle, and the columns are scaled with the same reciprocals
+// when the tile is written back.
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32_t *info,
                                                          int64_t base)
 {
     __shared__ __align__(16) T S[kTileMax * kTileLd];
-    __shared__ int fail;
+    __shared__ T rinv[kTileMax], sq[kTileMax];
     if (*info != 0) return;
     load_lower_tile(S, A, w);
-    if (threadIdx.x == 0) fail = -1;
     __syncthreads();
+    int fail = -1;
     for (int j = 0; j < w; ++j) {
-        if (threadIdx.x == 0) {
-            const T d = S[j * kTileLd + j];
-            if (!(d > T(0))) fail = j;
-            else S[j * kTileLd + j] = sqrt(d);
-        }
-        __syncthreads();
-        if (fail >= 0) break;
-        const T djj = S[j * kTileLd + j];
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) S[i * kTileLd + j] /= djj;
-        __syncthreads();
+        const T d = S[j * kTileLd + j];
+        if (!(d > T(0))) { fail = j; break; }      // every thread sees the same d
+        const T r = sqrt(d), ri = T(1) / r;
+        if (threadIdx.x == 0) { sq[j] = r; rinv[j] = ri; }
         const int rem = w - j - 1;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
             const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-            if (k <= i) S[i * kTileLd + k] -= S[i * kTileLd + j] * S[k * kTileLd + j];
+            if (k <= i) S[i * kTileLd + k] -= (S[i * kTileLd + j] * ri) * (S[k * kTileLd + j] * ri);
         }
         __syncthreads();
     }
@@ -441,7 +493,12 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32
         if (threadIdx.x == 0) *info = (int32_t)(base + fail + 1);
         return;
     }
-    store_lower_tile(A, S, w);
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int i, j;
+        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
+        if (i > j) A(i, j) = S[i * kTileLd + j] * rinv[j];
+        else if (i == j) A(i, j) = sq[j];
+    }
 }
 
 template <typename T>
@@ -543,6 +600,9 @@ cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int6
 #define RFP_INSTANTIATE(T)                                                                    \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
                                     int64_t, T, T, int, int, int, const int32_t *, bool);     \
+    template cudaError_t gemm_nt_splitk<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t,   \
+                                           int64_t, int64_t, T, T, int, int, int,             \
+                                           const int32_t *, int, T *);                        \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,  \
                                        const int32_t *);                                      \
     template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);       \

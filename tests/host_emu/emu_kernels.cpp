@@ -158,6 +158,60 @@ cudaError_t gemm_nt(cudaStream_t, View<T> C, View<T> A, View<T> B, int64_t M, in
     return L.commit();
 }
 
+// Split-K: CTA (z, tile) writes slice z of the work buffer, then the reduce
+// kernel sums the slices into C (one CTA per element range).
+template <typename T>
+cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
+                           int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
+                           const int32_t *abort, int splits, T *work)
+{
+    if (splits <= 1 || !work) return gemm_nt(st, C, A, B, M, N, K, alpha, beta, cmode, amask, bmask, abort);
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int64_t kc = (K + splits - 1) / splits;
+    for (int z = 0; z < splits; ++z) {      // each slice's launch part, checked like a launch
+        const int64_t k0 = std::min<int64_t>(K, z * kc), k1 = std::min<int64_t>(K, k0 + kc);
+        View<T> Wz{work + (int64_t)z * M * N, 1, M};
+        cudaError_t e;
+        if (k1 > k0) {
+            e = gemm_nt(st, Wz, A.sub(0, k0), B.sub(0, k0), M, N, k1 - k0, T(1), T(0), cmode,
+                        MASK_NONE, MASK_NONE, abort, false);
+            // masks in the full K coordinates: emulate directly when a mask is set
+            if (amask != MASK_NONE || bmask != MASK_NONE) {
+                Launch L;
+                for (int64_t i = 0; i < M; ++i)
+                    for (int64_t j = 0; j < N; ++j) {
+                        T acc = T(0);
+                        for (int64_t k = k0; k < k1; ++k) {
+                            T a = mask_keeps(amask, i, k) ? L.rd(&A(i, k)) : T(0);
+                            T b = mask_keeps(bmask, j, k) ? L.rd(&B(j, k)) : T(0);
+                            acc += a * b;
+                        }
+                        L.wr(&Wz(i, j), acc);
+                    }
+                e = L.commit();
+            }
+        } else {
+            Launch L;
+            for (int64_t i = 0; i < M; ++i)
+                for (int64_t j = 0; j < N; ++j) L.wr(&Wz(i, j), T(0));
+            e = L.commit();
+        }
+        if (e != cudaSuccess) return e;
+    }
+    Launch L;
+    if (abort && L.rd(abort)) return L.commit();
+    for (int64_t j = 0; j < N; ++j)
+        for (int64_t i = 0; i < M; ++i) {
+            if (cmode == MASK_LOWER && j > i) continue;
+            T s = T(0);
+            for (int z = 0; z < splits; ++z) s += L.rd(&work[(int64_t)z * M * N + i + j * M]);
+            T v = alpha * s;
+            if (beta != T(0)) v += beta * L.rd(&C(i, j));
+            L.wr(&C(i, j), v);
+        }
+    return L.commit();
+}
+
 template <typename T>
 cudaError_t trsm_strip(cudaStream_t, View<T> X, View<T> Lt, int64_t M, int w, int transL, T alpha,
                        const int32_t *abort)
@@ -209,8 +263,9 @@ cudaError_t potrf_tile(cudaStream_t, View<T> A, int w, int32_t *info, int64_t ba
             *info = v;
             return g_violations ? cudaErrorIllegalAddress : cudaSuccess;
         }
-        s[j * w + j] = std::sqrt(d);
-        for (int i = j + 1; i < w; ++i) s[i * w + j] /= s[j * w + j];
+        const T sqd = std::sqrt(d), ri = T(1) / sqd;   // same arithmetic as the kernel
+        s[j * w + j] = sqd;
+        for (int i = j + 1; i < w; ++i) s[i * w + j] *= ri;
         for (int i = j + 1; i < w; ++i)
             for (int k = j + 1; k <= i; ++k) s[i * w + k] -= s[i * w + j] * s[k * w + j];
     }
@@ -504,6 +559,8 @@ template cudaError_t batched_run<float>(int64_t, const void *, float *, float *,
 #define EMU_INST(T)                                                                                  \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \
                                     T, T, int, int, int, const int32_t *, bool);                     \
+    template cudaError_t gemm_nt_splitk<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
+                                           int64_t, T, T, int, int, int, const int32_t *, int, T *); \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,         \
                                        const int32_t *);                                             \
     template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);              \

@@ -89,3 +89,15 @@ def test_mixed_argument_checks():
             rfp.rfp_dpfsv_mixed("N", "L", *args, status)
         assert e.value.status == code
     assert rfp.rfp_dpfsv_mixed_workspace(n, nrhs, 9) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_mixed_large_split_k_residual(prec):
+    """n = 8200: the refinement's FP64 residual products run split along K
+    (two chunks) through the workspace; the solve must still meet the bar."""
+    n = 8200
+    A = gen.spd_bbt(n, seed=5)
+    B = gen.rhs(n, 4, seed=6)
+    X, st = solve_mixed("T", "U", A, B, PRECS[prec])
+    assert st["info"] == 0 and st["tc_error"] == 0 and st["converged"] == 1, st
+    assert oracle.solve_backward_error(A, X, B) <= 1e-14
