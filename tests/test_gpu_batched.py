@@ -60,7 +60,8 @@ def run_batch(entries, arf_all, b_all, dtype=torch.float64, stream=None):
     count = len(entries)
     plan = torch.empty(rfp.rfp_batch_plan_bytes(count), dtype=torch.uint8, device="cuda")
     rfp.rfp_batch_plan(count, entries, arf_all.size, b_all.size, plan, plan.numel())
-    d_arf = torch.from_numpy(arf_all).to(dtype).cuda()
+    d_arf = torch.from_numpy(arf_all).to(dtype).cuda() if arf_all.size else \
+        torch.zeros(1, dtype=dtype, device="cuda")          # the library wants a real pointer
     d_b = torch.from_numpy(b_all).to(dtype).cuda() if b_all.size else \
         torch.zeros(1, dtype=dtype, device="cuda")
     info = torch.full((count,), -7, dtype=torch.int32, device="cuda")
