@@ -138,7 +138,7 @@ def test_batched_graph_capture_and_alone_vs_mix_bit_identical():
         a1 = arf_all[m["arf_off"]: m["arf_off"] + nt]
         b1 = b_all[m["b_off"]: m["b_off"] + m["n"] * m["nrhs"]]
         _, d1, db1, _ = run_batch(one, a1, b1)
-        assert np.array_equal(d1.cpu().numpy(), eager_arf[m["arf_off"]: m["arf_off"] + nt])
+        assert np.array_equal(d1.cpu().numpy()[:nt], eager_arf[m["arf_off"]: m["arf_off"] + nt])
         if m["nrhs"] and m["n"]:
             assert np.array_equal(db1.cpu().numpy()[: b1.size],
                                   eager_b[m["b_off"]: m["b_off"] + b1.size])
