@@ -461,12 +461,13 @@ __device__ __forceinline__ void store_lower_tile(View<T> A, const T *S, int w)
     }
 }
 
-// Unblocked right-looking Cholesky of one tile with one barrier per column:
-// at step j every thread reads the (final) pivot S[j][j] and forms
-// l_ij = S[i][j] * (1 / sqrt(pivot)) itself (LAPACK's unblocked Cholesky also
-// scales a column by the reciprocal of its diagonal), updates its share of the
-// trailing triangle, and the columns are scaled with the same reciprocals
-// when the tile is written back.
+// Unblocked right-looking Cholesky of one tile.  At step j every thread reads
+// the (final) pivot S[j][j] itself and uses l_ij = S[i][j] * (1 / sqrt(pivot))
+// (LAPACK's unblocked Cholesky also scales a column by the reciprocal of its
+// diagonal).  FP32: one barrier per column, each thread forms the scaled
+// values it needs and the columns are scaled on write-back.  FP64: the
+// column is scaled in place first (two barriers per column), so a trailing
+// element costs one DFMA.
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32_t *info,
                                                          int64_t base)
@@ -483,9 +484,20 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32
         const T r = sqrt(d), ri = T(1) / r;
         if (threadIdx.x == 0) { sq[j] = r; rinv[j] = ri; }
         const int rem = w - j - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-            if (k <= i) S[i * kTileLd + k] -= (S[i * kTileLd + j] * ri) * (S[k * kTileLd + j] * ri);
+        if constexpr (sizeof(T) == 8) {
+            // FP64: scale the column once (one extra barrier) so that each
+            // trailing element costs one DFMA on the FP64 pipe
+            for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) S[i * kTileLd + j] *= ri;
+            __syncthreads();
+            for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+                const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+                if (k <= i) S[i * kTileLd + k] -= S[i * kTileLd + j] * S[k * kTileLd + j];
+            }
+        } else {
+            for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+                const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+                if (k <= i) S[i * kTileLd + k] -= (S[i * kTileLd + j] * ri) * (S[k * kTileLd + j] * ri);
+            }
         }
         __syncthreads();
     }
@@ -496,7 +508,7 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32
     for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
         int i, j;
         if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
-        if (i > j) A(i, j) = S[i * kTileLd + j] * rinv[j];
+        if (i > j) A(i, j) = sizeof(T) == 8 ? S[i * kTileLd + j] : S[i * kTileLd + j] * rinv[j];
         else if (i == j) A(i, j) = sq[j];
     }
 }
