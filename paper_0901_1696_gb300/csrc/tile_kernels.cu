@@ -293,6 +293,33 @@ int device_sm_count()
 // Strip triangular solve: X op(L) = alpha X, 64 rows per CTA, w <= 64.
 
 constexpr int kTileMax = 64, kTileLd = 65, kStripRows = 64;
+constexpr int kTileThreads = 256;
+
+// Tile loaders with a compile-time trip count: every thread issues all its
+// global loads before its first shared-memory store, so a 64 x 64 tile costs
+// one load latency rather than one per loop iteration.  Element (i, j) of the
+// 64 x 64 index space is read when (i, j) is inside the w x w (or rows x w)
+// block and keep(i, j) holds; the shared tile gets `fill(i, j)` elsewhere.
+template <int NT, typename T, typename Keep, typename Fill>
+__device__ __forceinline__ void load_tile64(T *S, View<T> A, int rows, int w, Keep keep, Fill fill,
+                                            T scale = T(1))
+{
+    constexpr int IT = kTileMax * kTileMax / NT;
+    const bool rowfast = A.rs == 1;
+    T v[IT];
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+        const int e = threadIdx.x + q * NT, a = e % kTileMax, b = e / kTileMax;
+        const int i = rowfast ? a : b, j = rowfast ? b : a;
+        v[q] = (i < rows && j < w && keep(i, j)) ? scale * A(i, j) : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+        const int e = threadIdx.x + q * NT, a = e % kTileMax, b = e / kTileMax;
+        const int i = rowfast ? a : b, j = rowfast ? b : a;
+        S[i * kTileLd + j] = (i < rows && j < w && keep(i, j)) ? v[q] : fill(i, j);
+    }
+}
 
 template <typename T>
 struct TrsmArgs {
@@ -313,18 +340,14 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
     const int tid = threadIdx.x, w = a.w;
     const int64_t r0 = (int64_t)blockIdx.x * kStripRows;
 
-    for (int e = tid; e < w * w; e += 256) {
-        int i, j;
-        if (a.L.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
-        Ls[i * kTileLd + j] = (i >= j) ? a.L(i, j) : T(0);
-    }
-    const bool xrow = (a.X.rs == 1);
-    for (int e = tid; e < kStripRows * w; e += 256) {
-        int rr, cc;
-        if (xrow) { rr = e % kStripRows; cc = e / kStripRows; } else { cc = e % w; rr = e / w; }
-        const int64_t gr = r0 + rr;
-        Xs[rr * kTileLd + cc] = gr < a.M ? a.alpha * a.X(gr, cc) : T(0);
-    }
+    load_tile64<kTileThreads>(Ls, a.L, w, w, [](int i, int j) { return i >= j; },
+                              [](int, int) { return T(0); });
+    const int64_t rows_left = a.M - r0;
+    const int rows = (int)(rows_left < kStripRows ? rows_left : kStripRows);
+    View<T> Xv = a.X.sub(r0, 0);
+    const T alpha = a.alpha;
+    load_tile64<kTileThreads>(Xs, Xv, rows, w, [](int, int) { return true; },
+                              [](int, int) { return T(0); }, alpha);
     __syncthreads();
 
     const int row = tid % kStripRows, grp = tid / kStripRows;   // 4 column groups
@@ -347,11 +370,15 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
         }
     }
 
-    for (int e = tid; e < kStripRows * w; e += 256) {
-        int rr, cc;
-        if (xrow) { rr = e % kStripRows; cc = e / kStripRows; } else { cc = e % w; rr = e / w; }
-        const int64_t gr = r0 + rr;
-        if (gr < a.M) a.X(gr, cc) = Xs[rr * kTileLd + cc];
+    {
+        constexpr int IT = kTileMax * kTileMax / kTileThreads;
+        const bool xrow = (a.X.rs == 1);
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int e = tid + q * kTileThreads, p1 = e % kTileMax, p2 = e / kTileMax;
+            const int rr = xrow ? p1 : p2, cc = xrow ? p2 : p1;
+            if (rr < rows && cc < w) Xv(rr, cc) = Xs[rr * kTileLd + cc];
+        }
     }
 }
 
@@ -369,14 +396,8 @@ __global__ void __launch_bounds__(kRowsPerCta) trsm_rows_f32_kernel(TrsmArgs<flo
     __shared__ float Ls[kTileMax][kTileMax + 1];
     if (a.abort && *a.abort) return;
     const int w = a.w;
-    for (int e = threadIdx.x; e < kTileMax * kTileMax; e += blockDim.x) {
-        int i, j;
-        if (a.L.rs == 1) { i = e % kTileMax; j = e / kTileMax; } else { j = e % kTileMax; i = e / kTileMax; }
-        float v;
-        if (i < w && j < w) v = (i >= j) ? a.L(i, j) : 0.f;
-        else v = (i == j) ? 1.f : 0.f;
-        Ls[i][j] = v;
-    }
+    load_tile64<kRowsPerCta>(&Ls[0][0], a.L, w, w, [](int i, int j) { return i >= j; },
+                             [w](int i, int j) { return (i == j && i >= w) ? 1.f : 0.f; });
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * kRowsPerCta + threadIdx.x;
     if (r >= a.M) return;
@@ -444,20 +465,20 @@ cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int 
 template <typename T>
 __device__ __forceinline__ void load_lower_tile(T *S, View<T> A, int w)
 {
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i, j;
-        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
-        S[i * kTileLd + j] = (i >= j) ? A(i, j) : T(0);
-    }
+    load_tile64<kTileThreads>(S, A, w, w, [](int i, int j) { return i >= j; },
+                              [](int, int) { return T(0); });
 }
 
 template <typename T>
 __device__ __forceinline__ void store_lower_tile(View<T> A, const T *S, int w)
 {
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i, j;
-        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
-        if (i >= j) A(i, j) = S[i * kTileLd + j];
+    constexpr int IT = kTileMax * kTileMax / kTileThreads;
+    const bool rowfast = A.rs == 1;
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+        const int e = threadIdx.x + q * kTileThreads, p1 = e % kTileMax, p2 = e / kTileMax;
+        const int i = rowfast ? p1 : p2, j = rowfast ? p2 : p1;
+        if (i < w && j < w && i >= j) A(i, j) = S[i * kTileLd + j];
     }
 }
 
@@ -505,11 +526,15 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32
         if (threadIdx.x == 0) *info = (int32_t)(base + fail + 1);
         return;
     }
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        int i, j;
-        if (A.rs == 1) { i = e % w; j = e / w; } else { j = e % w; i = e / w; }
+    constexpr int IT = kTileMax * kTileMax / kTileThreads;
+    const bool rowfast = A.rs == 1;
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+        const int e = threadIdx.x + q * kTileThreads, p1 = e % kTileMax, p2 = e / kTileMax;
+        const int i = rowfast ? p1 : p2, j = rowfast ? p2 : p1;
+        if (i >= w || j >= w || i < j) continue;
         if (i > j) A(i, j) = sizeof(T) == 8 ? S[i * kTileLd + j] : S[i * kTileLd + j] * rinv[j];
-        else if (i == j) A(i, j) = sq[j];
+        else A(i, j) = sq[j];
     }
 }
 
