@@ -382,62 +382,50 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
     }
 }
 
-// FP32 variant: one thread solves one row of X against the 64 x 64 triangle
-// in shared memory (padded with the identity when w < 64), with no barrier
-// inside the substitution.  In FP32 the per-column barriers of
-// trsm_right_kernel, not the arithmetic, bound a diagonal-block solve; FP64
-// keeps trsm_right_kernel, whose four threads per row spread the FP64 work
-// over more of the SM's pipes.  The row lives in shared memory (one padded
-// row per thread, conflict-free) and the column loop stays rolled: a fully
-// unrolled substitution is ~6k straight-line instructions executed once,
-// which the instruction cache cannot hold.
-constexpr int kRowsPerCta = 64;
+// FP32 variant: one thread solves one row of X entirely in registers against
+// the 64 x 64 triangle in shared memory (padded with the identity when w < 64),
+// with no barrier inside the substitution.  In FP32 the per-column barriers
+// of trsm_right_kernel, not the arithmetic, bound a diagonal-block solve;
+// FP64 keeps trsm_right_kernel, whose four threads per row spread the FP64
+// work over more of the SM's pipes.
+constexpr int kRowsPerCta = 128;
 
 template <int TRANSL>
 __global__ void __launch_bounds__(kRowsPerCta) trsm_rows_f32_kernel(TrsmArgs<float> a)
 {
     __shared__ float Ls[kTileMax][kTileMax + 1];
-    __shared__ float Xs[kRowsPerCta][kTileMax + 1];
     if (a.abort && *a.abort) return;
     const int w = a.w;
-    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerCta;
-    const int64_t rows_left = a.M - r0;
-    const int rows = (int)(rows_left < kRowsPerCta ? rows_left : kRowsPerCta);
-    View<float> Xv = a.X.sub(r0, 0);
     load_tile64<kRowsPerCta>(&Ls[0][0], a.L, w, w, [](int i, int j) { return i >= j; },
                              [w](int i, int j) { return (i == j && i >= w) ? 1.f : 0.f; });
-    load_tile64<kRowsPerCta>(&Xs[0][0], Xv, rows, w, [](int, int) { return true; },
-                             [](int, int) { return 0.f; }, a.alpha);
     __syncthreads();
-    float *x = Xs[threadIdx.x];
-    // Right-looking order: once x_j is final its contribution is removed from
-    // every later x_c (the per-element summation order is ascending j).
+    const int64_t r = (int64_t)blockIdx.x * kRowsPerCta + threadIdx.x;
+    if (r >= a.M) return;
+    float x[kTileMax];
+#pragma unroll
+    for (int c = 0; c < kTileMax; ++c) x[c] = (c < w) ? a.alpha * a.X(r, c) : 0.f;
+    // Right-looking order: once x_j is final, its contribution is removed
+    // from every later x_c at once, so each step issues up to 63 independent
+    // FMAs (the per-element summation order is the same ascending order as
+    // the dot-product form).
     if (TRANSL) {            // X L^T = B: x_j = (b_j - sum_{k<j} L(j,k) x_k) / L(j,j)
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < kTileMax; ++j) {
-            const float xj = x[j] / Ls[j][j];
-            x[j] = xj;
-#pragma unroll 8
-            for (int c = j + 1; c < kTileMax; ++c) x[c] -= Ls[c][j] * xj;
+            x[j] = x[j] / Ls[j][j];
+#pragma unroll
+            for (int c = j + 1; c < kTileMax; ++c) x[c] -= Ls[c][j] * x[j];
         }
     } else {                 // X L = B: x_j = (b_j - sum_{k>j} L(k,j) x_k) / L(j,j)
-#pragma unroll 1
+#pragma unroll
         for (int j = kTileMax - 1; j >= 0; --j) {
-            const float xj = x[j] / Ls[j][j];
-            x[j] = xj;
-#pragma unroll 8
-            for (int c = 0; c < j; ++c) x[c] -= Ls[j][c] * xj;
+            x[j] = x[j] / Ls[j][j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) x[c] -= Ls[j][c] * x[j];
         }
     }
-    __syncthreads();
-    constexpr int IT = kTileMax * kTileMax / kRowsPerCta;
-    const bool xrow = (a.X.rs == 1);
 #pragma unroll
-    for (int q = 0; q < IT; ++q) {
-        const int e = threadIdx.x + q * kRowsPerCta, p1 = e % kTileMax, p2 = e / kTileMax;
-        const int rr = xrow ? p1 : p2, cc = xrow ? p2 : p1;
-        if (rr < rows && cc < w) Xv(rr, cc) = Xs[rr][cc];
-    }
+    for (int c = 0; c < kTileMax; ++c)
+        if (c < w) a.X(r, c) = x[c];
 }
 
 template <typename T>
