@@ -435,8 +435,8 @@ def run_mixed(args):
                 ev[1].record(stream)
                 torch.cuda.synchronize(dev)
                 stages = {}
-                for name, t in lib.rfp_stage_times():
-                    stages[name] = stages.get(name, 0.0) + t
+                for stage, t in lib.rfp_stage_times():
+                    stages[stage] = stages.get(stage, 0.0) + t
                 lib.rfp_stage_timing(False)
             ms = ev[0].elapsed_time(ev[1])
             st = rfp.mixed_status(status.cpu().numpy().tobytes())

@@ -181,6 +181,59 @@ cudaError_t potrf_rec(cudaStream_t st, View<T> V, int64_t m, int32_t *info, int6
     return potrf_rec(st, V.sub(m1, m1), m2, info, base + m1);
 }
 
+// ---- FP32 solves with inverted diagonal blocks ----------------------------------------
+//
+// For repeated solves with one factor (iterative refinement): the diagonal
+// blocks of width kInvBlock are inverted once (inv_diag_blocks), and each
+// recursive solve ends in leaves that are in-place products with those
+// inverses instead of substitutions.  With few right-hand sides a leaf
+// substitution is one long dependency chain per right-hand side; the
+// product with the inverse has none.
+
+static int64_t split_point_inv(int64_t m)
+{
+    return std::max<int64_t>(kInvBlock, (m / 2 + kInvBlock - 1) / kInvBlock * kInvBlock);
+}
+
+static View<float> inv_block(const float *Inv, int64_t b)
+{
+    return View<float>{const_cast<float *>(Inv) + b * kInvBlock * kInvBlock, 1, kInvBlock};
+}
+
+// L X = B in place (B m x nrhs); block blk0 is the inverse of V's first diagonal block.
+cudaError_t trsm_left_lower_notrans_inv(cudaStream_t st, View<float> B, int64_t nrhs,
+                                        View<float> V, int64_t m, const float *Inv, int64_t blk0,
+                                        const int32_t *abort)
+{
+    if (m <= 0 || nrhs <= 0) return cudaSuccess;
+    if (m <= kInvBlock)   // B <- W B, W = L^{-1} lower
+        return gemm_nt(st, B, inv_block(Inv, blk0), B.t(), m, nrhs, m, 1.f, 0.f, MASK_NONE,
+                       MASK_LOWER, MASK_NONE, abort, true);
+    const int64_t m1 = split_point_inv(m), m2 = m - m1;
+    RFP_TRY(trsm_left_lower_notrans_inv(st, B, nrhs, V, m1, Inv, blk0, abort));
+    RFP_TRY(gemm_nt(st, B.sub(m1, 0), V.sub(m1, 0), B.t(), m2, nrhs, m1, -1.f, 1.f, MASK_NONE,
+                    MASK_NONE, MASK_NONE, abort));
+    return trsm_left_lower_notrans_inv(st, B.sub(m1, 0), nrhs, V.sub(m1, m1), m2, Inv,
+                                       blk0 + m1 / kInvBlock, abort);
+}
+
+// L^T X = B in place.
+cudaError_t trsm_left_lower_trans_inv(cudaStream_t st, View<float> B, int64_t nrhs, View<float> V,
+                                      int64_t m, const float *Inv, int64_t blk0,
+                                      const int32_t *abort)
+{
+    if (m <= 0 || nrhs <= 0) return cudaSuccess;
+    if (m <= kInvBlock)   // B <- W^T B
+        return gemm_nt(st, B, inv_block(Inv, blk0).t(), B.t(), m, nrhs, m, 1.f, 0.f, MASK_NONE,
+                       MASK_UPPER, MASK_NONE, abort, true);
+    const int64_t m1 = split_point_inv(m), m2 = m - m1;
+    RFP_TRY(trsm_left_lower_trans_inv(st, B.sub(m1, 0), nrhs, V.sub(m1, m1), m2, Inv,
+                                      blk0 + m1 / kInvBlock, abort));
+    RFP_TRY(gemm_nt(st, B, V.sub(m1, 0).t(), B.sub(m1, 0).t(), m1, nrhs, m2, -1.f, 1.f,
+                    MASK_NONE, MASK_NONE, MASK_NONE, abort));
+    return trsm_left_lower_trans_inv(st, B, nrhs, V, m1, Inv, blk0, abort);
+}
+
 // In-place W = L^{-1} on an m x m lower triangle V.  Right-looking over the
 // block columns p: with X = C_{p-1}^{-1} ... C_1^{-1} held where L was
 // consumed, step p applies C_p^{-1} (block column p of L):

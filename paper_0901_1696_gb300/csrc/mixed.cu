@@ -10,7 +10,8 @@
 //        RFP_PREC_TF32 / RFP_PREC_BF16: tcgen05 tensor cores (rfp_ssyrk_tc's
 //        kernel) on 512-wide panels converted to TF32 / BF16, FP32 accumulate;
 //      the diagonal blocks and the panel solves stay in FP32.
-//   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 solves, Section 4),
+//   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 solves, Section 4,
+//      whose 128-wide diagonal blocks are applied as inverses formed once),
 //      X += D (FP64), R = B - A X with A read from the FP64 RFP array (FP64),
 //      until max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol
 //      or max_iter steps.  Convergence is decided on the device: every later
@@ -24,12 +25,14 @@ constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 int64_t ldw_for(int64_t n) { return (n + 31) / 32 * 32; }
 size_t panel_elem(int prec) { return prec == RFP_PREC_BF16 ? 2 : 4; }
+size_t inv_elems(int64_t n) { return (size_t)((n + kInvBlock - 1) / kInvBlock) * kInvBlock * kInvBlock; }
 }  // namespace
 
 size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec)
 {
     size_t b = 0;
     b += up((size_t)ldw_for(n) * (size_t)n * sizeof(float));                  // W
+    b += up(inv_elems(n) * sizeof(float));                                    // Inv
     if (prec != RFP_PREC_FP32) b += up((size_t)n * kMixedPanel * panel_elem(prec));   // P
     b += up((size_t)n * (size_t)nrhs * sizeof(double));                       // R
     b += up((size_t)n * (size_t)nrhs * sizeof(float));                        // D
@@ -48,6 +51,8 @@ bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, Mi
     w->ldw = ldw_for(n);
     w->W = reinterpret_cast<float *>(p);
     p += up((size_t)w->ldw * (size_t)n * sizeof(float));
+    w->Inv = reinterpret_cast<float *>(p);
+    p += up(inv_elems(n) * sizeof(float));
     w->P = nullptr;
     if (prec != RFP_PREC_FP32) {
         w->P = p;
@@ -160,6 +165,7 @@ cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_
     if (prec == RFP_PREC_FP32) RFP_TRY(potrf_rec<float>(st, W, n, info, 0));
     else RFP_TRY(factor_tc(st, W, n, prec, w, info));
     RFP_TRY(stop_on_failure(st, status, w.tc_err, w.stop));
+    RFP_TRY(inv_diag_blocks(st, W, n, w.Inv, w.stop));
     stage_mark(st, "mixed.factor");
     // 3. refinement (step marks: "mixed.solve", "mixed.residual" per iteration)
     RFP_TRY(fill(st, X, n, nrhs, 0.0));
@@ -167,8 +173,8 @@ cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_
     stage_mark(st, "mixed.setup");
     for (int it = 0; it < max_iter; ++it) {
         RFP_TRY((convert<double, float>(st, R, D, n, nrhs, false, w.stop)));
-        RFP_TRY(trsm_left_lower_notrans_rec<float>(st, D, nrhs, W, n, w.stop));
-        RFP_TRY(trsm_left_lower_trans_rec<float>(st, D, nrhs, W, n, w.stop));
+        RFP_TRY(trsm_left_lower_notrans_inv(st, D, nrhs, W, n, w.Inv, 0, w.stop));
+        RFP_TRY(trsm_left_lower_trans_inv(st, D, nrhs, W, n, w.Inv, 0, w.stop));
         RFP_TRY(add_correction(st, X, D, n, nrhs, w.stop));
         stage_mark(st, "mixed.solve");
         RFP_TRY(residual(st, v, B, X, R, nrhs, w.stop, w.splits, w.splitk));

@@ -34,6 +34,7 @@ cudaError_t stop_on_failure(cudaStream_t st, rfp_mixed_status_t *status, const i
 struct MixedWork {
     float *W;          // FP32 working matrix / factor, ldw x n column-major (lower used)
     int64_t ldw;
+    float *Inv;        // inverses of the factor's diagonal blocks, ceil(n / kInvBlock) x kInvBlock^2
     void *P;           // low-precision panel, n x kPanel, K-contiguous
     double *R;         // FP64 residual, n x nrhs
     float *D;          // FP32 correction, n x nrhs

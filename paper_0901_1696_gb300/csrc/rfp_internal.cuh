@@ -202,6 +202,24 @@ template <typename T>
 cudaError_t trsm_left_lower_trans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
                                       int64_t m, const int32_t *abort);
 
+// FP32 solves that reuse inverted diagonal blocks, for many solves with one
+// factor.  inv_diag_blocks writes Inv[b] = (diagonal block b of width
+// kInvBlock of the m x m lower triangle V)^{-1} for b = 0 .. ceil(m /
+// kInvBlock) - 1, each kInvBlock x kInvBlock column-major with zeros above
+// the diagonal and outside the block's order (one launch, one CTA per block).
+// The solves take the block index of their first row.  kInvBlock is the
+// height of the large FP32 GEMM tile, so that a leaf product with a block
+// inverse runs in place in one row of CTAs.
+constexpr int64_t kInvBlock = 128;
+cudaError_t inv_diag_blocks(cudaStream_t st, View<float> V, int64_t m, float *Inv,
+                            const int32_t *abort);
+cudaError_t trsm_left_lower_notrans_inv(cudaStream_t st, View<float> B, int64_t nrhs,
+                                        View<float> V, int64_t m, const float *Inv, int64_t blk0,
+                                        const int32_t *abort);
+cudaError_t trsm_left_lower_trans_inv(cudaStream_t st, View<float> B, int64_t nrhs, View<float> V,
+                                      int64_t m, const float *Inv, int64_t blk0,
+                                      const int32_t *abort);
+
 // Blocked algorithms on the RFP blocks (Sections 3-5).
 template <typename T>
 cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info);

@@ -581,6 +581,60 @@ cudaError_t trtri_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Inverses of the kInvBlock-wide diagonal blocks of an FP32 lower triangle,
+// one CTA per block.  Thread c forms column c of W = L_bb^{-1} by forward
+// substitution on L_bb e_c, i.e. W(c, c) = 1 / L(c, c) and, for i > c,
+//   W(i, c) = -(sum_{p = c}^{i-1} L(i, p) W(p, c)) / L(i, i).
+// Both triangles sit in shared memory (2 x 128 x 129 floats).
+
+constexpr int kInvThreads = (int)kInvBlock, kInvLd = (int)kInvBlock + 1;
+
+__global__ void __launch_bounds__(kInvThreads) inv_diag_kernel(View<float> V, int64_t m,
+                                                                float *Inv, const int32_t *abort)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Ls = reinterpret_cast<float *>(smem_raw);
+    float *Ws = Ls + kInvBlock * kInvLd;
+    if (abort && *abort) return;
+    const int64_t k0 = (int64_t)blockIdx.x * kInvBlock;
+    const int w = (int)(m - k0 < kInvBlock ? m - k0 : kInvBlock);
+    const int t = threadIdx.x;
+    const bool rowfast = V.rs == 1;
+    View<float> Vb = V.sub(k0, k0);
+    for (int q = 0; q < (int)kInvBlock; ++q) {     // coalesced along V's unit-stride index
+        const int i = rowfast ? t : q, j = rowfast ? q : t;
+        Ls[i * kInvLd + j] = (i < w && j <= i) ? Vb(i, j) : 0.f;
+    }
+    __syncthreads();
+    const int c = t;
+    for (int i = 0; i < (int)kInvBlock; ++i) Ws[i * kInvLd + c] = 0.f;
+    if (c < w) {
+        Ws[c * kInvLd + c] = 1.f / Ls[c * kInvLd + c];
+        for (int i = c + 1; i < w; ++i) {
+            float s = 0.f;
+            for (int p = c; p < i; ++p) s += Ls[i * kInvLd + p] * Ws[p * kInvLd + c];
+            Ws[i * kInvLd + c] = -s / Ls[i * kInvLd + i];
+        }
+    }
+    __syncthreads();
+    float *out = Inv + (int64_t)blockIdx.x * kInvBlock * kInvBlock;   // column-major, ld kInvBlock
+    for (int j = 0; j < (int)kInvBlock; ++j) out[(int64_t)j * kInvBlock + t] = Ws[t * kInvLd + j];
+}
+
+cudaError_t inv_diag_blocks(cudaStream_t st, View<float> V, int64_t m, float *Inv,
+                            const int32_t *abort)
+{
+    if (m <= 0) return cudaSuccess;
+    const int smem = 2 * (int)kInvBlock * kInvLd * (int)sizeof(float);
+    cudaError_t e = set_smem_once<float>((const void *)inv_diag_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((m + kInvBlock - 1) / kInvBlock);
+    inv_diag_kernel<<<grid, kInvThreads, smem, st>>>(V, m, Inv, abort);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) lauum_tile_kernel(View<T> A, int w, const int32_t *abort)
 {

@@ -296,6 +296,35 @@ cudaError_t trtri_tile(cudaStream_t, View<T> A, int w, const int32_t *abort)
     return L.commit();
 }
 
+// One CTA per kInvBlock-wide diagonal block: reads the block's lower
+// triangle, writes the whole kInvBlock^2 slot of Inv.
+cudaError_t inv_diag_blocks(cudaStream_t, View<float> V, int64_t m, float *Inv, const int32_t *abort)
+{
+    if (m <= 0) return cudaSuccess;
+    const int64_t nb = kInvBlock, nblk = (m + nb - 1) / nb;
+    Launch L;
+    for (int64_t b = 0; b < nblk; ++b) {
+        L.cta = (int)b;
+        if (aborted(L, abort)) continue;
+        const int64_t k0 = b * nb, w = std::min(nb, m - k0);
+        std::vector<float> l(nb * nb, 0.f), x(nb * nb, 0.f);
+        for (int64_t i = 0; i < w; ++i)
+            for (int64_t j = 0; j <= i; ++j) l[i * nb + j] = L.rd(&V(k0 + i, k0 + j));
+        for (int64_t c = 0; c < w; ++c) {
+            x[c * nb + c] = 1.f / l[c * nb + c];
+            for (int64_t i = c + 1; i < w; ++i) {
+                float s = 0.f;
+                for (int64_t p = c; p < i; ++p) s += l[i * nb + p] * x[p * nb + c];
+                x[i * nb + c] = -s / l[i * nb + i];
+            }
+        }
+        float *out = Inv + b * nb * nb;
+        for (int64_t j = 0; j < nb; ++j)
+            for (int64_t i = 0; i < nb; ++i) L.wr(&out[j * nb + i], x[i * nb + j]);
+    }
+    return L.commit();
+}
+
 template <typename T>
 cudaError_t lauum_tile(cudaStream_t, View<T> A, int w, const int32_t *abort)
 {
