@@ -156,7 +156,12 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
  *   prec RFP_PREC_FP32: FP32 factorization on the FP32 FMA pipes;
  *   prec RFP_PREC_TF32 / RFP_PREC_BF16: FP32 storage, the SYRK updates of
  *        512-wide panels on tcgen05 tensor cores from TF32 / BF16 operands
- *        with FP32 accumulation.
+ *        with FP32 accumulation;
+ *   prec RFP_PREC_TF32X3: as RFP_PREC_TF32, but each panel value is split
+ *        into two TF32 parts (hi = tf32(x), lo = tf32(x - hi), both rounded
+ *        to nearest) and the update sums the three products
+ *        hi hi^T + lo hi^T + hi lo^T on the tensor cores: FP32's 24 bits per
+ *        operand instead of TF32's 11 (panel buffer four times larger).
  * Refinement: X = 0, R = B, then up to max_iter times D = (L L^T)^{-1} R in
  * FP32, X += D in FP64, R = B - A X in FP64 from arf; it stops as soon as
  * max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol, decided on
@@ -173,6 +178,7 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
  * 10 prec, 11 max_iter, 12 tol, 13 work, 14 work_bytes, 15 status, 16 stream.
  */
 #define RFP_PREC_FP32 2
+#define RFP_PREC_TF32X3 3
 typedef struct rfp_mixed_status {
     int32_t info, iterations, converged, tc_error;
     double backward_error;
@@ -196,7 +202,9 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
  * 11 max_iter, 12 tol, 13 status, 14 stream.  Problems whose
  * rfp_dpfsv_mixed_workspace exceeds rfp_dpfsv_mixed_noalloc_capacity() are
  * rejected: -3 if n does not fit even with nrhs = 1, else -4 (for example
- * n = 2048 with nrhs <= 256 fits in every precision).
+ * n = 2048 with nrhs <= 256 fits in the FP32, TF32 and BF16 modes; the
+ * split-TF32 mode, whose panel buffer is four times larger, fits n = 1664
+ * with nrhs <= 256).
  * All calls share the array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race on it; serialize them.  The array keeps
  * the previous call's contents; the solve itself clears what must start at

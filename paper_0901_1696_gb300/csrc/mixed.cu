@@ -9,6 +9,8 @@
 //        RFP_PREC_FP32: FP32 FMA (SIMT), the s-precision kernels,
 //        RFP_PREC_TF32 / RFP_PREC_BF16: tcgen05 tensor cores (rfp_ssyrk_tc's
 //        kernel) on 512-wide panels converted to TF32 / BF16, FP32 accumulate;
+//        RFP_PREC_TF32X3: the same kernel on a split panel P = hi + lo (both
+//        TF32), C -= hi hi^T + lo hi^T + hi lo^T (three products, one launch);
 //      the diagonal blocks and the panel solves stay in FP32.
 //   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 solves, Section 4,
 //      whose 128-wide diagonal blocks are applied as inverses formed once),
@@ -33,7 +35,7 @@ size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec)
     size_t b = 0;
     b += up((size_t)ldw_for(n) * (size_t)n * sizeof(float));                  // W
     b += up(inv_elems(n) * sizeof(float));                                    // Inv
-    if (prec != RFP_PREC_FP32) b += up((size_t)n * kMixedPanel * panel_elem(prec));   // P
+    if (prec != RFP_PREC_FP32) b += up((size_t)n * panel_cols(prec) * panel_elem(prec));   // P
     b += up((size_t)n * (size_t)nrhs * sizeof(double));                       // R
     b += up((size_t)n * (size_t)nrhs * sizeof(float));                        // D
     b += up((size_t)nrhs * sizeof(double));                                   // berr
@@ -56,7 +58,7 @@ bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, Mi
     w->P = nullptr;
     if (prec != RFP_PREC_FP32) {
         w->P = p;
-        p += up((size_t)n * kMixedPanel * panel_elem(prec));
+        p += up((size_t)n * panel_cols(prec) * panel_elem(prec));
     }
     w->R = reinterpret_cast<double *>(p);
     p += up((size_t)n * (size_t)nrhs * sizeof(double));
@@ -92,16 +94,26 @@ static cudaError_t factor_tc(cudaStream_t st, View<float> W, int64_t n, int prec
         if (j1 >= n) break;
         const int64_t m = n - j1;
         RFP_TRY(trsm_right_lower_trans_rec<float>(st, W.sub(j1, j0), m, W.sub(j0, j0), nb, info));
-        // panel -> K-contiguous low-precision copy P (row r, column k at P[r*512 + k])
+        // panel -> K-contiguous low-precision copy P (row r, column k at P[r*pitch + k])
         if (prec == RFP_PREC_BF16) {
             View<__nv_bfloat16> P{static_cast<__nv_bfloat16 *>(w.P), kMixedPanel, 1};
             RFP_TRY((convert<float, __nv_bfloat16>(st, W.sub(j1, j0), P, m, nb, false, info)));
-        } else {
+        } else if (prec == RFP_PREC_TF32) {
             View<float> P{static_cast<float *>(w.P), kMixedPanel, 1};
             RFP_TRY((convert<float, float>(st, W.sub(j1, j0), P, m, nb, false, info)));
+        } else {
+            RFP_TRY(split_tf32(st, W.sub(j1, j0), static_cast<float *>(w.P), m, nb, kMixedPanel, info));
         }
-        RFP_TRY(tc_gemm_nt(st, prec, w.P, m, kMixedPanel, 0, w.P, m, kMixedPanel, 0, W.sub(j1, j1),
-                           m, m, nb, -1.0f, 1.0f, MASK_LOWER, w.tc_err));
+        if (prec == RFP_PREC_TF32X3) {
+            // A = segments 1..3 = [hi | lo | hi], B = segments 0..2 = [hi | hi | lo]
+            const float *Q = static_cast<const float *>(w.P);
+            RFP_TRY(tc_gemm_nt(st, RFP_PREC_TF32, Q + kMixedPanel, m, 4 * kMixedPanel, 0, Q, m,
+                               4 * kMixedPanel, 0, W.sub(j1, j1), m, m, 3 * kMixedPanel, -1.0f, 1.0f,
+                               MASK_LOWER, w.tc_err));
+        } else {
+            RFP_TRY(tc_gemm_nt(st, prec, w.P, m, kMixedPanel, 0, w.P, m, kMixedPanel, 0,
+                               W.sub(j1, j1), m, m, nb, -1.0f, 1.0f, MASK_LOWER, w.tc_err));
+        }
     }
     return cudaSuccess;
 }

@@ -20,6 +20,10 @@ struct RfpViews {
 template <typename Ts, typename Td>
 cudaError_t convert(cudaStream_t st, View<Ts> src, View<Td> dst, int64_t rows, int64_t cols,
                     bool tri, const int32_t *stop);
+// Q rows of four K-segments [hi | hi | lo | hi] (width seg) of the rows x cols
+// FP32 block src, hi = x truncated to TF32, lo = x - hi.
+cudaError_t split_tf32(cudaStream_t st, View<float> src, float *Q, int64_t rows, int64_t cols,
+                       int64_t seg, const int32_t *stop);
 cudaError_t add_correction(cudaStream_t st, View<double> X, View<float> D, int64_t n, int64_t nrhs,
                            const int32_t *stop);
 cudaError_t fill(cudaStream_t st, View<double> X, int64_t n, int64_t nrhs, double v);
@@ -55,6 +59,9 @@ inline int residual_splits(int64_t n)
 }
 
 constexpr int64_t kMixedPanel = 512;   // panel width of the tensor-core factorization
+
+// Columns of one panel row in P: the split-TF32 mode keeps four segments.
+inline int64_t panel_cols(int prec) { return prec == RFP_PREC_TF32X3 ? 4 * kMixedPanel : kMixedPanel; }
 
 size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec);
 bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, MixedWork *w);

@@ -65,6 +65,64 @@ cudaError_t convert(cudaStream_t st, View<Ts> src, View<Td> dst, int64_t rows, i
     return cudaGetLastError();
 }
 
+// Rounding of an FP32 value to TF32 (10 stored mantissa bits), to nearest
+// with ties away from zero: add half a TF32 unit to the magnitude, clear the
+// 13 low mantissa bits.  Finite inputs only (the panels are bounded).
+__device__ __forceinline__ float round_tf32(float x)
+{
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+
+// Split of an FP32 panel for three-product TF32 updates: hi = tf32(x),
+// lo = tf32(x - hi) (x - hi is exact in FP32 by Sterbenz's lemma), so
+// |x - hi - lo| <= 2^-24 |x|: hi + lo carries FP32's precision.  Row r of Q
+// holds the four K-segments [hi | hi | lo | hi] of width seg, so that with
+// A = Q + seg and B = Q a single K = 3 seg product sums
+// hi hi^T + lo hi^T + hi lo^T (the dropped lo lo^T is below 2^-22 |x y|).
+__global__ void __launch_bounds__(256) split_tf32_kernel(View<float> src, float *Q, int64_t rows,
+                                                         int64_t cols, int64_t seg,
+                                                         const int32_t *stop)
+{
+    __shared__ float tile[kCvtTile][kCvtTile + 1];
+    if (stop && *stop) return;
+    const int64_t r0 = (int64_t)blockIdx.y * kCvtTile, c0 = (int64_t)blockIdx.x * kCvtTile;
+    const int fast = threadIdx.x % kCvtTile, slow0 = threadIdx.x / kCvtTile;
+    const bool srow = src.rs == 1;
+#pragma unroll
+    for (int q = 0; q < kCvtTile / 8; ++q) {
+        const int sl = slow0 + 8 * q;
+        const int ti = srow ? fast : sl, tj = srow ? sl : fast;
+        if (r0 + ti < rows && c0 + tj < cols) tile[ti][tj] = src(r0 + ti, c0 + tj);
+    }
+    __syncthreads();
+    const int64_t pitch = 4 * seg;
+#pragma unroll
+    for (int q = 0; q < kCvtTile / 8; ++q) {
+        const int ti = slow0 + 8 * q, tj = fast;          // k (column) is Q's unit stride
+        const int64_t r = r0 + ti, k = c0 + tj;
+        if (r < rows && k < cols) {
+            const float x = tile[ti][tj];
+            const float hi = round_tf32(x);
+            const float lo = round_tf32(x - hi);
+            float *row = Q + r * pitch + k;
+            row[0] = hi;
+            row[seg] = hi;
+            row[2 * seg] = lo;
+            row[3 * seg] = hi;
+        }
+    }
+}
+
+cudaError_t split_tf32(cudaStream_t st, View<float> src, float *Q, int64_t rows, int64_t cols,
+                       int64_t seg, const int32_t *stop)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((cols + kCvtTile - 1) / kCvtTile), (unsigned)((rows + kCvtTile - 1) / kCvtTile));
+    split_tf32_kernel<<<grid, 256, 0, st>>>(src, Q, rows, cols, seg, stop);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // X += (double) D, n x nrhs.
 __global__ void axpy_kernel(View<double> X, View<float> D, int64_t n, int64_t nrhs,
                             const int32_t *stop)

@@ -12,8 +12,8 @@
 //   * every GPU that loads the library holds the 32 MiB array until the
 //     process exits;
 //   * problems whose workspace (rfp_dpfsv_mixed_workspace) exceeds 32 MiB are
-//     rejected (for example n = 2048 with nrhs up to 256 fits, in every
-//     precision);
+//     rejected (for example n = 2048 with nrhs up to 256 fits in the FP32,
+//     TF32 and BF16 modes, n = 1664 in the split-TF32 mode);
 //   * all calls share the one array: calls whose work overlaps on the GPU (two
 //     streams, or two host threads) race on it and give wrong results;
 //     serialize them;

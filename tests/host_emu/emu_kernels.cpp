@@ -410,7 +410,12 @@ cudaError_t tc_gemm_nt(cudaStream_t, int kind, const void *A, int64_t a_rows, in
             memcpy(&f, &bits, 4);
             return f;
         }
-        return L.rd((const float *)base + r * pitch + k);
+        float f = L.rd((const float *)base + r * pitch + k);   // kind::tf32 reads 19 bits
+        uint32_t bits;
+        memcpy(&bits, &f, 4);
+        bits &= 0xffffe000u;
+        memcpy(&f, &bits, 4);
+        return f;
     };
     const int64_t gm = (M + T - 1) / T, gn = (N + T - 1) / T;
     const bool lower_tiles = cmode == MASK_LOWER && M == N;
@@ -476,6 +481,38 @@ cudaError_t convert(cudaStream_t, View<Ts> src, View<Td> dst, int64_t rows, int6
                 for (int64_t j = c0; j < std::min(cols, c0 + T); ++j) {
                     if (tri && i < j) continue;
                     put(L, &dst(i, j), L.rd(&src(i, j)));
+                }
+        }
+    return L.commit();
+}
+
+cudaError_t split_tf32(cudaStream_t, View<float> src, float *Q, int64_t rows, int64_t cols,
+                       int64_t seg, const int32_t *stop)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    Launch L;
+    const int64_t T = 32, gy = (rows + T - 1) / T, gx = (cols + T - 1) / T;
+    for (int64_t by = 0; by < gy; ++by)
+        for (int64_t bx = 0; bx < gx; ++bx) {
+            L.cta = (int)(by * gx + bx);
+            if (aborted(L, stop)) continue;
+            for (int64_t r = by * T; r < std::min(rows, by * T + T); ++r)
+                for (int64_t k = bx * T; k < std::min(cols, bx * T + T); ++k) {
+                    auto tf32 = [](float v) {    // to nearest, ties away from zero
+                        uint32_t bits;
+                        memcpy(&bits, &v, 4);
+                        bits = (bits + 0x1000u) & 0xffffe000u;
+                        memcpy(&v, &bits, 4);
+                        return v;
+                    };
+                    const float x = L.rd(&src(r, k));
+                    const float hi = tf32(x);
+                    const float lo = tf32(x - hi);
+                    float *row = Q + r * 4 * seg + k;
+                    L.wr(row, hi);
+                    L.wr(row + seg, hi);
+                    L.wr(row + 2 * seg, lo);
+                    L.wr(row + 3 * seg, hi);
                 }
         }
     return L.commit();

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 rfp = pytest.importorskip("paper_0901_1696_gb300.binding")
 
-PRECS = {"fp32": 2, "tf32": 1, "bf16": 0}
+PRECS = {"fp32": 2, "tf32": 1, "bf16": 0, "tf32x3": 3}
 
 
 def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
@@ -40,7 +40,7 @@ def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
     return X, st
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32", "bf16"])
 @pytest.mark.parametrize("transr,uplo,n", [("N", "L", 100), ("T", "U", 513), ("N", "U", 1300),
                                            ("T", "L", 2100)])
 def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
@@ -56,7 +56,7 @@ def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
 
 
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32", "bf16"])
 def test_mixed_conditioning(prec, kappa):
     n = 1200
     A = gen.spd_spectrum(n, seed=7, kappa=kappa)
@@ -64,7 +64,7 @@ def test_mixed_conditioning(prec, kappa):
     X, st = solve_mixed("N", "L", A, B, PRECS[prec], max_iter=40)
     assert st["tc_error"] == 0
     bwd = oracle.solve_backward_error(A, X, B) if st["info"] == 0 else np.inf
-    u_f = {"fp32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
+    u_f = {"fp32": 2.0 ** -24, "tf32x3": 2.0 ** -21, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
     if st["converged"]:
         assert st["backward_error"] <= 1e-15 and bwd <= 1e-14, (st, bwd)
     if kappa * u_f * 100 < 1:         # well inside the convergence condition
@@ -91,7 +91,22 @@ def test_mixed_argument_checks():
     assert rfp.rfp_dpfsv_mixed_workspace(n, nrhs, 9) == 0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_tf32x3_refines_like_fp32():
+    """The split-TF32 updates carry about 22 bits per operand: at kappa = 1e4
+    the refinement needs no more than one step beyond the FP32 factor's and
+    fewer than the plain TF32 factor's."""
+    n = 2100
+    A = gen.spd_spectrum(n, seed=11, kappa=1e4)
+    B = gen.rhs(n, 8, seed=12)
+    its = {}
+    for name in ["fp32", "tf32x3", "tf32"]:
+        _, st = solve_mixed("N", "L", A, B, PRECS[name], max_iter=40)
+        assert st["info"] == 0 and st["converged"] == 1, (name, st)
+        its[name] = st["iterations"]
+    assert its["tf32x3"] <= its["fp32"] + 1 and its["tf32x3"] < its["tf32"], its
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32"])
 def test_mixed_large_split_k_residual(prec):
     """n = 8200: the refinement's FP64 residual products run split along K
     (two chunks) through the workspace; the solve must still meet the bar."""

@@ -67,7 +67,10 @@ def test_no_alloc_rejects_problems_beyond_its_scratch():
         rfp.rfp_dpfsv_mixed_noalloc("N", "L", big, 1, 16, 16, big, 16, big, 2, 5, 1e-14, st)
     assert e.value.status == -3
     n = 2048
-    assert rfp.rfp_dpfsv_mixed_workspace(n, 256, 0) <= cap
+    for prec in (0, 1, 2):
+        assert rfp.rfp_dpfsv_mixed_workspace(n, 256, prec) <= cap
+    assert rfp.rfp_dpfsv_mixed_workspace(1664, 256, 3) <= cap
+    assert rfp.rfp_dpfsv_mixed_workspace(n, 1, 3) > cap
     assert rfp.rfp_dpfsv_mixed_workspace(n, 4096, 2) > cap
     with pytest.raises(rfp.RfpError) as e:
         rfp.rfp_dpfsv_mixed_noalloc("N", "L", n, 4096, 16, 16, n, 16, n, 2, 5, 1e-14, st)
