@@ -32,6 +32,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# dram__bytes_read.sum + dram__bytes_write.sum of the PFTRF step-3 launch at
+# n = 16384 (one ncu capture of the unchanged kernel, summarized under
+# profiles/): 20.29 GB + 0.281 GB.
+SYRK_TRAFFIC_N16384 = 20.57e9
 METRIC = "PFTRF+PFTRS TFLOP/s & % peak; served solves/s, p50/p99 at ≤1e-12 bwd err"
 LAYOUTS = [(t, u) for t in "NT" for u in "LU"]
 
@@ -298,7 +302,10 @@ def run_ours(args, rank: int, world: int):
                    "l2": "inputs larger than L2 (RFP 1.07 GB); no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": SYRK_TRAFFIC_N16384 if n == 16384 else None,
+                     "traffic_source": "profiles/gemm_nt_syrk_n16384_traffic.md (ncu, one launch "
+                                       "at n = 16384)" if n == 16384 else None,
                      "kernel": "gemm_nt_kernel<double>: PFTRF step 3 (T2 -= S S^T), one launch",
                      "peak_source": "FP64 FMA pipe: 152 SMs x units x 2 x median SM clock"},
         "breakdown": {

@@ -12,8 +12,9 @@
 //        RFP_PREC_TF32X3: the same kernel on a split panel P = hi + lo (both
 //        TF32), C -= hi hi^T + lo hi^T + hi lo^T (three products, one launch);
 //      the diagonal blocks and the panel solves stay in FP32.
-//   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 solves, Section 4,
-//      whose 128-wide diagonal blocks are applied as inverses formed once),
+//   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 block solves of
+//      Section 4, one launch each, the 128-wide diagonal blocks applied as
+//      inverses formed once),
 //      X += D (FP64), R = B - A X with A read from the FP64 RFP array (FP64),
 //      until max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol
 //      or max_iter steps.  Convergence is decided on the device: every later
@@ -40,6 +41,7 @@ size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec)
     b += up((size_t)n * (size_t)nrhs * sizeof(float));                        // D
     b += up((size_t)nrhs * sizeof(double));                                   // berr
     b += up(sizeof(double)) + up(sizeof(int32_t)) + up(sizeof(int32_t));      // anorm, stop, tc_err
+    b += up(wavefront_sync_words(n, nrhs) * sizeof(int32_t));                 // solve sync
     if (residual_splits(n) > 1)
         b += up((size_t)residual_splits(n) * (size_t)n * (size_t)nrhs * sizeof(double));
     return b;
@@ -72,6 +74,8 @@ bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, Mi
     p += up(sizeof(int32_t));
     w->tc_err = reinterpret_cast<int32_t *>(p);
     p += up(sizeof(int32_t));
+    w->sync = reinterpret_cast<int32_t *>(p);
+    p += up(wavefront_sync_words(n, nrhs) * sizeof(int32_t));
     w->splits = residual_splits(n);
     w->splitk = w->splits > 1 ? reinterpret_cast<double *>(p) : nullptr;
     return true;
@@ -185,8 +189,9 @@ cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_
     stage_mark(st, "mixed.setup");
     for (int it = 0; it < max_iter; ++it) {
         RFP_TRY((convert<double, float>(st, R, D, n, nrhs, false, w.stop)));
-        RFP_TRY(trsm_left_lower_notrans_inv(st, D, nrhs, W, n, w.Inv, 0, w.stop));
-        RFP_TRY(trsm_left_lower_trans_inv(st, D, nrhs, W, n, w.Inv, 0, w.stop));
+        RFP_TRY(trsm_wavefront(st, W, n, w.Inv, w.D, n, nrhs, false, w.sync, w.tc_err, w.stop));
+        RFP_TRY(trsm_wavefront(st, W, n, w.Inv, w.D, n, nrhs, true, w.sync, w.tc_err, w.stop));
+        RFP_TRY(stop_on_failure(st, status, w.tc_err, w.stop));
         RFP_TRY(add_correction(st, X, D, n, nrhs, w.stop));
         stage_mark(st, "mixed.solve");
         RFP_TRY(residual(st, v, B, X, R, nrhs, w.stop, w.splits, w.splitk));

@@ -45,7 +45,8 @@ struct MixedWork {
     double *berr;      // per-column backward errors (nrhs)
     double *anorm;     // ||A||_inf
     int32_t *stop;     // refinement stop word
-    int32_t *tc_err;   // tensor-core kernel error word
+    int32_t *tc_err;   // tensor-core / solve kernel error word
+    int32_t *sync;     // task counter and ready flags of the one-launch solves
     double *splitk;    // split-K slices of the residual products (residual_splits x n x nrhs)
     int splits;
 };

@@ -220,6 +220,19 @@ cudaError_t trsm_left_lower_trans_inv(cudaStream_t st, View<float> B, int64_t nr
                                       int64_t m, const float *Inv, int64_t blk0,
                                       const int32_t *abort);
 
+// One-launch FP32 block triangular solve (trsm_wavefront.cu): L X = B
+// (trans = false) or L^T X = B (trans = true) in place on X (n x nrhs,
+// column-major, ldx), L the n x n lower triangle of the column-major view Lv
+// (unit row stride, column stride a multiple of 4, 16-byte aligned) and Inv
+// its inverted diagonal blocks from inv_diag_blocks.  sync: device scratch of
+// wavefront_sync_words(n, nrhs) int32 (cleared by the call, stream-ordered);
+// err: error word, set to 4 if a wait between tasks expired; stop: if set at
+// launch, nothing is done.
+size_t wavefront_sync_words(int64_t n, int64_t nrhs);
+cudaError_t trsm_wavefront(cudaStream_t st, View<float> Lv, int64_t n, const float *Inv, float *X,
+                           int64_t ldx, int64_t nrhs, bool trans, int32_t *sync, int32_t *err,
+                           const int32_t *stop);
+
 // Blocked algorithms on the RFP blocks (Sections 3-5).
 template <typename T>
 cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info);

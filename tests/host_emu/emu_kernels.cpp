@@ -50,16 +50,35 @@ struct Launch {
     std::vector<std::pair<void *, float>> pend_f;
     std::vector<std::pair<void *, uint16_t>> pend_b;
     int cta = 0;
+    // Ordered launches (CTAs that hand results to each other through ready
+    // flags) run their CTAs in ticket order with writes applied at once;
+    // only bounds are checked.
+    bool ordered = false;
     template <typename T>
     T rd(const T *p)
     {
         if (!in_bounds(p, sizeof(T))) { violation("out-of-bounds read", p); return T(0); }
+        if (ordered) return *p;
         auto &v = readers[(uintptr_t)p];
         if (v.empty() || v.back() != cta) v.push_back(cta);
         return *p;
     }
-    void wr(double *p, double x) { wr_any(p, sizeof(double)); pend_d.push_back({p, x}); }
-    void wr(float *p, float x) { wr_any(p, sizeof(float)); pend_f.push_back({p, x}); }
+    void wr(double *p, double x)
+    {
+        if (ordered) { if (in_bounds(p, 8)) *p = x; else violation("out-of-bounds write", p); return; }
+        wr_any(p, sizeof(double)); pend_d.push_back({p, x});
+    }
+    void wr(float *p, float x)
+    {
+        if (ordered) { if (in_bounds(p, 4)) *p = x; else violation("out-of-bounds write", p); return; }
+        wr_any(p, sizeof(float)); pend_f.push_back({p, x});
+    }
+    void wr(int32_t *p, int32_t x)
+    {
+        if (!in_bounds(p, 4)) { violation("out-of-bounds write", p); return; }
+        if (!ordered) violation("int write outside an ordered launch", p);
+        *p = x;
+    }
     void wr_any(void *p, size_t sz)
     {
         if (!in_bounds(p, sz)) { violation("out-of-bounds write", p); return; }
@@ -293,6 +312,67 @@ cudaError_t trtri_tile(cudaStream_t, View<T> A, int w, const int32_t *abort)
     }
     for (int i = 0; i < w; ++i)
         for (int j = 0; j <= i; ++j) L.wr(&A(i, j), x[i * w + j]);
+    return L.commit();
+}
+
+// One-launch block triangular solve: tasks (block row, 16-column group) in
+// ticket order; each reads its rows of X, the blocks of L before (forward)
+// or after (backward) its diagonal block, the finished X blocks of the
+// earlier tasks and its inverted diagonal block, and writes its X block and
+// ready flag.
+size_t wavefront_sync_words(int64_t n, int64_t nrhs)
+{
+    const int64_t nb = (n + kInvBlock - 1) / kInvBlock, ng = (nrhs + 15) / 16;
+    return (size_t)(1 + nb * ng);
+}
+
+cudaError_t trsm_wavefront(cudaStream_t, View<float> Lv, int64_t n, const float *Inv, float *X,
+                           int64_t ldx, int64_t nrhs, bool trans, int32_t *sync, int32_t *err,
+                           const int32_t *stop)
+{
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    if (Lv.rs != 1 || Lv.cs % 4 != 0 || (uintptr_t)Lv.p % 16 || (uintptr_t)Inv % 16)
+        return cudaErrorInvalidValue;
+    const int64_t B = kInvBlock, nb = (n + B - 1) / B, ng = (nrhs + 15) / 16;
+    Launch L;
+    L.ordered = true;
+    for (size_t w = 0; w < wavefront_sync_words(n, nrhs); ++w) L.wr(sync + w, 0);   // the memset
+    (void)err;
+    if (aborted(L, stop)) return L.commit();
+    for (int64_t t = 0; t < nb * ng; ++t) {
+        L.cta = (int)t;
+        L.wr(sync, (int32_t)(t + 1));                       // ticket counter
+        const int64_t g = t % ng, step = t / ng, i = trans ? nb - 1 - step : step;
+        const int64_t r0 = i * B, rows = std::min(B, n - r0), c0 = g * 16,
+                      cols = std::min<int64_t>(16, nrhs - c0);
+        std::vector<float> acc(rows * cols);
+        for (int64_t c = 0; c < cols; ++c)
+            for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = L.rd(&X[(c0 + c) * ldx + r0 + r]);
+        const int64_t jlo = trans ? i + 1 : 0, jhi = trans ? nb : i;
+        for (int64_t jj = jlo; jj < jhi; ++jj) {
+            const int64_t j = trans ? nb - 1 - (jj - jlo) : jj;   // solve order
+            if (L.rd(sync + 1 + j * ng + g) != 1) violation("X block read before its flag", sync);
+            const int64_t kv = std::min(B, n - j * B);
+            for (int64_t c = 0; c < cols; ++c)
+                for (int64_t r = 0; r < rows; ++r) {
+                    float s = acc[c * rows + r];
+                    for (int64_t k = 0; k < kv; ++k) {
+                        const float a = trans ? L.rd(&Lv(j * B + k, r0 + r)) : L.rd(&Lv(r0 + r, j * B + k));
+                        s -= a * L.rd(&X[(c0 + c) * ldx + j * B + k]);
+                    }
+                    acc[c * rows + r] = s;
+                }
+        }
+        const float *W = Inv + i * B * B;                    // column-major, ld B
+        for (int64_t c = 0; c < cols; ++c)
+            for (int64_t r = 0; r < rows; ++r) {
+                float s = 0.f;
+                for (int64_t k = 0; k < rows; ++k)
+                    s += (trans ? L.rd(&W[r * B + k]) : L.rd(&W[k * B + r])) * acc[c * rows + k];
+                L.wr(&X[(c0 + c) * ldx + r0 + r], s);
+            }
+        L.wr(sync + 1 + i * ng + g, 1);
+    }
     return L.commit();
 }
 

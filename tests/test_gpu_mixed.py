@@ -116,3 +116,17 @@ def test_mixed_large_split_k_residual(prec):
     X, st = solve_mixed("T", "U", A, B, PRECS[prec])
     assert st["info"] == 0 and st["tc_error"] == 0 and st["converged"] == 1, st
     assert oracle.solve_backward_error(A, X, B) <= 1e-14
+
+
+@pytest.mark.parametrize("transr,uplo,n,nrhs", [("N", "L", 1000, 20), ("T", "U", 4097, 64),
+                                                ("N", "U", 129, 1)])
+def test_one_step_is_one_fp32_solve(transr, uplo, n, nrhs):
+    """max_iter = 1: X = (L L^T)^{-1} fl32(B) with the FP32 factor, i.e. the
+    one-launch block solves alone, against the oracle's FP64 solve (forward
+    error of an FP32 solve of a well-conditioned system)."""
+    A, rng = gen.spd_bbt(n, seed=n + 3, return_rng=True)
+    B = gen.rhs(n, nrhs, rng)
+    X, st = solve_mixed(transr, uplo, A, B, PRECS["fp32"], max_iter=1)
+    assert st["info"] == 0 and st["tc_error"] == 0 and st["iterations"] == 1, st
+    ref = oracle.pftrs(transr, uplo, n, oracle.pftrf(transr, uplo, n, oracle.pack(transr, uplo, A))[0], B)
+    assert np.max(np.abs(X - ref)) <= 1e-4 * np.max(np.abs(ref))

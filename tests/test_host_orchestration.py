@@ -253,3 +253,30 @@ def test_emulated_mixed_precision_solve(emu_lib, prec, transr, uplo, n):
     assert st["converged"] == 1 and 1 <= st["iterations"] <= 6, st
     assert oracle.solve_backward_error(A, X[:n], B) <= 1e-15
     np.testing.assert_array_equal(arf, oracle.pack(transr, uplo, A))   # A untouched
+
+
+@pytest.mark.parametrize("transr,uplo,n", [("N", "L", 600), ("T", "U", 257)])
+def test_emulated_one_step_is_one_fp32_solve(emu_lib, transr, uplo, n):
+    """max_iter = 1 returns X = (L L^T)^{-1} fl32(B) from the FP32 factor: the
+    block solves alone (several 128-row blocks, a ragged last block, two
+    column groups of which the second is ragged) against the oracle's solve."""
+    from paper_0901_1696_gb300.binding import mixed_status
+    emu = emu_lib
+    emu.lib.emu_set_sms(152)
+    A, rng = gen.spd_bbt(n, seed=n + 1, return_rng=True)
+    nrhs = 20
+    B = gen.rhs(n, nrhs, rng)
+    arf = oracle.pack(transr, uplo, A)
+    X = np.zeros((n, nrhs), order="F")
+    wbytes = emu.rfp_dpfsv_mixed_workspace(n, nrhs, 2)
+    work = _aligned_bytes(wbytes)
+    status = _aligned_bytes(24, 8)
+    Bc = np.asfortranarray(B)
+    _register(emu, arf, Bc, X, work, status)
+    emu.rfp_dpfsv_mixed(transr, uplo, n, nrhs, arf, Bc, n, X, n, 2, 1, 1e-15, work, wbytes,
+                        status, 0)
+    _ok(emu)
+    st = mixed_status(status.tobytes())
+    assert st["info"] == 0 and st["tc_error"] == 0 and st["iterations"] == 1, st
+    ref = oracle.pftrs(transr, uplo, n, oracle.pftrf(transr, uplo, n, arf)[0], B)
+    assert np.max(np.abs(X - ref)) <= 1e-4 * np.max(np.abs(ref))
