@@ -61,7 +61,7 @@ def parse():
                         "reference step)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["fp64", "mixed"], default="fp64",
+    p.add_argument("--mode", choices=["fp64", "mixed", "batched"], default="fp64",
                    help="fp64: the FP64 hot path (default line); mixed: the mixed-precision "
                         "solve at n = 32768 against the FP64 path (its own line)")
     p.add_argument("--mixed-n", type=int, default=32768)
@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--kappas", default="1e2,1e4,1e6")
     p.add_argument("--precs", default="fp32,tf32x3,tf32,bf16")
     p.add_argument("--max-iter", type=int, default=30, help="refinement steps (mixed mode)")
+    p.add_argument("--batch", type=int, default=4096, help="batched mode: matrices per batch")
+    p.add_argument("--retune", action="store_true",
+                   help="batched mode: re-run the panel-width autotuner even if cached")
     p.add_argument("--no-fp64-ref", action="store_true",
                    help="mixed mode: skip the FP64 PFTRF + PFTRS reference run")
     return p.parse_args()
@@ -373,16 +376,25 @@ def e2e_leg(args, lib, A, B0, dev, stream):
             "d2h_bytes_per_step": n * nrhs * 8, "ms_per_step": ms}
 
 
+def sampled_backward_error(A, X, B):
+    """max_j ||b_j - A x_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) with a
+    plain host FP64 residual (numpy) on the given columns."""
+    import numpy as np
+    R = B - A @ X
+    anorm = float(np.max(np.sum(np.abs(A), axis=1)))
+    den = anorm * np.max(np.abs(X), axis=0) + np.max(np.abs(B), axis=0)
+    return float(np.max(np.max(np.abs(R), axis=0) / den))
+
+
 def run_mixed(args):
     """Mixed-precision solve (low-precision factor + FP64 refinement) of an
     n = 32768 FP64 RFPF system with nrhs = 64, for each condition number and
     precision, against FP64 PFTRF + PFTRS on the same GPU.  Errors: the
-    device's backward error, the oracle's compensated backward error on 4
-    sampled columns, and the max-norm distance to the FP64 solution."""
+    device's backward error, a host FP64 residual on 4 sampled columns, and
+    the max-norm distance to the FP64 solution."""
     import numpy as np
     import torch
 
-    import oracle
     import rfp_inputs as gen
     from paper_0901_1696_gb300 import binding as rfp
     from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
@@ -427,8 +439,7 @@ def run_mixed(args):
             X64h = X64.cpu().numpy().T
             fp64.append({"kappa": kappa, "ms": ms64, "info": int(info.item()),
                          "tflops": (pftrf_flops(n) + pftrs_flops(n, nrhs)) / (ms64 * 1e-3) / 1e12,
-                         "oracle_bwd_sampled": oracle.solve_backward_error(Ah, X64h[:, sample],
-                                                                           Bh[:, sample])})
+                         "bwd_sampled": sampled_backward_error(Ah, X64h[:, sample], Bh[:, sample])})
             del fac, X64
         for name in args.precs.split(","):
             prec = precs[name]
@@ -457,7 +468,7 @@ def run_mixed(args):
                 "iterations": st["iterations"], "converged": st["converged"],
                 "info": st["info"], "tc_error": st["tc_error"],
                 "backward_error": st["backward_error"],
-                "oracle_bwd_sampled": oracle.solve_backward_error(Ah, Xh[:, sample], Bh[:, sample])
+                "bwd_sampled": sampled_backward_error(Ah, Xh[:, sample], Bh[:, sample])
                 if st["info"] == 0 else None,
                 "fwd_vs_fp64": fwd,
                 "factor_tflops": pftrf_flops(n) / (stages.get("mixed.factor", 0) * 1e-3) / 1e12
@@ -474,10 +485,117 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Batched PFTRF + PFTRS: `--batch` independent SPD matrices of uneven
+    order n ~ U{32..512}, each in one of the 8 layouts (uniform), nrhs ~
+    U{1..8}, A_k = B B^T / n + I (rfp_inputs.spd_bbt, seed 1000 + k), in
+    FP64 and in FP32, one graph-captured launch per batch.  The panel width
+    per n-bucket comes from the autotuner's cache (tuned on first use)."""
+    import numpy as np
+    import torch
+
+    import rfp_inputs as gen
+    from paper_0901_1696_gb300 import batched as bt
+    from paper_0901_1696_gb300 import binding as rfp
+    from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
+    from paper_0901_1696_gb300.peaks import FP32_FMA_PER_SM_CLK, SM_COUNT, SM_MAX_MHZ
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    gpu = torch.cuda.get_device_properties(dev).name
+    count = args.batch
+    rng = np.random.default_rng(0)
+    ns = [int(x) for x in rng.integers(32, 513, count)]
+    lay = rng.integers(0, 8, count)
+    layouts = [("N", "L"), ("N", "U"), ("T", "L"), ("T", "U")]
+    transrs = [layouts[int(x) % 4][0] for x in lay]
+    uplos = [layouts[int(x) % 4][1] for x in lay]
+    nrhss = [int(x) for x in rng.integers(1, 9, count)]
+    # (the 8 layouts: 4 TRANSR x UPLO pairs x the parity of n, which n's own draw sets)
+    entries, arf_len, b_len = bt.make_entries(ns, transrs, uplos, nrhss)
+    flops = sum(pftrf_flops(n) + pftrs_flops(n, r) for n, r in zip(ns, nrhss))
+    sample = sorted(set(int(x) for x in np.linspace(0, count - 1, 12)))
+    kept = {}
+    legs = {}
+    for prec, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        arf = torch.empty(max(arf_len, 1), dtype=dtype, device=dev)
+        B = torch.empty(max(b_len, 1), dtype=dtype, device=dev)
+        pack = lib.rfp_dpack if dtype == torch.float64 else lib.rfp_spack
+        t_gen = time.time()
+        for k in range(count):
+            n, r = ns[k], nrhss[k]
+            A, r2 = gen.spd_bbt(n, seed=1000 + k, return_rng=True)
+            Bk = gen.rhs(n, r, r2)
+            if k in sample:
+                kept[k] = (A, Bk)
+            dA = torch.from_numpy(A).to(dev, dtype)
+            pack(transrs[k], uplos[k], n, dA, n, arf[int(entries["arf"][k]):])
+            off = int(entries["b"][k])
+            B[off: off + n * r] = torch.from_numpy(Bk.ravel(order="F")).to(dev, dtype)
+        torch.cuda.synchronize(dev)
+        t_gen = time.time() - t_gen
+        cache = bt.TuningCache()
+        tuned = False
+        if args.retune or not cache.get(gpu, prec):
+            bt.autotune(prec, cache=cache)
+            tuned = True
+        cache.fill_nb(entries, gpu, prec)
+        # warm-up replays, then timed replays; inputs restored before each (not timed)
+        sampler = ClockSampler(0)
+        t0 = time.time()
+        bt.time_batch(torch, lib, entries, arf, B, dtype, reps=max(args.warmup, 1))
+        sampler.start()
+        ms, out_a, out_b, info = bt.time_batch(torch, lib, entries, arf, B, dtype,
+                                               reps=max(args.steps, 1))
+        clocks = sampler.stop()
+        wall = time.time() - t0
+        info_h = info.cpu().numpy()
+        bh = out_b.cpu().numpy().astype(np.float64)
+        bwd = 0.0
+        for k in sample:
+            A, Bk = kept[k]
+            n, r = ns[k], nrhss[k]
+            off = int(entries["b"][k])
+            Xk = bh[off: off + n * r].reshape(r, n).T
+            bwd = max(bwd, sampled_backward_error(A, Xk, Bk))
+        mhz = clocks["sm_mhz"] or SM_MAX_MHZ
+        if prec == "f64":
+            peak, bound = fp64_peak_tflops(mhz), "FP64 FMA pipe: 152 SMs x 2 FMA x 2 x clock"
+        else:
+            peak = SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+            bound = "FP32 FMA pipe: 152 SMs x 128 FMA x 2 x clock"
+        tflops = flops / (ms * 1e-3) / 1e12
+        legs[prec] = {
+            "ms": ms, "tflops": tflops, "matrices_per_s": count / (ms * 1e-3),
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "traffic": None, "kernel": "batched_kernel",
+                         "peak_source": bound},
+            "info_nonzero": int(np.count_nonzero(info_h)), "bwd_sampled_max": bwd,
+            "nb_table": cache.get(gpu, prec), "autotuned_now": tuned,
+            "clocks": clocks, "gen_s": t_gen, "wall_s": wall}
+        del arf, B, out_a, out_b
+        torch.cuda.empty_cache()
+    line = {"mode": "batched", "metric": "batched PFTRF+PFTRS TFLOP/s (uneven SPD RFPF batch)",
+            "value": legs["f64"]["tflops"], "unit": "TFLOP/s", "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+            "data": "synthetic: A_k = B B^T / n + I, B ~ U[-1,1] (numpy PCG64, seed 1000 + k)",
+            "config": {"workload": f"{count} SPD matrices, n ~ U{{32..512}}, 8 layouts uniform, "
+                                   "nrhs ~ U{1..8}; one graph-captured launch per batch",
+                       "batch": count, "flops_per_batch": flops,
+                       "l2": "inputs restored before every replay (untimed copy of "
+                             f"{arf_len * 8 / 1e9:.2f} GB FP64 > L2)"},
+            "f64": legs["f64"], "f32": legs["f32"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.mode == "mixed":
         run_mixed(args)
+        return
+    if args.mode == "batched":
+        run_batched(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

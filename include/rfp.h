@@ -229,7 +229,10 @@ int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, con
  *   b       element offset of its right-hand sides (column-major, ldb) in B
  *   nrhs    0 (factor only) to 8; ldb >= max(1, n) when nrhs > 0
  *   transr, uplo   its layout ('N'/'T', 'L'/'U')
- *   nb      panel width 16 or 32 (0 = 32), e.g. from the package's autotuner
+ *   nb      panel width 16, 24 or 32 (0 = 32), e.g. from the package's
+ *           autotuner; a launch reserves shared memory for the plan's widest
+ *           panel (in FP64, plans whose panels are all <= 24 columns wide run
+ *           two CTAs per SM)
  *
  * rfp_batch_plan (host, not capturable): validates every entry against the
  * buffer lengths arf_len / b_len (elements), orders the matrices largest
@@ -238,7 +241,9 @@ int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, con
  * `stream`.  Returns 0, -2 if an entry is invalid (its index is written to
  * *bad_entry when bad_entry is not NULL), -5 / -6 for a bad d_plan /
  * plan_bytes, or RFP_ERR_CUDA.  A plan can be reused for any number of runs
- * with the same entries, in FP64 or FP32.
+ * with the same entries, in FP64 or FP32.  The library remembers, per d_plan
+ * address, the widest panel of the plan last written there; a run on a plan
+ * copied to another address is sized for 32-column panels (same results).
  * Arguments: 1 batch, 2 h_entries, 3 arf_len, 4 b_len, 5 d_plan, 6 plan_bytes,
  * 7 bad_entry, 8 stream.
  *

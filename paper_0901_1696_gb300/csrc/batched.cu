@@ -5,20 +5,25 @@
 // ordered by rfp_batch_plan) and runs, on that matrix alone, the blocked
 // right-looking Cholesky of Section 3 on the logical lower factor held in the
 // RFP blocks T1 / S / T2, followed by the forward and back substitutions of
-// Section 4 for its right-hand sides.  Per NB-wide panel (NB = 16 or 32, the
-// entry's autotuned choice):
+// Section 4 for its right-hand sides.  Per NB-wide panel (NB = 16, 24 or 32,
+// the entry's autotuned choice):
 //   1. the panel (rows k0..n-1, NB columns) is read into shared memory,
-//   2. it is factored there column by column (pivot, scale, rank-1 update of
-//      the remaining panel columns): this is both the diagonal POTRF and the
-//      panel TRSM,
+//      column-major,
+//   2. it is factored there column by column (pivot and its reciprocal by
+//      one thread, then per row: scale, rank-1 update of the remaining panel
+//      columns): this is both the diagonal POTRF and the panel TRSM,
 //   3. it is written back and the trailing lower triangle receives
-//      A(i, j) -= P(i, :) P(j, :)^T in 4 x 4 register tiles.
-// Orders up to 512 (the panel then takes 128 KB of shared memory in FP64).
+//      A(i, j) -= P(i, :) P(j, :)^T in 4 x 4 register tiles, whose operands
+//      are four consecutive rows of a panel column.
+// Orders up to 512 (the panel then takes 129 KB of shared memory in FP64).
 // A failing pivot stores the global 1-based index in info[entry] and skips
 // that matrix's solve.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "../../include/rfp.h"
@@ -61,47 +66,79 @@ __device__ __forceinline__ View<T> bview(T *base, const Block &b, int64_t ld)
     return b.trans ? View<T>{base + b.off, ld, 1} : View<T>{base + b.off, 1, ld};
 }
 
+// Shared-memory layout of one CTA: the panel P (kMaxNb columns of kPanelLd
+// rows, column-major: a column's rows are contiguous), then the solve's
+// diagonal block D (32 x 33), its block of solutions Y (32 x 8), the
+// reciprocals of D's diagonal and the current pivot's reciprocal.
+// A launch is sized for the widest panel among its plan's entries (16, 24
+// or 32 columns): in FP64 a 24-column panel leaves room for two CTAs per SM.
+constexpr int kPanelLd = kBatchMaxN + 4;     // rows padded to a multiple of 4
+constexpr int kSolveNb = 32, kSolveLd = kSolveNb + 1, kMaxRhs = 8;
+constexpr int smem_elems(int maxnb)
+{
+    return maxnb * kPanelLd + kSolveNb * kSolveLd + kSolveNb * kMaxRhs + kSolveNb + 2;
+}
+
+// Four consecutive elements from shared memory (16-byte aligned).
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
+{
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
 // Factor one matrix in place; returns 0 or the 1-based failing index.
 template <typename T, int NB>
-__device__ int factor_one(const Mat<T> &A, int64_t n, T *P /* smem (kBatchMaxN) x (NB + 1) */,
-                          int *s_fail)
+__device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fail)
 {
-    constexpr int LDP = NB + 1;
+    constexpr int LDC = kPanelLd;
     const int tid = threadIdx.x;
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         const int kb = (int)(n - k0 < NB ? n - k0 : NB);
         const int rows = (int)(n - k0);
-        // 1. panel -> shared memory (lower part of the diagonal block only)
-        for (int e = tid; e < rows * kb; e += blockDim.x) {
-            const int r = e % rows, c = e / rows;
-            P[r * LDP + c] = (r >= c) ? *A.at(k0 + r, k0 + c) : T(0);
-        }
+        const int rpad = (rows + 3) & ~3;
+        // 1. panel -> shared memory; zero above the diagonal and in the row padding
+        for (int c = 0; c < kb; ++c)
+            for (int r = tid; r < rpad; r += blockDim.x)
+                P[c * LDC + r] = (r >= c && r < rows) ? *A.at(k0 + r, k0 + c) : T(0);
         if (tid == 0) *s_fail = -1;
         __syncthreads();
-        // 2. unblocked right-looking Cholesky of the rows x kb panel
+        // 2. right-looking Cholesky of the rows x kb panel, column by column
         for (int c = 0; c < kb; ++c) {
-            if (tid == 0) {
-                const T d = P[c * LDP + c];
-                if (!(d > T(0))) *s_fail = c;
-                else P[c * LDP + c] = sqrt(d);
+            if (tid == 0) {   // pivot; scale the panel's own rows c+1 .. kb-1 of column c
+                const T d = P[c * LDC + c];
+                if (!(d > T(0))) {
+                    *s_fail = c;
+                } else {
+                    const T sq = sqrt(d), ri = T(1) / sq;
+                    P[c * LDC + c] = sq;
+                    *s_rinv = ri;
+                    for (int q = c + 1; q < kb; ++q) P[c * LDC + q] *= ri;
+                }
             }
             __syncthreads();
             if (*s_fail >= 0) return (int)(k0 + *s_fail + 1);
-            const T dc = P[c * LDP + c];
-            for (int r = c + 1 + tid; r < rows; r += blockDim.x) P[r * LDP + c] /= dc;
-            __syncthreads();
-            const int rem = kb - c - 1;
-            for (int e = tid; e < (rows - c - 1) * rem; e += blockDim.x) {
-                const int r = c + 1 + e / rem, q = c + 1 + e % rem;
-                if (q <= r) P[r * LDP + q] -= P[r * LDP + c] * P[q * LDP + c];
+            const T ri = *s_rinv;
+            // row r: l_rc = a_rc / l_cc, then a_rq -= l_rc l_qc for c < q <= min(r, kb-1)
+            for (int r = c + 1 + tid; r < rows; r += blockDim.x) {
+                T lr = P[c * LDC + r];
+                if (r >= kb) {
+                    lr *= ri;
+                    P[c * LDC + r] = lr;
+                }
+                const int qmax = r < kb - 1 ? r : kb - 1;
+                for (int q = c + 1; q <= qmax; ++q) P[q * LDC + r] -= lr * P[c * LDC + q];
             }
             __syncthreads();
         }
         // 3a. panel back to the matrix
-        for (int e = tid; e < rows * kb; e += blockDim.x) {
-            const int r = e % rows, c = e / rows;
-            if (r >= c) *A.at(k0 + r, k0 + c) = P[r * LDP + c];
-        }
+        for (int c = 0; c < kb; ++c)
+            for (int r = c + tid; r < rows; r += blockDim.x) *A.at(k0 + r, k0 + c) = P[c * LDC + r];
         // 3b. trailing update of the lower triangle rows/cols >= k0 + kb, 4 x 4 tiles
         const int m = rows - kb;
         if (m > 0) {
@@ -112,15 +149,12 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P /* smem (kBatchMaxN) 
                 while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
                 while (ti * (ti + 1) / 2 > t) --ti;
                 const int tj = t - ti * (ti + 1) / 2;
+                const T *pa = P + kb + 4 * ti, *pb = P + kb + 4 * tj;   // zero beyond `rows`
                 T acc[4][4] = {};
                 for (int c = 0; c < kb; ++c) {
                     T a[4], b[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int ri = kb + 4 * ti + u, rj = kb + 4 * tj + u;
-                        a[u] = ri < rows ? P[ri * LDP + c] : T(0);
-                        b[u] = rj < rows ? P[rj * LDP + c] : T(0);
-                    }
+                    ld4(pa + c * LDC, a);
+                    ld4(pb + c * LDC, b);
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -148,72 +182,121 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P /* smem (kBatchMaxN) 
     return 0;
 }
 
-// L L^T X = B in place for nrhs <= 8 columns (B column-major, ldb), blocked by NB.
-template <typename T, int NB>
-__device__ void solve_one(const Mat<T> &A, int64_t n, T *Bm, int64_t ldb, int nrhs,
-                          T *D /* smem NB x (NB + 1) */)
+// The solve's right-looking update after diagonal block [k0, k0 + kb):
+// FWD: rows i >= k0 + kb get b_i -= L(i, block) y_block;
+// !FWD: rows i < k0 get y_i -= L(block, i)^T x_block.
+// One thread per row, R right-hand sides in registers.
+template <typename T, bool FWD, int R>
+__device__ __forceinline__ void rows_update_r(const Mat<T> &A, int64_t n, int64_t k0, int kb,
+                                              T *Bm, int64_t ldb, const T *Y)
 {
-    constexpr int LDD = NB + 1;
-    const int tid = threadIdx.x;
-    // forward: L y = b
-    for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        const int kb = (int)(n - k0 < NB ? n - k0 : NB);
+    const int64_t lo = FWD ? k0 + kb : 0, hi = FWD ? n : k0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T acc[R] = {};
+        for (int c = 0; c < kb; ++c) {
+            const T l = FWD ? *A.at(i, k0 + c) : *A.at(k0 + c, i);
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[q] = fma(l, Y[c * kMaxRhs + q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) Bm[i + q * ldb] -= acc[q];
+    }
+}
+
+template <typename T, bool FWD>
+__device__ void rows_update(const Mat<T> &A, int64_t n, int64_t k0, int kb, T *Bm, int64_t ldb,
+                            int nrhs, const T *Y)
+{
+    switch (nrhs) {
+    case 1: rows_update_r<T, FWD, 1>(A, n, k0, kb, Bm, ldb, Y); break;
+    case 2: rows_update_r<T, FWD, 2>(A, n, k0, kb, Bm, ldb, Y); break;
+    case 3: rows_update_r<T, FWD, 3>(A, n, k0, kb, Bm, ldb, Y); break;
+    case 4: rows_update_r<T, FWD, 4>(A, n, k0, kb, Bm, ldb, Y); break;
+    case 5: rows_update_r<T, FWD, 5>(A, n, k0, kb, Bm, ldb, Y); break;
+    case 6: rows_update_r<T, FWD, 6>(A, n, k0, kb, Bm, ldb, Y); break;
+    case 7: rows_update_r<T, FWD, 7>(A, n, k0, kb, Bm, ldb, Y); break;
+    default: rows_update_r<T, FWD, 8>(A, n, k0, kb, Bm, ldb, Y); break;
+    }
+}
+
+// L L^T X = B in place for nrhs <= 8 columns (B column-major, ldb), by
+// 32-row blocks.  Each diagonal block is solved by one warp per right-hand
+// side (lane r holds row r; the finished value of row c is broadcast with a
+// shuffle); the block's contribution to the remaining rows is then
+// subtracted with one thread per row (right-looking).
+template <typename T>
+__device__ void solve_one(const Mat<T> &A, int64_t n, T *Bm, int64_t ldb, int nrhs, T *D, T *Y,
+                          T *rdiag)
+{
+    constexpr int SB = kSolveNb, LDD = kSolveLd;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t nblk = (n + SB - 1) / SB;
+    for (int e = tid; e < SB * kMaxRhs; e += blockDim.x) Y[e] = T(0);
+    auto stage_diag = [&](int64_t k0, int kb) {
         for (int e = tid; e < kb * kb; e += blockDim.x) {
             const int r = e % kb, c = e / kb;
             D[r * LDD + c] = (r >= c) ? *A.at(k0 + r, k0 + c) : T(0);
         }
-        // b(block) -= L(block, 0:k0) y(0:k0): one thread per (row, rhs)
-        for (int e = tid; e < kb * nrhs; e += blockDim.x) {
-            const int r = e % kb, q = e / kb;
-            T s = Bm[k0 + r + q * ldb];
-            for (int64_t p = 0; p < k0; ++p) s -= *A.at(k0 + r, p) * Bm[p + q * ldb];
-            Bm[k0 + r + q * ldb] = s;
+        __syncthreads();
+        if (tid < kb) rdiag[tid] = T(1) / D[tid * LDD + tid];
+        __syncthreads();
+    };
+    // forward: L y = b
+    for (int64_t bk = 0; bk < nblk; ++bk) {
+        const int64_t k0 = bk * SB;
+        const int kb = (int)(n - k0 < SB ? n - k0 : SB);
+        stage_diag(k0, kb);
+        if (warp < nrhs) {
+            T y = lane < kb ? Bm[k0 + lane + warp * ldb] : T(0);
+            for (int c = 0; c < kb; ++c) {
+                if (lane == c) y *= rdiag[c];
+                const T yc = __shfl_sync(0xffffffffu, y, c);
+                if (lane > c && lane < kb) y -= D[lane * LDD + c] * yc;
+            }
+            if (lane < kb) {
+                Bm[k0 + lane + warp * ldb] = y;
+                Y[lane * kMaxRhs + warp] = y;
+            }
         }
         __syncthreads();
-        for (int q = tid; q < nrhs; q += blockDim.x)       // triangle solve, one thread per rhs
-            for (int r = 0; r < kb; ++r) {
-                T s = Bm[k0 + r + q * ldb];
-                for (int p = 0; p < r; ++p) s -= D[r * LDD + p] * Bm[k0 + p + q * ldb];
-                Bm[k0 + r + q * ldb] = s / D[r * LDD + r];
-            }
+        rows_update<T, true>(A, n, k0, kb, Bm, ldb, nrhs, Y);   // b_i -= L(i, block) y_block
         __syncthreads();
     }
     // backward: L^T x = y
-    const int64_t nblk = (n + NB - 1) / NB;
     for (int64_t bk = nblk - 1; bk >= 0; --bk) {
-        const int64_t k0 = bk * NB;
-        const int kb = (int)(n - k0 < NB ? n - k0 : NB);
-        for (int e = tid; e < kb * kb; e += blockDim.x) {
-            const int r = e % kb, c = e / kb;
-            D[r * LDD + c] = (r >= c) ? *A.at(k0 + r, k0 + c) : T(0);
-        }
-        // b(block) -= L(k0+kb:n, block)^T x(k0+kb:n)
-        for (int e = tid; e < kb * nrhs; e += blockDim.x) {
-            const int r = e % kb, q = e / kb;
-            T s = Bm[k0 + r + q * ldb];
-            for (int64_t p = k0 + kb; p < n; ++p) s -= *A.at(p, k0 + r) * Bm[p + q * ldb];
-            Bm[k0 + r + q * ldb] = s;
+        const int64_t k0 = bk * SB;
+        const int kb = (int)(n - k0 < SB ? n - k0 : SB);
+        stage_diag(k0, kb);
+        if (warp < nrhs) {
+            T y = lane < kb ? Bm[k0 + lane + warp * ldb] : T(0);
+            for (int c = kb - 1; c >= 0; --c) {
+                if (lane == c) y *= rdiag[c];
+                const T xc = __shfl_sync(0xffffffffu, y, c);
+                if (lane < c) y -= D[c * LDD + lane] * xc;
+            }
+            if (lane < kb) {
+                Bm[k0 + lane + warp * ldb] = y;
+                Y[lane * kMaxRhs + warp] = y;
+            }
         }
         __syncthreads();
-        for (int q = tid; q < nrhs; q += blockDim.x)
-            for (int r = kb - 1; r >= 0; --r) {
-                T s = Bm[k0 + r + q * ldb];
-                for (int p = r + 1; p < kb; ++p) s -= D[p * LDD + r] * Bm[k0 + p + q * ldb];
-                Bm[k0 + r + q * ldb] = s / D[r * LDD + r];
-            }
+        rows_update<T, false>(A, n, k0, kb, Bm, ldb, nrhs, Y);  // y_i -= L(block, i)^T x_block
         __syncthreads();
     }
 }
 
-template <typename T>
+template <typename T, int MAXNB>
 __global__ void __launch_bounds__(kBatchThreads) batched_kernel(PlanHeader *hdr,
                                                                 const PlanEntry *table,
                                                                 int64_t batch, T *arf, T *B,
                                                                 int32_t *info)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *P = reinterpret_cast<T *>(smem_raw);                       // kBatchMaxN x 33
-    T *D = P + kBatchMaxN * 33;                                   // 32 x 33
+    T *P = reinterpret_cast<T *>(smem_raw);
+    T *D = P + MAXNB * kPanelLd;
+    T *Y = D + kSolveNb * kSolveLd;
+    T *rdiag = Y + kSolveNb * kMaxRhs;
+    T *s_rinv = rdiag + kSolveNb;
     __shared__ int s_idx, s_fail;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&hdr->counter, 1);
@@ -224,33 +307,66 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(PlanHeader *hdr,
         const PlanEntry e = table[idx];
         Mat<T> A{bview(arf + e.arf, e.t1, e.ld), bview(arf + e.arf, e.s, e.ld),
                  bview(arf + e.arf, e.t2, e.ld), e.n1};
-        const int fail = e.nb == 16 ? factor_one<T, 16>(A, e.n, P, &s_fail)
-                                    : factor_one<T, 32>(A, e.n, P, &s_fail);
+        const int nb = e.nb < MAXNB ? e.nb : MAXNB;
+        int fail;
+        if (nb == 16) fail = factor_one<T, 16>(A, e.n, P, s_rinv, &s_fail);
+        else if (MAXNB >= 24 && nb == 24) fail = factor_one<T, (MAXNB >= 24 ? 24 : 16)>(A, e.n, P, s_rinv, &s_fail);
+        else fail = factor_one<T, MAXNB>(A, e.n, P, s_rinv, &s_fail);
         if (threadIdx.x == 0) info[e.index] = fail;
         __syncthreads();
-        if (fail == 0 && e.nrhs > 0) {
-            if (e.nb == 16) solve_one<T, 16>(A, e.n, B + e.b, e.ldb, e.nrhs, D);
-            else solve_one<T, 32>(A, e.n, B + e.b, e.ldb, e.nrhs, D);
-        }
+        if (fail == 0 && e.nrhs > 0) solve_one<T>(A, e.n, B + e.b, e.ldb, e.nrhs, D, Y, rdiag);
         __syncthreads();
     }
 }
 
-int g_batch_ctas_cache[64][2] = {};
+// Resident CTAs of batched_kernel<T, MAXNB> on the current device (cached).
+std::mutex g_ctas_mutex;
+std::map<std::tuple<int, int, int>, int> g_ctas_cache;
 
-template <typename T>
+template <typename T, int MAXNB>
 int resident_ctas(int smem)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    const int e = sizeof(T) == 8 ? 0 : 1;
-    if (dev >= 0 && dev < 64 && g_batch_ctas_cache[dev][e]) return g_batch_ctas_cache[dev][e];
+    const auto key = std::make_tuple(dev, (int)sizeof(T), MAXNB);
+    {
+        std::lock_guard<std::mutex> lock(g_ctas_mutex);
+        auto it = g_ctas_cache.find(key);
+        if (it != g_ctas_cache.end()) return it->second;
+    }
     int per_sm = 1;
-    cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>, kBatchThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T, MAXNB>, kBatchThreads,
+                                                  smem);
     const int ctas = std::max(1, per_sm) * device_sm_count();
-    if (dev >= 0 && dev < 64) g_batch_ctas_cache[dev][e] = ctas;
+    std::lock_guard<std::mutex> lock(g_ctas_mutex);
+    g_ctas_cache[key] = ctas;
     return ctas;
+}
+
+// Widest panel of the plan last written at each d_plan address by this
+// process; a launch is sized for it (32 when the address is unknown).
+std::mutex g_plan_mutex;
+std::map<const void *, int> g_plan_maxnb;
+
+int plan_maxnb(const void *d_plan)
+{
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    auto it = g_plan_maxnb.find(d_plan);
+    return it == g_plan_maxnb.end() ? 32 : it->second;
+}
+
+template <typename T, int MAXNB>
+cudaError_t launch_batched(int64_t batch, PlanHeader *hdr, const PlanEntry *table, T *arf, T *B,
+                           int32_t *info, cudaStream_t st)
+{
+    const int smem = smem_elems(MAXNB) * (int)sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel<T, MAXNB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(batch, resident_ctas<T, MAXNB>(smem));
+    batched_kernel<T, MAXNB><<<(unsigned)grid, kBatchThreads, smem, st>>>(hdr, table, batch, arf,
+                                                                         B, info);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -272,7 +388,8 @@ int batch_plan(int64_t batch, const rfp_batch_entry_t *h, int64_t arf_len, int64
         const bool up_ok = e.uplo == 'L' || e.uplo == 'l' || e.uplo == 'U' || e.uplo == 'u';
         const int64_t nt = e.n * (e.n + 1) / 2;
         bool ok = tr_ok && up_ok && e.n >= 0 && e.n <= kBatchMaxN && e.arf >= 0 &&
-                  e.arf + nt <= arf_len && (e.nb == 0 || e.nb == 16 || e.nb == 32) && e.nrhs >= 0 &&
+                  e.arf + nt <= arf_len && (e.nb == 0 || e.nb == 16 || e.nb == 24 || e.nb == 32) &&
+                  e.nrhs >= 0 &&
                   e.nrhs <= 8;
         if (ok && e.nrhs > 0)   // an order-0 matrix reads no right-hand side
             ok = e.ldb >= std::max<int64_t>(1, e.n) &&
@@ -288,6 +405,8 @@ int batch_plan(int64_t batch, const rfp_batch_entry_t *h, int64_t arf_len, int64
         r.nb = e.nb == 0 ? 32 : e.nb; r.index = (int32_t)k;
         r.t1 = L.t1; r.s = L.s; r.t2 = L.t2; r.n1 = L.n1; r.ld = L.ld;
     }
+    int maxnb = 16;
+    for (const PlanEntry &r : rows) maxnb = std::max(maxnb, (int)r.nb);
     std::stable_sort(rows.begin(), rows.end(),
                      [](const PlanEntry &a, const PlanEntry &b) { return a.n > b.n; });
     PlanHeader hdr;
@@ -297,6 +416,10 @@ int batch_plan(int64_t batch, const rfp_batch_entry_t *h, int64_t arf_len, int64
         err = cudaMemcpyAsync(static_cast<char *>(d_plan) + sizeof hdr, rows.data(),
                               rows.size() * sizeof(PlanEntry), cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);   // host staging is released below
+    if (err == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_plan_mutex);
+        g_plan_maxnb[d_plan] = maxnb;
+    }
     return err == cudaSuccess ? 0 : 1000 + (int)err;
 }
 
@@ -308,14 +431,13 @@ cudaError_t batched_run(int64_t batch, const void *d_plan, T *arf, T *B, int32_t
     PlanHeader *hdr = static_cast<PlanHeader *>(const_cast<void *>(d_plan));
     const PlanEntry *table = reinterpret_cast<const PlanEntry *>(static_cast<const char *>(d_plan) +
                                                                  sizeof(PlanHeader));
-    const int smem = (kBatchMaxN * 33 + 32 * 33) * (int)sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(batched_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaMemsetAsync(&hdr->counter, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(&hdr->counter, 0, sizeof(int32_t), st);
+    const int maxnb = plan_maxnb(d_plan);
+    if (maxnb <= 16) e = launch_batched<T, 16>(batch, hdr, table, arf, B, info, st);
+    else if (maxnb <= 24) e = launch_batched<T, 24>(batch, hdr, table, arf, B, info, st);
+    else e = launch_batched<T, 32>(batch, hdr, table, arf, B, info, st);
     if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(batch, resident_ctas<T>(smem));
-    batched_kernel<T><<<(unsigned)grid, kBatchThreads, smem, st>>>(hdr, table, batch, arf, B, info);
     note_launch();
     return cudaGetLastError();
 }

@@ -10,3 +10,6 @@ the roof.
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2.0
+# FP32 FMA issue rate per SM per clock (4 sub-partitions x 32 lanes); the
+# same probe measured 74.46 TFLOP/s (118 FMA/clk/SM at 2070 MHz).
+FP32_FMA_PER_SM_CLK = 128.0

@@ -44,7 +44,7 @@ def make_batch(count, seed, n_max=512, fail_every=0):
         B = gen.rhs(n, nrhs, r2) if nrhs else np.zeros((n, 0))
         arf = oracle.pack(transr, uplo, A)
         entries[k] = (n, arf_off, b_off, nrhs, max(n, 1), transr.encode(), uplo.encode(),
-                      [0, 16, 32][k % 3], 0)
+                      [0, 16, 24, 32][k % 4], 0)
         mats.append(dict(n=n, A=A, B=B, transr=transr, uplo=uplo, nrhs=nrhs, arf_off=arf_off,
                          b_off=b_off, fail=fail))
         arf_parts.append(arf)
@@ -142,3 +142,18 @@ def test_batched_graph_capture_and_alone_vs_mix_bit_identical():
         if m["nrhs"] and m["n"]:
             assert np.array_equal(db1.cpu().numpy()[: b1.size],
                                   eager_b[m["b_off"]: m["b_off"] + b1.size])
+
+
+def test_autotune_small_writes_cache(tmp_path):
+    """The autotuner times both panel widths per bucket and TRANSR (tiny
+    batches here) and stores a complete table that fill_nb can apply."""
+    from paper_0901_1696_gb300 import batched as bt
+    cache = bt.TuningCache(str(tmp_path / "tune.json"))
+    table = bt.autotune("f64", count=4, reps=1, cache=cache)
+    assert set(table) == {"N", "T"}
+    for t in "NT":
+        assert len(table[t]) == len(bt.BUCKETS) and set(table[t]) <= {16, 24, 32}
+    gpu = torch.cuda.get_device_properties(0).name
+    assert bt.TuningCache(str(tmp_path / "tune.json")).get(gpu, "f64") == table
+    e, _, _ = bt.make_entries([40, 400], ["N", "T"], ["L", "U"], [1, 2])
+    assert cache.fill_nb(e, gpu, "f64") and set(e["nb"]) <= {16, 24, 32}
