@@ -61,7 +61,7 @@ def parse():
                         "reference step)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["fp64", "mixed", "batched"], default="fp64",
+    p.add_argument("--mode", choices=["fp64", "mixed", "batched", "serve"], default="fp64",
                    help="fp64: the FP64 hot path (default line); mixed: the mixed-precision "
                         "solve at n = 32768 against the FP64 path (its own line)")
     p.add_argument("--mixed-n", type=int, default=32768)
@@ -70,6 +70,11 @@ def parse():
     p.add_argument("--precs", default="fp32,tf32x3,tf32,bf16")
     p.add_argument("--max-iter", type=int, default=30, help="refinement steps (mixed mode)")
     p.add_argument("--batch", type=int, default=4096, help="batched mode: matrices per batch")
+    p.add_argument("--serve-requests", type=int, default=1000,
+                   help="serve mode: requests per run (the stream description uses 20000)")
+    p.add_argument("--serve-pool", type=int, default=64, help="serve mode: distinct matrices")
+    p.add_argument("--serve-loads", default="0.5,0.7,0.9",
+                   help="serve mode: offered loads as fractions of the measured capacity")
     p.add_argument("--retune", action="store_true",
                    help="batched mode: re-run the panel-width autotuner even if cached")
     p.add_argument("--no-fp64-ref", action="store_true",
@@ -589,6 +594,150 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving loop (rfp_serve_*): a stream of factor+solve requests, n
+    log-uniform in [64, 8192], kappa log-uniform in [1e1, 1e6], nrhs ~
+    U{1..32}, layouts uniform, FP64 / mixed-precision modes uniform, host
+    inputs in pinned memory.  Runs: closed-loop saturation (all requests at
+    t = 0) to measure capacity, then Poisson arrivals at the given fractions
+    of it, then solve requests on resident factors.  Latency = done - submit
+    on the server's host clock."""
+    import numpy as np
+    import torch
+
+    import rfp_inputs as gen
+    from paper_0901_1696_gb300 import batched as bt
+    from paper_0901_1696_gb300 import binding as rfp
+    from paper_0901_1696_gb300 import serve as sv
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    R, P = args.serve_requests, args.serve_pool
+    rng = np.random.default_rng(0)
+    layouts = [("N", "L"), ("N", "U"), ("T", "L"), ("T", "U")]
+    pool = []
+    for i in range(P):
+        n = int(round(np.exp(rng.uniform(np.log(64), np.log(8192)))))
+        kappa = float(10 ** rng.uniform(1, 6))
+        t, u = layouts[int(rng.integers(0, 4))]
+        A = gen.spd_reflectors(n, seed=500 + i, kappa=kappa, device=dev)
+        arf_d = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
+        lib.rfp_dpack(t, u, n, A, n, arf_d)
+        del A
+        pool.append(dict(n=n, kappa=kappa, t=t, u=u, arf_d=arf_d,
+                         arf_h=arf_d.cpu().pin_memory()))
+    torch.cuda.synchronize(dev)
+    which = rng.integers(0, P, R)
+    nrhs = rng.integers(1, 33, R)
+    modes = rng.integers(0, 2, R)
+    sizes = [pool[int(w)]["n"] * int(r) for w, r in zip(which, nrhs)]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    Bh = torch.from_numpy(rng.uniform(-1, 1, int(offs[-1]))).pin_memory()
+    Xh = torch.zeros(int(offs[-1]), dtype=torch.float64).pin_memory()
+    gpu = torch.cuda.get_device_properties(dev).name
+    table = bt.TuningCache().get(gpu, "f64")
+    nb = [[(table or {}).get(t, [16] * 8)[b] for b in range(8)] for t in ("N", "T")]
+    arena = 150 << 30
+
+    def one_run(arrivals, key_base):
+        """arrivals: submit times (s) relative to the start, or None (all at once)."""
+        Xh.zero_()
+        with sv.Server(arena_bytes=arena, streams=8, batch_max=1024, small_n=512,
+                       max_iter=30, tol=1e-15, batch_nb=nb) as s:
+            t0 = time.perf_counter()
+            for k in range(R):
+                if arrivals is not None:
+                    dt = arrivals[k] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                pm = pool[int(which[k])]
+                n, r = pm["n"], int(nrhs[k])
+                s.submit(k, sv.OP_FACTOR_SOLVE, int(modes[k]), pm["t"], pm["u"], n, r,
+                         arf=pm["arf_h"].data_ptr(),
+                         B=Bh.data_ptr() + 8 * int(offs[k]), X=Xh.data_ptr() + 8 * int(offs[k]),
+                         key=key_base + k)
+            done = s.wait(R, timeout=1800)
+            st = s.stats()
+        done.sort(key=lambda c: c["id"])
+        lat = np.array([c["t_done"] - c["t_submit"] for c in done]) * 1e3
+        span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
+        ok = [c["status"] == 0 for c in done]
+        fp64 = modes == 0
+        return {"requests_per_s": R / span, "solves_per_s": float(nrhs.sum()) / span,
+                "span_s": span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "p50_fp64_ms": float(np.percentile(lat[fp64], 50)),
+                "p50_mixed_ms": float(np.percentile(lat[~fp64], 50)),
+                "ok": int(sum(ok)), "failed": int(R - sum(ok)),
+                "statuses": sorted(set(int(c["status"]) for c in done)),
+                "batched_fraction": st["batched_requests"] / R,
+                "mean_batch": st["batched_requests"] / max(st["batches"], 1),
+                "evictions": st["evictions"], "cache_gb": st["cache_bytes"] / 1e9}, done
+
+    runs = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    sat, done = one_run(None, 0)
+    clocks = sampler.stop()
+    runs["saturation"] = sat
+    # sampled backward errors of the saturation run: host-side checker, FP64 residual on the GPU
+    check = sorted(set(int(x) for x in np.linspace(0, R - 1, 48)))
+    bwd = []
+    for k in check:
+        pm = pool[int(which[k])]
+        n, r = pm["n"], int(nrhs[k])
+        Af = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        lib.rfp_dunpack(pm["t"], pm["u"], n, pm["arf_d"], Af, n)   # one triangle (row-major view)
+        Af = Af + Af.T - torch.diag(torch.diagonal(Af))
+        B = Bh[int(offs[k]): int(offs[k]) + n * r].to(dev).view(r, n).T
+        X = Xh[int(offs[k]): int(offs[k]) + n * r].to(dev).view(r, n).T
+        res = (B - Af @ X).abs().amax(0)
+        den = Af.abs().sum(1).amax() * X.abs().amax(0) + B.abs().amax(0)
+        bwd.append(dict(k=k, n=n, mode=int(modes[k]), bwd=float((res / den).max())))
+        del Af
+    cap = sat["requests_per_s"]
+    for f in [float(x) for x in args.serve_loads.split(",") if x]:
+        gaps = np.random.default_rng(7).exponential(1.0 / (f * cap), R)
+        runs[f"load_{f:g}"] = one_run(np.cumsum(gaps) - gaps[0], 10 ** 7 * (1 + len(runs)))[0]
+    # solve requests on resident factors (cache hits): FP64 factors of the pool
+    with sv.Server(arena_bytes=arena, streams=8, batch_max=1024, small_n=512, batch_nb=nb) as s:
+        prime_x = torch.zeros(sum(pm["n"] for pm in pool), dtype=torch.float64).pin_memory()
+        po = np.concatenate([[0], np.cumsum([pm["n"] for pm in pool])])
+        for i, pm in enumerate(pool):
+            s.submit(i, sv.OP_FACTOR_SOLVE, sv.MODE_FP64, pm["t"], pm["u"], pm["n"], 1,
+                     arf=pm["arf_h"].data_ptr(), B=Bh.data_ptr(),
+                     X=prime_x.data_ptr() + 8 * int(po[i]), key=i)
+        s.wait(P)
+        m = min(R, 1000)
+        for k in range(m):
+            i = int(which[k])
+            pm = pool[i]
+            s.submit(P + k, sv.OP_SOLVE, sv.MODE_FP64, pm["t"], pm["u"], pm["n"], int(nrhs[k]),
+                     B=Bh.data_ptr() + 8 * int(offs[k]), X=Xh.data_ptr() + 8 * int(offs[k]), key=i)
+        hits = s.wait(m)
+    hl = np.array([c["t_done"] - c["t_submit"] for c in hits]) * 1e3
+    runs["resident_solves"] = {"requests": m, "cache_hit_fraction": float(np.mean([c["cache_hit"] for c in hits])),
+                               "p50_ms": float(np.percentile(hl, 50)), "p99_ms": float(np.percentile(hl, 99)),
+                               "ok": int(sum(c["status"] == 0 for c in hits))}
+    worst = max(b["bwd"] for b in bwd)
+    line = {"mode": "serve", "metric": "served solves/s, p50/p99 at <=1e-12 bwd err",
+            "value": sat["solves_per_s"], "unit": "solves/s (right-hand sides)",
+            "higher_is_better": True, "dtype": "f64 in/out (FP64 or split-TF32 + FP64 refinement)",
+            "data": "synthetic: A = Q diag(lam) Q^T, Q = 8 Householder reflectors, lam log-uniform "
+                    "on [1, kappa]",
+            "config": {"workload": f"{R} factor+solve requests per run over {P} matrices, n "
+                                   "log-uniform [64, 8192], kappa log-uniform [1e1, 1e6], nrhs ~ "
+                                   "U{1..32}, layouts uniform, FP64 / mixed uniform; arena 150 GB, "
+                                   "8 streams + batched launches for FP64 n <= 512, nrhs <= 8",
+                       "requests": R, "pool": P},
+            "runs": runs, "bwd_sampled": {"count": len(bwd), "max": worst,
+                                          "all_le_1e-12": bool(worst <= 1e-12),
+                                          "max_mixed": max([b["bwd"] for b in bwd if b["mode"] == 1] or [0.0])},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.mode == "mixed":
@@ -596,6 +745,9 @@ def main():
         return
     if args.mode == "batched":
         run_batched(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

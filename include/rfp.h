@@ -277,6 +277,91 @@ const char *rfp_status_string(int status);
 
 /* Name of the last CUDA error seen by the calling host thread inside this
  * library ("no error" if none). */
+/*
+ * Serving loop (the serving direction of the project; the paper has no
+ * counterpart): a native scheduler that accepts factor+solve, solve and
+ * invert requests of uneven order from any host thread and runs them on one
+ * GPU with continuous batching.  One scheduler thread admits requests, oldest
+ * first, as soon as a stream slot and device memory are free, so requests
+ * that arrive while others run overlap with them on the device:
+ *   - FP64 factor+solve requests with n <= small_n and nrhs <= 8 whose factor
+ *     is not resident go into one launch of the batched kernel
+ *     (rfp_dpfsv_batched) whenever one of its two streams is idle (every such
+ *     request that arrived meanwhile joins that launch, up to batch_max);
+ *   - every other request runs on its own stream (one of `streams`): FP64
+ *     PFTRF + PFTRS, the mixed-precision solve (rfp_dpfsv_mixed with
+ *     RFP_PREC_TF32X3), or PFTRI on a copy of a resident array.
+ * All device memory is one arena of arena_bytes allocated at creation.  The
+ * RFP array of a request with key >= 0 stays resident after it completes
+ * (FP64 mode: the factor; mixed mode: the FP64 matrix) and is reused by later
+ * requests with that key and the same n / layout / mode (a factor+solve on a
+ * resident key skips the upload and the factorization).  Resident arrays are
+ * admitted by their RFP bytes n(n+1)/2 * 8 and evicted least recently used
+ * first when the arena is needed, never while a request uses them.
+ * Results are independent of what else runs: every request computes exactly
+ * what the corresponding single call computes.
+ *
+ * rfp_serve_create: cfg->arena_bytes >= 1 MiB; 1 <= streams <= 64;
+ * 1 <= batch_max <= 4096; 0 <= small_n <= 512 (0: no batching); max_iter >= 0
+ * and tol > 0 for mixed requests; batch_nb[t][b]: panel width (0 = 16, or
+ * 16, 24, 32) for TRANSR t (0 'N', 1 'T') and order bucket b (n in
+ * (64 b, 64 (b + 1)]).  Returns 0 (*server set), -1 bad config, -2 null
+ * server, RFP_ERR_CUDA (arena, pinned memory or streams could not be made).
+ * rfp_serve_submit: queues a copy of *req and returns at once (0, -1 null
+ * server, -2 invalid request: layout, op, mode, n < 1, nrhs < 1 for
+ * solves, null arrays, or key < 0 for SOLVE / INVERT).  The host arrays must
+ * stay valid until the request's completion has been polled; pinned memory
+ * makes the copies asynchronous.  arf: the RFP array of A (FACTOR_SOLVE),
+ * B: n x nrhs column-major (ld n), X: receives the n x nrhs solution, or for
+ * INVERT the n(n+1)/2 RFP array of A^{-1} in the request's layout.
+ * rfp_serve_poll: up to max completions, waiting up to timeout_s for the
+ * first; returns how many were written.  A completion's status is 0, > 0 the
+ * failing pivot index (not SPD), or RFP_SERVE_E*: ETOOLARGE (cannot fit the
+ * arena even when empty), ENOKEY (no matching resident array), ENOCONV
+ * (mixed refinement did not converge), ECUDA.  Times are seconds on the host
+ * clock since creation: submitted, started (enqueued on the GPU), done
+ * (observed complete by a host callback after the result copies).
+ * rfp_serve_destroy: finishes every submitted request, then frees everything.
+ */
+#define RFP_SERVE_OP_FACTOR_SOLVE 0
+#define RFP_SERVE_OP_SOLVE 1
+#define RFP_SERVE_OP_INVERT 2
+#define RFP_SERVE_MODE_FP64 0
+#define RFP_SERVE_MODE_MIXED 1
+#define RFP_SERVE_ETOOLARGE (-101)
+#define RFP_SERVE_ENOKEY (-102)
+#define RFP_SERVE_ENOCONV (-103)
+#define RFP_SERVE_ECUDA (-104)
+typedef struct rfp_serve_config {
+    size_t arena_bytes;
+    int32_t streams, batch_max, small_n, max_iter;
+    double tol;
+    int16_t batch_nb[2][8];
+} rfp_serve_config_t;
+typedef struct rfp_serve_request {
+    int64_t id, key, n;
+    int32_t nrhs, op, mode;
+    char transr, uplo;
+    int16_t reserved;
+    const double *arf;
+    const double *B;
+    double *X;
+} rfp_serve_request_t;
+typedef struct rfp_serve_completion {
+    int64_t id;
+    int32_t status, iterations, cache_hit, batched;
+    double t_submit, t_start, t_done, backward_error;
+} rfp_serve_completion_t;
+typedef struct rfp_serve_stats {
+    int64_t submitted, completed, batches, batched_requests, cache_hits, evictions, cache_entries;
+    size_t cache_bytes, arena_in_use, arena_capacity;
+} rfp_serve_stats_t;
+int rfp_serve_create(const rfp_serve_config_t *cfg, void **server);
+int rfp_serve_submit(void *server, const rfp_serve_request_t *req);
+int rfp_serve_poll(void *server, rfp_serve_completion_t *out, int max, double timeout_s);
+int rfp_serve_stats(void *server, rfp_serve_stats_t *stats);
+int rfp_serve_destroy(void *server);
+
 const char *rfp_last_cuda_error(void);
 
 /*

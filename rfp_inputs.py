@@ -21,6 +21,11 @@ benchmark configurations describe):
   eigenvector is spread over all coordinates (n must be a power of two).
   O(n^2 log n) work: the stand-in for a Haar Q at n = 32768, where the QR of
   a Gaussian matrix would cost ~1e14 FP64 flops.
+* ``spd_reflectors(n, seed, kappa, device)``: A = Q diag(lam) Q^T with the
+  same spectrum recipe and Q the product of 8 random Householder reflectors
+  I - 2 v v^T (v uniform on the sphere): O(n^2) work per reflector, any n,
+  every entry non-zero; the serving workload's generator (orders up to 8192
+  for hundreds of matrices).
 * ``spd_integer_factor(n, seed)``: A = L0 L0^T with L0 unit lower triangular
   with small integer entries; the exact Cholesky factor is L0.
 * ``pascal(n)``: P_ij = C(i+j, i); its Cholesky factor is L_ij = C(i, j).
@@ -124,6 +129,27 @@ def spd_butterfly(n: int, seed: int = 0, kappa: float = 1e4, device=None):
                 V[:, :, 1] = ss * x + cc * y
         h *= 2
     return 0.5 * (A + A.T)
+
+
+def spd_reflectors(n: int, seed: int = 0, kappa: float = 1e4, device=None, reflectors: int = 8):
+    """A = Q diag(lam) Q^T, Q = H_1 ... H_r with H_i = I - 2 v_i v_i^T (torch
+    FP64 on ``device``, returned as a torch tensor)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = torch.rand(n, dtype=torch.float64, device=device, generator=g)
+    lam = 10.0 ** (u * np.log10(kappa))
+    lam[0] = 1.0
+    if n > 1:
+        lam[-1] = float(kappa)
+    A = torch.diag(lam)
+    for _ in range(reflectors):
+        v = torch.randn(n, dtype=torch.float64, device=device, generator=g)
+        v /= torch.linalg.vector_norm(v)
+        # H A H with H = I - 2 v v^T:  A - 2 v w^T - 2 w v^T + 4 (v^T w) v v^T, w = A v
+        w = A @ v
+        A -= 2.0 * torch.outer(v, w) + 2.0 * torch.outer(w, v) - 4.0 * torch.dot(v, w) * torch.outer(v, v)
+    return (A + A.T) * 0.5
 
 
 def spd_integer_factor(n: int, seed: int = 0, lo: int = -2, hi: int = 2):
