@@ -717,7 +717,11 @@ def run_serve(args):
                      B=Bh.data_ptr() + 8 * int(offs[k]), X=Xh.data_ptr() + 8 * int(offs[k]), key=i)
         hits = s.wait(m)
     hl = np.array([c["t_done"] - c["t_submit"] for c in hits]) * 1e3
-    runs["resident_solves"] = {"requests": m, "cache_hit_fraction": float(np.mean([c["cache_hit"] for c in hits])),
+    hspan = max(c["t_done"] for c in hits) - min(c["t_submit"] for c in hits)
+    runs["resident_solves"] = {"requests": m, "submitted": "all at once (latency includes queueing)",
+                               "solves_per_s": float(nrhs[:m].sum()) / hspan,
+                               "requests_per_s": m / hspan,
+                               "cache_hit_fraction": float(np.mean([c["cache_hit"] for c in hits])),
                                "p50_ms": float(np.percentile(hl, 50)), "p99_ms": float(np.percentile(hl, 99)),
                                "ok": int(sum(c["status"] == 0 for c in hits))}
     worst = max(b["bwd"] for b in bwd)
