@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--mixed-n", type=int, default=32768)
     p.add_argument("--mixed-nrhs", type=int, default=64)
     p.add_argument("--kappas", default="1e2,1e4,1e6")
-    p.add_argument("--precs", default="fp32,tf32x3,tf32,bf16")
+    p.add_argument("--precs", default="fp32,tf32x3,bf16x6,tf32,bf16")
     p.add_argument("--max-iter", type=int, default=30, help="refinement steps (mixed mode)")
     p.add_argument("--batch", type=int, default=4096, help="batched mode: matrices per batch")
     p.add_argument("--serve-requests", type=int, default=1000,
@@ -410,7 +410,7 @@ def run_mixed(args):
     stream = torch.cuda.current_stream(dev)
     n, nrhs = args.mixed_n, args.mixed_nrhs
     precs = {"fp32": rfp.RFP_PREC_FP32, "tf32": rfp.RFP_PREC_TF32, "bf16": rfp.RFP_PREC_BF16,
-             "tf32x3": rfp.RFP_PREC_TF32X3}
+             "tf32x3": rfp.RFP_PREC_TF32X3, "bf16x6": rfp.RFP_PREC_BF16X6}
     results, fp64 = [], []
     Bh = gen.rhs(n, nrhs, seed=3)
     dB = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev)

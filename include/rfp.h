@@ -161,7 +161,12 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
  *        into two TF32 parts (hi = tf32(x), lo = tf32(x - hi), both rounded
  *        to nearest) and the update sums the three products
  *        hi hi^T + lo hi^T + hi lo^T on the tensor cores: FP32's 24 bits per
- *        operand instead of TF32's 11 (panel buffer four times larger).
+ *        operand instead of TF32's 11 (panel buffer four times larger);
+ *   prec RFP_PREC_BF16X6: the BF16 tensor cores with FP32-accurate updates:
+ *        each panel value is split into three BF16 parts (hi + mid + lo,
+ *        Henry, Tang and Heinecke's bfloat16 splitting) and the update sums
+ *        the six products hi hi, hi mid, mid hi, mid mid, hi lo, lo hi (panel
+ *        buffer twelve times a BF16 panel).
  * Refinement: X = 0, R = B, then up to max_iter times D = (L L^T)^{-1} R in
  * FP32, X += D in FP64, R = B - A X in FP64 from arf; it stops as soon as
  * max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol, decided on
@@ -179,6 +184,7 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
  */
 #define RFP_PREC_FP32 2
 #define RFP_PREC_TF32X3 3
+#define RFP_PREC_BF16X6 4
 typedef struct rfp_mixed_status {
     int32_t info, iterations, converged, tc_error;
     double backward_error;
@@ -203,8 +209,8 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
  * rfp_dpfsv_mixed_workspace exceeds rfp_dpfsv_mixed_noalloc_capacity() are
  * rejected: -3 if n does not fit even with nrhs = 1, else -4 (for example
  * n = 2048 with nrhs <= 256 fits in the FP32, TF32 and BF16 modes; the
- * split-TF32 mode, whose panel buffer is four times larger, fits n = 1664
- * with nrhs <= 256).
+ * split modes, whose panel buffers are larger, fit n = 1664 (split-TF32)
+ * and n = 1472 (split-BF16) with nrhs <= 256).
  * All calls share the array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race on it; serialize them.  The array keeps
  * the previous call's contents; the solve itself clears what must start at

@@ -29,6 +29,7 @@ from .binding import (  # noqa: F401
     RFP_PREC_TF32,
     RFP_PREC_FP32,
     RFP_PREC_TF32X3,
+    RFP_PREC_BF16X6,
     rfp_dpfsv_mixed,
     rfp_dpfsv_mixed_workspace,
     mixed_status,

@@ -48,7 +48,7 @@ SIGNATURES = {
     "rfp_ssyrk_tc": [_c, _i64, _i64, ctypes.c_float, _p, _i64, ctypes.c_int, ctypes.c_float, _p,
                      _i64, _i32p, _p],
 }
-RFP_PREC_BF16, RFP_PREC_TF32, RFP_PREC_FP32, RFP_PREC_TF32X3 = 0, 1, 2, 3
+RFP_PREC_BF16, RFP_PREC_TF32, RFP_PREC_FP32, RFP_PREC_TF32X3, RFP_PREC_BF16X6 = 0, 1, 2, 3, 4
 
 
 class RfpMixedStatus(ctypes.Structure):

@@ -123,6 +123,62 @@ cudaError_t split_tf32(cudaStream_t st, View<float> src, float *Q, int64_t rows,
     return cudaGetLastError();
 }
 
+// Split of an FP32 panel into three BF16 parts (Henry, Tang and Heinecke's
+// bfloat16 splitting): hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi -
+// mid), each difference exact in FP32, so hi + mid + lo carries FP32's 24
+// bits.  Row r of QA holds the K-segments [hi | hi | mid | mid | hi | lo] and
+// row r of QB [hi | mid | hi | mid | lo | hi] (width seg each), so one
+// K = 6 seg product QA QB^T sums the six terms hi hi^T, hi mid^T, mid hi^T,
+// mid mid^T, hi lo^T, lo hi^T; the dropped ones are below 2^-24 |x y|.
+__global__ void __launch_bounds__(256) split_bf16x3_kernel(View<float> src, __nv_bfloat16 *QA,
+                                                           __nv_bfloat16 *QB, int64_t rows,
+                                                           int64_t cols, int64_t seg,
+                                                           const int32_t *stop)
+{
+    __shared__ float tile[kCvtTile][kCvtTile + 1];
+    if (stop && *stop) return;
+    const int64_t r0 = (int64_t)blockIdx.y * kCvtTile, c0 = (int64_t)blockIdx.x * kCvtTile;
+    const int fast = threadIdx.x % kCvtTile, slow0 = threadIdx.x / kCvtTile;
+    const bool srow = src.rs == 1;
+#pragma unroll
+    for (int q = 0; q < kCvtTile / 8; ++q) {
+        const int sl = slow0 + 8 * q;
+        const int ti = srow ? fast : sl, tj = srow ? sl : fast;
+        if (r0 + ti < rows && c0 + tj < cols) tile[ti][tj] = src(r0 + ti, c0 + tj);
+    }
+    __syncthreads();
+    const int64_t pitch = 6 * seg;
+#pragma unroll
+    for (int q = 0; q < kCvtTile / 8; ++q) {
+        const int ti = slow0 + 8 * q, tj = fast;
+        const int64_t r = r0 + ti, k = c0 + tj;
+        if (r < rows && k < cols) {
+            const float x = tile[ti][tj];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+            __nv_bfloat16 *a = QA + r * pitch + k, *b = QB + r * pitch + k;
+            a[0] = hi;        b[0] = hi;
+            a[seg] = hi;      b[seg] = mid;
+            a[2 * seg] = mid; b[2 * seg] = hi;
+            a[3 * seg] = mid; b[3 * seg] = mid;
+            a[4 * seg] = hi;  b[4 * seg] = lo;
+            a[5 * seg] = lo;  b[5 * seg] = hi;
+        }
+    }
+}
+
+cudaError_t split_bf16x3(cudaStream_t st, View<float> src, __nv_bfloat16 *QA, __nv_bfloat16 *QB,
+                         int64_t rows, int64_t cols, int64_t seg, const int32_t *stop)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((cols + kCvtTile - 1) / kCvtTile), (unsigned)((rows + kCvtTile - 1) / kCvtTile));
+    split_bf16x3_kernel<<<grid, 256, 0, st>>>(src, QA, QB, rows, cols, seg, stop);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // X += (double) D, n x nrhs.
 __global__ void axpy_kernel(View<double> X, View<float> D, int64_t n, int64_t nrhs,
                             const int32_t *stop)

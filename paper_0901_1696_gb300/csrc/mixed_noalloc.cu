@@ -13,7 +13,8 @@
 //     process exits;
 //   * problems whose workspace (rfp_dpfsv_mixed_workspace) exceeds 32 MiB are
 //     rejected (for example n = 2048 with nrhs up to 256 fits in the FP32,
-//     TF32 and BF16 modes, n = 1664 in the split-TF32 mode);
+//     TF32 and BF16 modes, n = 1664 in the split-TF32 mode and n = 1472 in
+//     the split-BF16 mode);
 //   * all calls share the one array: calls whose work overlaps on the GPU (two
 //     streams, or two host threads) race on it and give wrong results;
 //     serialize them;

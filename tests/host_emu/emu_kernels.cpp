@@ -598,6 +598,37 @@ cudaError_t split_tf32(cudaStream_t, View<float> src, float *Q, int64_t rows, in
     return L.commit();
 }
 
+cudaError_t split_bf16x3(cudaStream_t, View<float> src, __nv_bfloat16 *QA, __nv_bfloat16 *QB,
+                         int64_t rows, int64_t cols, int64_t seg, const int32_t *stop)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    Launch L;
+    const int64_t T = 32, gy = (rows + T - 1) / T, gx = (cols + T - 1) / T;
+    for (int64_t by = 0; by < gy; ++by)
+        for (int64_t bx = 0; bx < gx; ++bx) {
+            L.cta = (int)(by * gx + bx);
+            if (aborted(L, stop)) continue;
+            for (int64_t r = by * T; r < std::min(rows, by * T + T); ++r)
+                for (int64_t k = bx * T; k < std::min(cols, bx * T + T); ++k) {
+                    const float x = L.rd(&src(r, k));
+                    uint16_t bh, bm, bl;
+                    const float hi = bf16_round(x, &bh);
+                    const float r1 = x - hi;
+                    const float mid = bf16_round(r1, &bm);
+                    bf16_round(r1 - mid, &bl);
+                    const uint16_t a[6] = {bh, bh, bm, bm, bh, bl}, b[6] = {bh, bm, bh, bm, bl, bh};
+                    for (int q = 0; q < 6; ++q) {
+                        __nv_bfloat16 *pa = QA + r * 6 * seg + q * seg + k, *pb = QB + r * 6 * seg + q * seg + k;
+                        L.wr_any(pa, 2);
+                        L.pend_b.push_back({pa, a[q]});
+                        L.wr_any(pb, 2);
+                        L.pend_b.push_back({pb, b[q]});
+                    }
+                }
+        }
+    return L.commit();
+}
+
 cudaError_t add_correction(cudaStream_t, View<double> X, View<float> D, int64_t n, int64_t nrhs,
                            const int32_t *stop)
 {

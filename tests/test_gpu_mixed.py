@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 rfp = pytest.importorskip("paper_0901_1696_gb300.binding")
 
-PRECS = {"fp32": 2, "tf32": 1, "bf16": 0, "tf32x3": 3}
+PRECS = {"fp32": 2, "tf32": 1, "bf16": 0, "tf32x3": 3, "bf16x6": 4}
 
 
 def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
@@ -40,7 +40,7 @@ def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
     return X, st
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6", "tf32", "bf16"])
 @pytest.mark.parametrize("transr,uplo,n", [("N", "L", 100), ("T", "U", 513), ("N", "U", 1300),
                                            ("T", "L", 2100)])
 def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
@@ -56,7 +56,7 @@ def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
 
 
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6", "tf32", "bf16"])
 def test_mixed_conditioning(prec, kappa):
     n = 1200
     A = gen.spd_spectrum(n, seed=7, kappa=kappa)
@@ -64,7 +64,8 @@ def test_mixed_conditioning(prec, kappa):
     X, st = solve_mixed("N", "L", A, B, PRECS[prec], max_iter=40)
     assert st["tc_error"] == 0
     bwd = oracle.solve_backward_error(A, X, B) if st["info"] == 0 else np.inf
-    u_f = {"fp32": 2.0 ** -24, "tf32x3": 2.0 ** -21, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
+    u_f = {"fp32": 2.0 ** -24, "tf32x3": 2.0 ** -22, "bf16x6": 2.0 ** -22, "tf32": 2.0 ** -11,
+           "bf16": 2.0 ** -8}[prec]
     if st["converged"]:
         assert st["backward_error"] <= 1e-15 and bwd <= 1e-14, (st, bwd)
     if kappa * u_f * 100 < 1:         # well inside the convergence condition
@@ -104,6 +105,20 @@ def test_tf32x3_refines_like_fp32():
         assert st["info"] == 0 and st["converged"] == 1, (name, st)
         its[name] = st["iterations"]
     assert its["tf32x3"] <= its["fp32"] + 1 and its["tf32x3"] < its["tf32"], its
+
+
+def test_bf16x6_reaches_fp64_accuracy_where_bf16_cannot():
+    """kappa = 1e6: kappa u_bf16 >> 1, so the plain BF16 factor cannot drive
+    the refinement; the split-BF16 updates (same tensor cores, six products)
+    reach the FP64 bar like the FP32 factor."""
+    n = 2100
+    A = gen.spd_spectrum(n, seed=13, kappa=1e6)
+    B = gen.rhs(n, 4, seed=14)
+    X, st = solve_mixed("T", "L", A, B, PRECS["bf16x6"], max_iter=60)
+    assert st["info"] == 0 and st["tc_error"] == 0 and st["converged"] == 1, st
+    assert oracle.solve_backward_error(A, X, B) <= 1e-14
+    _, st16 = solve_mixed("T", "L", A, B, PRECS["bf16"], max_iter=60)
+    assert st16["info"] != 0 or st16["converged"] == 0
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32"])

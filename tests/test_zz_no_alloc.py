@@ -70,6 +70,7 @@ def test_no_alloc_rejects_problems_beyond_its_scratch():
     for prec in (0, 1, 2):
         assert rfp.rfp_dpfsv_mixed_workspace(n, 256, prec) <= cap
     assert rfp.rfp_dpfsv_mixed_workspace(1664, 256, 3) <= cap
+    assert rfp.rfp_dpfsv_mixed_workspace(1472, 256, 4) <= cap
     assert rfp.rfp_dpfsv_mixed_workspace(n, 1, 3) > cap
     assert rfp.rfp_dpfsv_mixed_workspace(n, 4096, 2) > cap
     with pytest.raises(rfp.RfpError) as e:
