@@ -21,3 +21,15 @@ from .oracle import (  # noqa: F401
     split,
     unpack,
 )
+from .lapack_surface import (  # noqa: F401
+    full_to_tp,
+    lansf,
+    sfrk,
+    tfsm,
+    tfttp,
+    tftri,
+    tp_index,
+    tp_to_full,
+    tpttf,
+    tri_inverse,
+)
