@@ -284,6 +284,63 @@ const char *rfp_status_string(int status);
 /* Name of the last CUDA error seen by the calling host thread inside this
  * library ("no error" if none). */
 /*
+ * The rest of the LAPACK 3.2 RFP routine set (the paper's table of new
+ * routines), with LAPACK's argument order and meaning; "d" FP64, "s" FP32.
+ * All arrays are device memory, all calls are asynchronous on `stream`, and
+ * the return value is 0, -i for an invalid argument i (checked before
+ * anything is enqueued), or RFP_ERR_CUDA.
+ *
+ * rfp_?tpttf / rfp_?tfttp: standard packed storage (AP, n(n+1)/2 elements,
+ *   column-major: UPLO 'U' AP[i + j(j+1)/2] = A(i, j), i <= j; 'L'
+ *   AP[i + j(2n-j-1)/2] = A(i, j), i >= j) to RFP and back, bit-exact.
+ *   Arguments: 1 transr, 2 uplo, 3 n, 4 source, 5 destination, 6 stream.
+ * rfp_?tftri: the inverse of the triangular matrix in RFP, in place (the
+ *   first stage of PFTRI).  diag 'N' or 'U'; with 'U' the diagonal is taken
+ *   as 1 and is left unchanged, and `work` (n elements) holds it meanwhile.
+ *   *info (device) = 0, or the first exactly zero diagonal (1-based).
+ *   Arguments: 1 transr, 2 uplo, 3 diag, 4 n, 5 arf, 6 info, 7 work, 8 stream.
+ * rfp_?sfrk: C := alpha op(A) op(A)^T + beta C for the symmetric C in RFP
+ *   (its UPLO triangle), op(A) = A (trans 'N', A n x k, lda >= max(1, n)) or
+ *   A^T (trans 'T', A k x n, lda >= max(1, k)), A column-major; beta = 0:
+ *   C is not read; alpha = 0 or k = 0: A is not read.
+ *   Arguments: 1 transr, 2 uplo, 3 trans, 4 n, 5 k, 6 alpha, 7 A, 8 lda,
+ *   9 beta, 10 C, 11 stream.
+ * rfp_?tfsm: B := alpha op(A)^{-1} B (side 'L', A of order m) or
+ *   alpha B op(A)^{-1} (side 'R', A of order n), A triangular in RFP,
+ *   op(A) = A (trans 'N') or A^T ('T'), unit diagonal when diag = 'U' (not
+ *   read); B m x n column-major, ldb >= max(1, m); alpha = 0: B := 0 and A
+ *   is not read.
+ *   Arguments: 1 transr, 2 side, 3 uplo, 4 trans, 5 diag, 6 m, 7 n, 8 alpha,
+ *   9 arf, 10 B, 11 ldb, 12 stream.
+ * rfp_?lansf: *value (device) = the norm of the symmetric matrix in RFP:
+ *   norm 'M' max |a_ij|, '1' / 'O' / 'I' one / infinity norm (equal for a
+ *   symmetric matrix), 'F' / 'E' Frobenius norm (scaled sums, no overflow for
+ *   finite entries); a NaN entry gives NaN.  work: 2n elements.  The result
+ *   does not depend on scheduling (fixed-order reductions).
+ *   Arguments: 1 norm, 2 transr, 3 uplo, 4 n, 5 arf, 6 work, 7 value, 8 stream.
+ */
+int rfp_dtpttf(char transr, char uplo, int64_t n, const double *ap, double *arf, void *stream);
+int rfp_stpttf(char transr, char uplo, int64_t n, const float *ap, float *arf, void *stream);
+int rfp_dtfttp(char transr, char uplo, int64_t n, const double *arf, double *ap, void *stream);
+int rfp_stfttp(char transr, char uplo, int64_t n, const float *arf, float *ap, void *stream);
+int rfp_dtftri(char transr, char uplo, char diag, int64_t n, double *arf, int32_t *info,
+               double *work, void *stream);
+int rfp_stftri(char transr, char uplo, char diag, int64_t n, float *arf, int32_t *info,
+               float *work, void *stream);
+int rfp_dsfrk(char transr, char uplo, char trans, int64_t n, int64_t k, double alpha,
+              const double *A, int64_t lda, double beta, double *C, void *stream);
+int rfp_ssfrk(char transr, char uplo, char trans, int64_t n, int64_t k, float alpha,
+              const float *A, int64_t lda, float beta, float *C, void *stream);
+int rfp_dtfsm(char transr, char side, char uplo, char trans, char diag, int64_t m, int64_t n,
+              double alpha, const double *arf, double *B, int64_t ldb, void *stream);
+int rfp_stfsm(char transr, char side, char uplo, char trans, char diag, int64_t m, int64_t n,
+              float alpha, const float *arf, float *B, int64_t ldb, void *stream);
+int rfp_dlansf(char norm, char transr, char uplo, int64_t n, const double *arf, double *work,
+               double *value, void *stream);
+int rfp_slansf(char norm, char transr, char uplo, int64_t n, const float *arf, float *work,
+               float *value, void *stream);
+
+/*
  * Serving loop (the serving direction of the project; the paper has no
  * counterpart): a native scheduler that accepts factor+solve, solve and
  * invert requests of uneven order from any host thread and runs them on one

@@ -48,6 +48,15 @@ SIGNATURES = {
     "rfp_ssyrk_tc": [_c, _i64, _i64, ctypes.c_float, _p, _i64, ctypes.c_int, ctypes.c_float, _p,
                      _i64, _i32p, _p],
 }
+for _x, _f in (("d", ctypes.c_double), ("s", ctypes.c_float)):
+    SIGNATURES.update({
+        f"rfp_{_x}tpttf": [_c, _c, _i64, _p, _p, _p],
+        f"rfp_{_x}tfttp": [_c, _c, _i64, _p, _p, _p],
+        f"rfp_{_x}tftri": [_c, _c, _c, _i64, _p, _i32p, _p, _p],
+        f"rfp_{_x}sfrk": [_c, _c, _c, _i64, _i64, _f, _p, _i64, _f, _p, _p],
+        f"rfp_{_x}tfsm": [_c, _c, _c, _c, _c, _i64, _i64, _f, _p, _p, _i64, _p],
+        f"rfp_{_x}lansf": [_c, _c, _c, _i64, _p, _p, _p, _p],
+    })
 RFP_PREC_BF16, RFP_PREC_TF32, RFP_PREC_FP32, RFP_PREC_TF32X3, RFP_PREC_BF16X6 = 0, 1, 2, 3, 4
 
 
@@ -254,6 +263,50 @@ class Library:
                                    _addr(d_err), _stream(stream))
         return self._check("rfp_ssyrk_tc", rc)
 
+    # ---- the rest of the LAPACK 3.2 RFP routine set ----
+    def _surface(self, name, args, stream):
+        conv = [(_ch(a) if isinstance(a, str) else (_addr(a) if hasattr(a, "data_ptr")
+                 or hasattr(a, "ctypes") else a)) for a in args]
+        return self._check(name, getattr(self.lib, name)(*conv, _stream(stream)))
+
+    def rfp_dtpttf(self, transr, uplo, n, ap, arf, stream=None):
+        return self._surface("rfp_dtpttf", (transr, uplo, n, ap, arf), stream)
+
+    def rfp_stpttf(self, transr, uplo, n, ap, arf, stream=None):
+        return self._surface("rfp_stpttf", (transr, uplo, n, ap, arf), stream)
+
+    def rfp_dtfttp(self, transr, uplo, n, arf, ap, stream=None):
+        return self._surface("rfp_dtfttp", (transr, uplo, n, arf, ap), stream)
+
+    def rfp_stfttp(self, transr, uplo, n, arf, ap, stream=None):
+        return self._surface("rfp_stfttp", (transr, uplo, n, arf, ap), stream)
+
+    def rfp_dtftri(self, transr, uplo, diag, n, arf, info, work=None, stream=None):
+        return self._surface("rfp_dtftri", (transr, uplo, diag, n, arf, info, work), stream)
+
+    def rfp_stftri(self, transr, uplo, diag, n, arf, info, work=None, stream=None):
+        return self._surface("rfp_stftri", (transr, uplo, diag, n, arf, info, work), stream)
+
+    def rfp_dsfrk(self, transr, uplo, trans, n, k, alpha, A, lda, beta, C, stream=None):
+        return self._surface("rfp_dsfrk", (transr, uplo, trans, n, k, alpha, A, lda, beta, C), stream)
+
+    def rfp_ssfrk(self, transr, uplo, trans, n, k, alpha, A, lda, beta, C, stream=None):
+        return self._surface("rfp_ssfrk", (transr, uplo, trans, n, k, alpha, A, lda, beta, C), stream)
+
+    def rfp_dtfsm(self, transr, side, uplo, trans, diag, m, n, alpha, arf, B, ldb, stream=None):
+        return self._surface("rfp_dtfsm", (transr, side, uplo, trans, diag, m, n, alpha, arf, B, ldb),
+                             stream)
+
+    def rfp_stfsm(self, transr, side, uplo, trans, diag, m, n, alpha, arf, B, ldb, stream=None):
+        return self._surface("rfp_stfsm", (transr, side, uplo, trans, diag, m, n, alpha, arf, B, ldb),
+                             stream)
+
+    def rfp_dlansf(self, norm, transr, uplo, n, arf, work, value, stream=None):
+        return self._surface("rfp_dlansf", (norm, transr, uplo, n, arf, work, value), stream)
+
+    def rfp_slansf(self, norm, transr, uplo, n, arf, work, value, stream=None):
+        return self._surface("rfp_slansf", (norm, transr, uplo, n, arf, work, value), stream)
+
     def rfp_dpftrs(self, transr, uplo, n, nrhs, arf, B, ldb, stream=None):
         return self._trs("rfp_dpftrs", transr, uplo, n, nrhs, arf, B, ldb, stream)
 
@@ -296,3 +349,9 @@ rfp_dpfsv_mixed_noalloc = _fwd("rfp_dpfsv_mixed_noalloc")
 rfp_batch_plan_bytes, rfp_batch_plan = _fwd("rfp_batch_plan_bytes"), _fwd("rfp_batch_plan")
 rfp_dpfsv_batched, rfp_spfsv_batched = _fwd("rfp_dpfsv_batched"), _fwd("rfp_spfsv_batched")
 rfp_dpfsv_mixed_noalloc_capacity = _fwd("rfp_dpfsv_mixed_noalloc_capacity")
+rfp_dtpttf, rfp_stpttf = _fwd("rfp_dtpttf"), _fwd("rfp_stpttf")
+rfp_dtfttp, rfp_stfttp = _fwd("rfp_dtfttp"), _fwd("rfp_stfttp")
+rfp_dtftri, rfp_stftri = _fwd("rfp_dtftri"), _fwd("rfp_stftri")
+rfp_dsfrk, rfp_ssfrk = _fwd("rfp_dsfrk"), _fwd("rfp_ssfrk")
+rfp_dtfsm, rfp_stfsm = _fwd("rfp_dtfsm"), _fwd("rfp_stfsm")
+rfp_dlansf, rfp_slansf = _fwd("rfp_dlansf"), _fwd("rfp_slansf")

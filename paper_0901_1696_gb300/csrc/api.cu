@@ -169,6 +169,119 @@ int pftri_entry(char transr, char uplo, int64_t n, T *arf, int32_t *info, void *
     return finish(rfp::pftri_impl<T>((cudaStream_t)stream, L, arf, info));
 }
 
+bool is_trans(char c) { return c == 'T' || c == 't'; }
+bool valid_trans(char c) { return c == 'N' || c == 'n' || is_trans(c); }
+bool valid_diag(char c) { return c == 'N' || c == 'n' || c == 'U' || c == 'u'; }
+bool is_unit(char c) { return c == 'U' || c == 'u'; }
+
+template <typename T>
+int tp_entry(char transr, char uplo, int64_t n, T *src, T *dst, void *stream, bool to_rfp)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN) return -3;
+    if (n == 0) return RFP_OK;
+    if (!src || !aligned(src)) return -4;
+    if (!dst || !aligned(dst)) return -5;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    // to_rfp: src = AP, dst = ARF; else src = ARF, dst = AP
+    return finish(rfp::tp_copy<T>((cudaStream_t)stream, L, to_rfp ? dst : src, to_rfp ? src : dst,
+                                  is_lower(uplo), to_rfp));
+}
+
+template <typename T>
+int tftri_entry(char transr, char uplo, char diag, int64_t n, T *arf, int32_t *info, T *work,
+                void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (!valid_diag(diag)) return -3;
+    if (n < 0 || n > kMaxN) return -4;
+    if (n > 0 && (!arf || !aligned(arf))) return -5;
+    if (!info || !aligned(info)) return -6;
+    if (n > 0 && is_unit(diag) && (!work || !aligned(work))) return -7;
+    if (n == 0) return finish(cudaMemsetAsync(info, 0, sizeof(int32_t), (cudaStream_t)stream));
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!is_unit(diag)) return finish(rfp::tftri_impl<T>(st, L, arf, info));
+    cudaError_t e = rfp::unit_diag<T>(st, L, arf, work, true);
+    if (e == cudaSuccess) e = rfp::tftri_impl<T>(st, L, arf, info);
+    if (e == cudaSuccess) e = rfp::unit_diag<T>(st, L, arf, work, false);
+    return finish(e);
+}
+
+template <typename T>
+int sfrk_entry(char transr, char uplo, char trans, int64_t n, int64_t k, T alpha, const T *A,
+               int64_t lda, T beta, T *C, void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (!valid_trans(trans)) return -3;
+    if (n < 0 || n > kMaxN) return -4;
+    if (k < 0 || k > (int64_t(1) << 40)) return -5;
+    const bool use_a = n > 0 && k > 0 && alpha != T(0);
+    if (use_a && (!A || !aligned(A))) return -7;
+    const int64_t rows = is_trans(trans) ? k : n;
+    if (lda < (rows > 1 ? rows : 1)) return -8;
+    if (n > 0 && (!C || !aligned(C))) return -10;
+    if (n == 0 || ((!use_a) && beta == T(1))) return RFP_OK;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    T *a = const_cast<T *>(A);   // read only
+    // op(A) as an n x k view: A (n x k, lda) or A^T (A k x n, lda)
+    rfp::View<T> opA = is_trans(trans) ? rfp::View<T>{a, lda, 1} : rfp::View<T>{a, 1, lda};
+    const int64_t kk = use_a ? k : 0;
+    return finish(rfp::sfrk_impl<T>((cudaStream_t)stream, L, C, opA, kk, use_a ? alpha : T(0), beta));
+}
+
+template <typename T>
+int tfsm_entry(char transr, char side, char uplo, char trans, char diag, int64_t m, int64_t n,
+               T alpha, const T *arf, T *B, int64_t ldb, void *stream)
+{
+    if (!valid_transr(transr)) return -1;
+    const bool left = side == 'L' || side == 'l';
+    if (!left && side != 'R' && side != 'r') return -2;
+    if (!valid_uplo(uplo)) return -3;
+    if (!valid_trans(trans)) return -4;
+    if (!valid_diag(diag)) return -5;
+    if (m < 0 || m > kMaxN) return -6;
+    if (n < 0 || n > kMaxN) return -7;
+    if (m == 0 || n == 0) return RFP_OK;
+    if (alpha != T(0) && (!arf || !aligned(arf))) return -9;
+    if (!B || !aligned(B)) return -10;
+    if (ldb < (m > 1 ? m : 1)) return -11;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, left ? m : n, &L);
+    // op(A) in terms of the logical lower L: UPLO 'L' stores L, 'U' stores L^T
+    const bool opT = is_lower(uplo) ? is_trans(trans) : !is_trans(trans);
+    return finish(rfp::tfsm_impl<T>((cudaStream_t)stream, L, arf, left, opT, is_unit(diag), m, n,
+                                    alpha, B, ldb));
+}
+
+template <typename T>
+int lansf_entry(char norm, char transr, char uplo, int64_t n, const T *arf, T *work, T *value,
+                void *stream)
+{
+    int which;
+    switch (norm) {
+    case 'M': case 'm': which = 0; break;
+    case '1': case 'O': case 'o': case 'I': case 'i': which = 1; break;
+    case 'F': case 'f': case 'E': case 'e': which = 2; break;
+    default: return -1;
+    }
+    if (!valid_transr(transr)) return -2;
+    if (!valid_uplo(uplo)) return -3;
+    if (n < 0 || n > kMaxN) return -4;
+    if (n > 0 && (!arf || !aligned(arf))) return -5;
+    if (n > 0 && (!work || !aligned(work))) return -6;
+    if (!value || !aligned(value)) return -7;
+    rfp::Layout L;
+    rfp::make_layout(transr, uplo, n, &L);
+    return finish(rfp::sym_norm<T>((cudaStream_t)stream, L, arf, which, work, value));
+}
+
 template <typename T>
 int batched_entry(int64_t batch, const void *d_plan, T *arf, T *B, int32_t *d_info, void *stream)
 {
@@ -367,6 +480,64 @@ int rfp_stage_times(int max, float *ms, const char **names)
         ++k;
     }
     return k;
+}
+
+// ---- the rest of the LAPACK 3.2 RFP routine set ----
+int rfp_dtpttf(char transr, char uplo, int64_t n, const double *ap, double *arf, void *stream)
+{
+    return tp_entry<double>(transr, uplo, n, const_cast<double *>(ap), arf, stream, true);
+}
+int rfp_stpttf(char transr, char uplo, int64_t n, const float *ap, float *arf, void *stream)
+{
+    return tp_entry<float>(transr, uplo, n, const_cast<float *>(ap), arf, stream, true);
+}
+int rfp_dtfttp(char transr, char uplo, int64_t n, const double *arf, double *ap, void *stream)
+{
+    return tp_entry<double>(transr, uplo, n, const_cast<double *>(arf), ap, stream, false);
+}
+int rfp_stfttp(char transr, char uplo, int64_t n, const float *arf, float *ap, void *stream)
+{
+    return tp_entry<float>(transr, uplo, n, const_cast<float *>(arf), ap, stream, false);
+}
+int rfp_dtftri(char transr, char uplo, char diag, int64_t n, double *arf, int32_t *info,
+               double *work, void *stream)
+{
+    return tftri_entry<double>(transr, uplo, diag, n, arf, info, work, stream);
+}
+int rfp_stftri(char transr, char uplo, char diag, int64_t n, float *arf, int32_t *info,
+               float *work, void *stream)
+{
+    return tftri_entry<float>(transr, uplo, diag, n, arf, info, work, stream);
+}
+int rfp_dsfrk(char transr, char uplo, char trans, int64_t n, int64_t k, double alpha,
+              const double *A, int64_t lda, double beta, double *C, void *stream)
+{
+    return sfrk_entry<double>(transr, uplo, trans, n, k, alpha, A, lda, beta, C, stream);
+}
+int rfp_ssfrk(char transr, char uplo, char trans, int64_t n, int64_t k, float alpha,
+              const float *A, int64_t lda, float beta, float *C, void *stream)
+{
+    return sfrk_entry<float>(transr, uplo, trans, n, k, alpha, A, lda, beta, C, stream);
+}
+int rfp_dtfsm(char transr, char side, char uplo, char trans, char diag, int64_t m, int64_t n,
+              double alpha, const double *arf, double *B, int64_t ldb, void *stream)
+{
+    return tfsm_entry<double>(transr, side, uplo, trans, diag, m, n, alpha, arf, B, ldb, stream);
+}
+int rfp_stfsm(char transr, char side, char uplo, char trans, char diag, int64_t m, int64_t n,
+              float alpha, const float *arf, float *B, int64_t ldb, void *stream)
+{
+    return tfsm_entry<float>(transr, side, uplo, trans, diag, m, n, alpha, arf, B, ldb, stream);
+}
+int rfp_dlansf(char norm, char transr, char uplo, int64_t n, const double *arf, double *work,
+               double *value, void *stream)
+{
+    return lansf_entry<double>(norm, transr, uplo, n, arf, work, value, stream);
+}
+int rfp_slansf(char norm, char transr, char uplo, int64_t n, const float *arf, float *work,
+               float *value, void *stream)
+{
+    return lansf_entry<float>(norm, transr, uplo, n, arf, work, value, stream);
 }
 
 }  // extern "C"

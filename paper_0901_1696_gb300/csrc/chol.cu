@@ -49,11 +49,11 @@ cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info,
 // X (rows x m) <- X L^{-T}, L the m x m lower triangle V (right-looking).
 template <typename T>
 cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
-                                          int64_t m, const int32_t *abort)
+                                          int64_t m, const int32_t *abort, bool unit)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
-        RFP_TRY(trsm_strip(st, X.sub(0, k0), V.sub(k0, k0), rows, (int)w, 1, T(1), abort));
+        RFP_TRY(trsm_strip(st, X.sub(0, k0), V.sub(k0, k0), rows, (int)w, 1, T(1), abort, unit));
         if (k1 < m)
             RFP_TRY(gemm_nt(st, X.sub(0, k1), X.sub(0, k0), V.sub(k1, k0), rows, m - k1, w,
                             T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
@@ -65,13 +65,13 @@ cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, Vie
 // the right).
 template <typename T>
 cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
-                                            int64_t m, T alpha, const int32_t *abort)
+                                            int64_t m, T alpha, const int32_t *abort, bool unit)
 {
     const int64_t nblk = (m + kNb - 1) / kNb;
     for (int64_t b = nblk - 1; b >= 0; --b) {
         const int64_t k0 = b * kNb, k1 = std::min(k0 + kNb, m), w = k1 - k0;
         const T a = (b == nblk - 1) ? alpha : T(1);
-        RFP_TRY(trsm_strip(st, X.sub(0, k0), V.sub(k0, k0), rows, (int)w, 0, a, abort));
+        RFP_TRY(trsm_strip(st, X.sub(0, k0), V.sub(k0, k0), rows, (int)w, 0, a, abort, unit));
         if (k0 > 0)   // X(:, 0:k0) = a X(:, 0:k0) - X_b L(k0:k1, 0:k0)
             RFP_TRY(gemm_nt(st, X, X.sub(0, k0), V.sub(k0, 0).t(), rows, k0, w, T(-1), a,
                             MASK_NONE, MASK_NONE, MASK_NONE, abort));
@@ -82,12 +82,12 @@ cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t rows, V
 // L X = B in place, B (m x nrhs), L the m x m lower triangle V (forward).
 template <typename T>
 cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
-                                           int64_t m, const int32_t *abort)
+                                           int64_t m, const int32_t *abort, bool unit)
 {
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
         // L_pp X_p = B_p  <=>  X_p^T L_pp^T = B_p^T
-        RFP_TRY(trsm_strip(st, B.sub(k0, 0).t(), V.sub(k0, k0), nrhs, (int)w, 1, T(1), abort));
+        RFP_TRY(trsm_strip(st, B.sub(k0, 0).t(), V.sub(k0, k0), nrhs, (int)w, 1, T(1), abort, unit));
         if (k1 < m)   // B(k1:m) -= L(k1:m, p) X_p
             RFP_TRY(gemm_nt(st, B.sub(k1, 0), V.sub(k1, k0), B.sub(k0, 0).t(), m - k1, nrhs, w,
                             T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
@@ -98,13 +98,13 @@ cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, Vi
 // L^T X = B in place, B (m x nrhs), L the m x m lower triangle V (backward).
 template <typename T>
 cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
-                                         int64_t m, const int32_t *abort)
+                                         int64_t m, const int32_t *abort, bool unit)
 {
     const int64_t nblk = (m + kNb - 1) / kNb;
     for (int64_t b = nblk - 1; b >= 0; --b) {
         const int64_t k0 = b * kNb, k1 = std::min(k0 + kNb, m), w = k1 - k0;
         // L_pp^T X_p = B_p  <=>  X_p^T L_pp = B_p^T
-        RFP_TRY(trsm_strip(st, B.sub(k0, 0).t(), V.sub(k0, k0), nrhs, (int)w, 0, T(1), abort));
+        RFP_TRY(trsm_strip(st, B.sub(k0, 0).t(), V.sub(k0, k0), nrhs, (int)w, 0, T(1), abort, unit));
         if (k0 > 0)   // B(0:k0) -= L(p, 0:k0)^T X_p
             RFP_TRY(gemm_nt(st, B, V.sub(k0, 0).t(), B.sub(k0, 0).t(), k0, nrhs, w, T(-1), T(1),
                             MASK_NONE, MASK_NONE, MASK_NONE, abort));
@@ -361,6 +361,104 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     return cudaSuccess;
 }
 
+// ---- the rest of the LAPACK 3.2 RFP routine set (Table lapack) --------------
+
+// TFTRI: the inverse of the triangle in place, i.e. stage 1 of PFTRI
+// (Section 5): W11 = L11^{-1}, W21 = -W22 L21 W11, W22 = L22^{-1}.
+template <typename T>
+cudaError_t tftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
+{
+    View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
+    RFP_TRY(check_diag(st, t1, L.n1, t2, L.n2, info));
+    if (L.n1 > 0 && L.n2 > 0) {
+        RFP_TRY(trsm_right_lower_notrans(st, s, L.n2, t1, L.n1, T(-1), info));
+        RFP_TRY(trsm_left_lower_notrans(st, s, L.n1, t2, L.n2, info));
+    }
+    RFP_TRY(trtri_blocked(st, t1, L.n1, info));
+    return trtri_blocked(st, t2, L.n2, info);
+}
+
+// SFRK: with op(A) split at n1 into A1 (rows 0..n1) and A2, the three blocks
+// of C are C11 = alpha A1 A1^T + beta C11 (lower), C21 = alpha A2 A1^T +
+// beta C21 and C22 = alpha A2 A2^T + beta C22 (lower): the paper's SYRK /
+// GEMM step 3 on each block.
+template <typename T>
+cudaError_t sfrk_impl(cudaStream_t st, const Layout &L, T *arf, View<T> opA, int64_t k, T alpha,
+                      T beta)
+{
+    View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
+    const int32_t *none = nullptr;
+    View<T> A1 = opA, A2 = opA.sub(L.n1, 0);
+    if (L.n1 > 0)
+        RFP_TRY(gemm_nt(st, t1, A1, A1, L.n1, L.n1, k, alpha, beta, MASK_LOWER, MASK_NONE,
+                        MASK_NONE, none));
+    if (L.n1 > 0 && L.n2 > 0)
+        RFP_TRY(gemm_nt(st, s, A2, A1, L.n2, L.n1, k, alpha, beta, MASK_NONE, MASK_NONE, MASK_NONE,
+                        none));
+    if (L.n2 > 0)
+        RFP_TRY(gemm_nt(st, t2, A2, A2, L.n2, L.n2, k, alpha, beta, MASK_LOWER, MASK_NONE,
+                        MASK_NONE, none));
+    return cudaSuccess;
+}
+
+// TFSM: Section 4's block substitutions with an arbitrary right-hand-side
+// block, from either side.  alpha is applied first (alpha = 0: B = 0).
+template <typename T>
+cudaError_t tfsm_impl(cudaStream_t st, const Layout &L, const T *arf_c, bool left, bool opT,
+                      bool unit, int64_t m, int64_t nc, T alpha, T *Bp, int64_t ldb)
+{
+    T *arf = const_cast<T *>(arf_c);   // read only below
+    View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
+    View<T> B{Bp, 1, ldb};
+    const int32_t *none = nullptr;
+    if (m <= 0 || nc <= 0) return cudaSuccess;
+    if (alpha != T(1))   // B = alpha B (a K = 0 product: C = 0 + beta C)
+        RFP_TRY(gemm_nt(st, B, B, B, m, nc, 0, T(0), alpha, MASK_NONE, MASK_NONE, MASK_NONE, none));
+    if (alpha == T(0)) return cudaSuccess;
+    const int64_t n1 = L.n1, n2 = L.n2;
+    if (left) {   // op(A) is m x m; B1 = rows [0, n1)
+        View<T> B1 = B, B2 = B.sub(n1, 0);
+        if (!opT) {   // L X = B
+            RFP_TRY(trsm_left_lower_notrans(st, B1, nc, t1, n1, none, unit));
+            if (n1 > 0 && n2 > 0)
+                RFP_TRY(gemm_nt(st, B2, s, B1.t(), n2, nc, n1, T(-1), T(1), MASK_NONE, MASK_NONE,
+                                MASK_NONE, none));
+            RFP_TRY(trsm_left_lower_notrans(st, B2, nc, t2, n2, none, unit));
+        } else {      // L^T X = B
+            RFP_TRY(trsm_left_lower_trans(st, B2, nc, t2, n2, none, unit));
+            if (n1 > 0 && n2 > 0)
+                RFP_TRY(gemm_nt(st, B1, s.t(), B2.t(), n1, nc, n2, T(-1), T(1), MASK_NONE,
+                                MASK_NONE, MASK_NONE, none));
+            RFP_TRY(trsm_left_lower_trans(st, B1, nc, t1, n1, none, unit));
+        }
+    } else {      // op(A) is nc x nc; B1 = columns [0, n1)
+        View<T> B1 = B, B2 = B.sub(0, n1);
+        if (!opT) {   // X L = B: X2 = B2 L22^{-1}, B1 -= X2 L21, X1 = B1 L11^{-1}
+            RFP_TRY(trsm_right_lower_notrans(st, B2, m, t2, n2, T(1), none, unit));
+            if (n1 > 0 && n2 > 0)
+                RFP_TRY(gemm_nt(st, B1, B2, s.t(), m, n1, n2, T(-1), T(1), MASK_NONE, MASK_NONE,
+                                MASK_NONE, none));
+            RFP_TRY(trsm_right_lower_notrans(st, B1, m, t1, n1, T(1), none, unit));
+        } else {      // X L^T = B: X1 = B1 L11^{-T}, B2 -= X1 L21^T, X2 = B2 L22^{-T}
+            RFP_TRY(trsm_right_lower_trans(st, B1, m, t1, n1, none, unit));
+            if (n1 > 0 && n2 > 0)
+                RFP_TRY(gemm_nt(st, B2, B1, s, m, n2, n1, T(-1), T(1), MASK_NONE, MASK_NONE,
+                                MASK_NONE, none));
+            RFP_TRY(trsm_right_lower_trans(st, B2, m, t2, n2, none, unit));
+        }
+    }
+    return cudaSuccess;
+}
+
+#define RFP_SURFACE_ORCH_INST(T)                                                                  \
+    template cudaError_t tftri_impl<T>(cudaStream_t, const Layout &, T *, int32_t *);             \
+    template cudaError_t sfrk_impl<T>(cudaStream_t, const Layout &, T *, View<T>, int64_t, T, T); \
+    template cudaError_t tfsm_impl<T>(cudaStream_t, const Layout &, const T *, bool, bool, bool,  \
+                                      int64_t, int64_t, T, T *, int64_t);
+RFP_SURFACE_ORCH_INST(float)
+RFP_SURFACE_ORCH_INST(double)
+#undef RFP_SURFACE_ORCH_INST
+
 #define RFP_REC_INST(T)                                                                          \
     template cudaError_t potrf_rec<T>(cudaStream_t, View<T>, int64_t, int32_t *, int64_t);         \
     template cudaError_t trsm_right_lower_trans_rec<T>(cudaStream_t, View<T>, int64_t, View<T>,     \
@@ -376,11 +474,13 @@ RFP_REC_INST(double)
 #define RFP_BLOCKED_INST(T)                                                                      \
     template cudaError_t potrf_blocked<T>(cudaStream_t, View<T>, int64_t, int32_t *, int64_t);     \
     template cudaError_t trsm_right_lower_trans<T>(cudaStream_t, View<T>, int64_t, View<T>, int64_t, \
-                                                   const int32_t *);                               \
+                                                   const int32_t *, bool);                         \
+    template cudaError_t trsm_right_lower_notrans<T>(cudaStream_t, View<T>, int64_t, View<T>,      \
+                                                     int64_t, T, const int32_t *, bool);           \
     template cudaError_t trsm_left_lower_notrans<T>(cudaStream_t, View<T>, int64_t, View<T>,       \
-                                                    int64_t, const int32_t *);                     \
+                                                    int64_t, const int32_t *, bool);               \
     template cudaError_t trsm_left_lower_trans<T>(cudaStream_t, View<T>, int64_t, View<T>, int64_t, \
-                                                  const int32_t *);
+                                                  const int32_t *, bool);
 RFP_BLOCKED_INST(float)
 RFP_BLOCKED_INST(double)
 #undef RFP_BLOCKED_INST

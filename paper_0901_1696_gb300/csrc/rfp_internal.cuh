@@ -126,10 +126,11 @@ cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int
                            const int32_t *abort, int splits, T *work);
 
 // Solve X * op(Ltri) = alpha * X in place for an M x w strip (w <= 64);
-// op = transpose when transL != 0.  Rows are independent.
+// op = transpose when transL != 0.  Rows are independent.  unit: Ltri has a
+// unit diagonal, which is not read.
 template <typename T>
 cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int w, int transL,
-                       T alpha, const int32_t *abort);
+                       T alpha, const int32_t *abort, bool unit = false);
 
 // In-place Cholesky of one w x w lower tile (w <= 64).  On a pivot <= 0 or
 // NaN at local column j, sets *info = base + j + 1 (when *info was 0).
@@ -178,15 +179,20 @@ cudaError_t pack_copy(cudaStream_t st, const Layout &L, bool lowerA, T *A, int64
 // double.  V is an m x m lower triangle; `abort` / `info` as for the kernels.
 template <typename T>
 cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info, int64_t base);
+// The blocked solves take unit = true for a unit-diagonal triangle (its
+// diagonal is not read).
 template <typename T>   // X (rows x m) <- X L^{-T}
 cudaError_t trsm_right_lower_trans(cudaStream_t st, View<T> X, int64_t rows, View<T> V, int64_t m,
-                                   const int32_t *abort);
+                                   const int32_t *abort, bool unit = false);
+template <typename T>   // X (rows x m) <- alpha X L^{-1}
+cudaError_t trsm_right_lower_notrans(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
+                                     int64_t m, T alpha, const int32_t *abort, bool unit = false);
 template <typename T>   // L X = B, B m x nrhs
 cudaError_t trsm_left_lower_notrans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
-                                    const int32_t *abort);
+                                    const int32_t *abort, bool unit = false);
 template <typename T>   // L^T X = B
 cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
-                                  const int32_t *abort);
+                                  const int32_t *abort, bool unit = false);
 
 // Recursive forms (split at a multiple of 64 near m/2, one long-K product per
 // level); same contracts as the blocked forms above.
@@ -232,6 +238,32 @@ size_t wavefront_sync_words(int64_t n, int64_t nrhs);
 cudaError_t trsm_wavefront(cudaStream_t st, View<float> Lv, int64_t n, const float *Inv, float *X,
                            int64_t ldx, int64_t nrhs, bool trans, int32_t *sync, int32_t *err,
                            const int32_t *stop);
+
+// The rest of the LAPACK 3.2 RFP routine set (surface.cu kernels, chol.cu
+// orchestration), all on the logical lower triangle's three block views.
+// TP <-> RFP copy (lowerTP: the packed array holds the lower triangle).
+template <typename T>
+cudaError_t tp_copy(cudaStream_t st, const Layout &L, T *arf, T *ap, bool lowerTP, bool to_rfp);
+// Norm of the symmetric matrix: which 0 max |a|, 1 one / infinity norm,
+// 2 Frobenius; work holds 2n elements; *out (device) receives the norm.
+template <typename T>
+cudaError_t sym_norm(cudaStream_t st, const Layout &L, const T *arf, int which, T *work, T *out);
+// Save the diagonal to work and set it to 1 (save), or put it back.
+template <typename T>
+cudaError_t unit_diag(cudaStream_t st, const Layout &L, T *arf, T *work, bool save);
+// TFTRI: W = L^{-1} in place (blocks W11, W21, W22); *info = first zero diagonal.
+template <typename T>
+cudaError_t tftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info);
+// SFRK: C = alpha op(A) op(A)^T + beta C on C's RFP blocks; op(A) is the
+// n x k view opA.
+template <typename T>
+cudaError_t sfrk_impl(cudaStream_t st, const Layout &L, T *arf, View<T> opA, int64_t k, T alpha,
+                      T beta);
+// TFSM: B (m x nc) = alpha op(A)^{-1} B (left) or alpha B op(A)^{-1}, op(A) =
+// L (opT false) or L^T (opT true) for the logical lower L of the RFP triangle.
+template <typename T>
+cudaError_t tfsm_impl(cudaStream_t st, const Layout &L, const T *arf, bool left, bool opT,
+                      bool unit, int64_t m, int64_t nc, T alpha, T *B, int64_t ldb);
 
 // Blocked algorithms on the RFP blocks (Sections 3-5).
 template <typename T>

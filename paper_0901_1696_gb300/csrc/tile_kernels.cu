@@ -328,6 +328,7 @@ struct TrsmArgs {
     int w, transL;
     T alpha;
     const int32_t *abort;
+    int unit;   // unit diagonal: the triangle's diagonal is taken as 1 and never read
 };
 
 template <typename T>
@@ -340,8 +341,9 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
     const int tid = threadIdx.x, w = a.w;
     const int64_t r0 = (int64_t)blockIdx.x * kStripRows;
 
-    load_tile64<kTileThreads>(Ls, a.L, w, w, [](int i, int j) { return i >= j; },
-                              [](int, int) { return T(0); });
+    const int unit = a.unit;
+    load_tile64<kTileThreads>(Ls, a.L, w, w, [unit](int i, int j) { return unit ? i > j : i >= j; },
+                              [unit](int i, int j) { return (unit && i == j) ? T(1) : T(0); });
     const int64_t rows_left = a.M - r0;
     const int rows = (int)(rows_left < kStripRows ? rows_left : kStripRows);
     View<T> Xv = a.X.sub(r0, 0);
@@ -396,8 +398,10 @@ __global__ void __launch_bounds__(kRowsPerCta) trsm_rows_f32_kernel(TrsmArgs<flo
     __shared__ float Ls[kTileMax][kTileMax + 1];
     if (a.abort && *a.abort) return;
     const int w = a.w;
-    load_tile64<kRowsPerCta>(&Ls[0][0], a.L, w, w, [](int i, int j) { return i >= j; },
-                             [w](int i, int j) { return (i == j && i >= w) ? 1.f : 0.f; });
+    const int unit = a.unit;
+    load_tile64<kRowsPerCta>(&Ls[0][0], a.L, w, w,
+                             [unit](int i, int j) { return unit ? i > j : i >= j; },
+                             [w, unit](int i, int j) { return (i == j && (unit || i >= w)) ? 1.f : 0.f; });
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * kRowsPerCta + threadIdx.x;
     if (r >= a.M) return;
@@ -438,11 +442,11 @@ static cudaError_t set_smem_once(const void *fn, int bytes)
 
 template <typename T>
 cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int w, int transL,
-                       T alpha, const int32_t *abort)
+                       T alpha, const int32_t *abort, bool unit)
 {
     if (M <= 0 || w <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4) {
-        TrsmArgs<float> a{X, Ltri, M, w, transL, alpha, abort};
+        TrsmArgs<float> a{X, Ltri, M, w, transL, alpha, abort, unit ? 1 : 0};
         const unsigned grid = (unsigned)((M + kRowsPerCta - 1) / kRowsPerCta);
         if (transL) trsm_rows_f32_kernel<1><<<grid, kRowsPerCta, 0, st>>>(a);
         else trsm_rows_f32_kernel<0><<<grid, kRowsPerCta, 0, st>>>(a);
@@ -452,7 +456,7 @@ cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int 
     const int smem = 2 * kTileMax * kTileLd * (int)sizeof(T);
     cudaError_t e = set_smem_once<T>((const void *)trsm_right_kernel<T>, smem);
     if (e != cudaSuccess) return e;
-    TrsmArgs<T> a{X, Ltri, M, w, transL, alpha, abort};
+    TrsmArgs<T> a{X, Ltri, M, w, transL, alpha, abort, unit ? 1 : 0};
     const unsigned grid = (unsigned)((M + kStripRows - 1) / kStripRows);
     trsm_right_kernel<T><<<grid, 256, smem, st>>>(a);
     note_launch();
@@ -695,7 +699,7 @@ cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int6
                                            int64_t, int64_t, T, T, int, int, int,             \
                                            const int32_t *, int, T *);                        \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,  \
-                                       const int32_t *);                                      \
+                                       const int32_t *, bool);                                \
     template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);       \
     template cudaError_t trtri_tile<T>(cudaStream_t, View<T>, int, const int32_t *);          \
     template cudaError_t lauum_tile<T>(cudaStream_t, View<T>, int, const int32_t *);          \

@@ -233,7 +233,7 @@ cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int
 
 template <typename T>
 cudaError_t trsm_strip(cudaStream_t, View<T> X, View<T> Lt, int64_t M, int w, int transL, T alpha,
-                       const int32_t *abort)
+                       const int32_t *abort, bool unit)
 {
     if (M <= 0 || w <= 0) return cudaSuccess;
     if (w > 64) { violation("trsm tile wider than 64", nullptr); return cudaErrorInvalidValue; }
@@ -243,7 +243,8 @@ cudaError_t trsm_strip(cudaStream_t, View<T> X, View<T> Lt, int64_t M, int w, in
         if (aborted(L, abort)) continue;
         std::vector<T> l(w * w), x;
         for (int i = 0; i < w; ++i)
-            for (int j = 0; j <= i; ++j) l[i * w + j] = L.rd(&Lt(i, j));
+            for (int j = 0; j <= i; ++j)
+                l[i * w + j] = (unit && i == j) ? T(1) : L.rd(&Lt(i, j));   // unit: diagonal not read
         for (int64_t r = r0; r < std::min(M, r0 + 64); ++r) {
             x.assign(w, T(0));
             for (int c = 0; c < w; ++c) x[c] = alpha * L.rd(&X(r, c));
@@ -375,6 +376,113 @@ cudaError_t trsm_wavefront(cudaStream_t, View<float> Lv, int64_t n, const float 
     }
     return L.commit();
 }
+
+// ---- the rest of the LAPACK 3.2 RFP routine set ----
+
+template <typename T>
+struct EmuLower {
+    View<T> t1, s, t2;
+    int64_t n1;
+    T *at(int64_t i, int64_t j) const
+    {
+        if (j >= n1) return &t2(i - n1, j - n1);
+        if (i >= n1) return &s(i - n1, j);
+        return &t1(i, j);
+    }
+};
+template <typename T>
+EmuLower<T> emu_lower(const Layout &Ly, T *arf)
+{
+    return EmuLower<T>{block_view(arf, Ly, Ly.t1), block_view(arf, Ly, Ly.s), block_view(arf, Ly, Ly.t2),
+                       Ly.n1};
+}
+
+// One CTA per 32 x 32 tile on or below the diagonal.
+template <typename T>
+cudaError_t tp_copy(cudaStream_t, const Layout &Ly, T *arf, T *ap, bool lowerTP, bool to_rfp)
+{
+    const int64_t n = Ly.n;
+    if (n <= 0) return cudaSuccess;
+    EmuLower<T> Lw = emu_lower(Ly, arf);
+    Launch L;
+    const int64_t t = (n + 31) / 32;
+    for (int64_t ti = 0; ti < t; ++ti)
+        for (int64_t tj = 0; tj <= ti; ++tj) {
+            L.cta = (int)(ti * t + tj);
+            for (int64_t i = ti * 32; i < std::min(n, ti * 32 + 32); ++i)
+                for (int64_t j = tj * 32; j < std::min(i + 1, tj * 32 + 32); ++j) {
+                    const int64_t p = lowerTP ? i + j * (2 * n - j - 1) / 2 : j + i * (i + 1) / 2;
+                    if (to_rfp) L.wr(Lw.at(i, j), L.rd(ap + p));
+                    else L.wr(ap + p, L.rd(Lw.at(i, j)));
+                }
+        }
+    return L.commit();
+}
+
+// Two launches: per-row values (8 rows per CTA), then one CTA for the norm.
+template <typename T>
+cudaError_t sym_norm(cudaStream_t, const Layout &Ly, const T *arf, int which, T *w, T *out)
+{
+    const int64_t n = Ly.n;
+    if (n <= 0) { *out = T(0); return cudaSuccess; }
+    EmuLower<T> Lw = emu_lower(Ly, const_cast<T *>(arf));
+    {
+        Launch L;
+        for (int64_t i = 0; i < n; ++i) {
+            L.cta = (int)(i / 8);
+            auto a = [&](int64_t j) { return j <= i ? L.rd(Lw.at(i, j)) : L.rd(Lw.at(j, i)); };
+            T v = T(0), q = T(0);
+            for (int64_t j = 0; j < n; ++j) {
+                const T x = std::fabs(a(j));
+                v = which == 1 ? v + x : std::max(v, x);
+            }
+            if (which == 2 && v > T(0))
+                for (int64_t j = 0; j < n; ++j) q += (a(j) / v) * (a(j) / v);
+            L.wr(w + i, v);
+            if (which == 2) L.wr(w + n + i, q);
+        }
+        cudaError_t e = L.commit();
+        if (e != cudaSuccess) return e;
+    }
+    Launch L;
+    T mx = T(0);
+    for (int64_t i = 0; i < n; ++i) mx = std::max(mx, L.rd(w + i));
+    T res = mx;
+    if (which == 2) {
+        T q = T(0);
+        if (mx > T(0))
+            for (int64_t i = 0; i < n; ++i) q += (L.rd(w + i) / mx) * (L.rd(w + i) / mx) * L.rd(w + n + i);
+        res = mx * std::sqrt(q);
+    }
+    L.wr(out, res);
+    return L.commit();
+}
+
+template <typename T>
+cudaError_t unit_diag(cudaStream_t, const Layout &Ly, T *arf, T *work, bool save)
+{
+    if (Ly.n <= 0) return cudaSuccess;
+    EmuLower<T> Lw = emu_lower(Ly, arf);
+    Launch L;
+    for (int64_t i = 0; i < Ly.n; ++i) {
+        L.cta = (int)(i / 256);
+        if (save) {
+            L.wr(work + i, L.rd(Lw.at(i, i)));
+            L.wr(Lw.at(i, i), T(1));
+        } else {
+            L.wr(Lw.at(i, i), L.rd(work + i));
+        }
+    }
+    return L.commit();
+}
+
+#define EMU_SURFACE_INST(T)                                                                        \
+    template cudaError_t tp_copy<T>(cudaStream_t, const Layout &, T *, T *, bool, bool);           \
+    template cudaError_t sym_norm<T>(cudaStream_t, const Layout &, const T *, int, T *, T *);      \
+    template cudaError_t unit_diag<T>(cudaStream_t, const Layout &, T *, T *, bool);
+EMU_SURFACE_INST(float)
+EMU_SURFACE_INST(double)
+#undef EMU_SURFACE_INST
 
 // One CTA per kInvBlock-wide diagonal block: reads the block's lower
 // triangle, writes the whole kInvBlock^2 slot of Inv.
@@ -739,7 +847,7 @@ template cudaError_t batched_run<float>(int64_t, const void *, float *, float *,
     template cudaError_t gemm_nt_splitk<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
                                            int64_t, T, T, int, int, int, const int32_t *, int, T *); \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,         \
-                                       const int32_t *);                                             \
+                                       const int32_t *, bool);                                       \
     template cudaError_t potrf_tile<T>(cudaStream_t, View<T>, int, int32_t *, int64_t);              \
     template cudaError_t trtri_tile<T>(cudaStream_t, View<T>, int, const int32_t *);                 \
     template cudaError_t lauum_tile<T>(cudaStream_t, View<T>, int, const int32_t *);                 \

@@ -280,3 +280,79 @@ def test_emulated_one_step_is_one_fp32_solve(emu_lib, transr, uplo, n):
     assert st["info"] == 0 and st["tc_error"] == 0 and st["iterations"] == 1, st
     ref = oracle.pftrs(transr, uplo, n, oracle.pftrf(transr, uplo, n, arf)[0], B)
     assert np.max(np.abs(X - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+# ---- the rest of the LAPACK 3.2 RFP routine set, emulated ----
+
+def _triangle_arf(transr, uplo, n, seed):
+    """A well-conditioned triangle in RFP: the Cholesky factor of B B^T / n + I."""
+    L = np.linalg.cholesky(gen.spd_bbt(n, seed=seed))
+    return oracle.pack(transr, uplo, L if uplo == "L" else L.T)
+
+
+@pytest.mark.parametrize("transr,uplo", LAYOUTS)
+@pytest.mark.parametrize("n", [1, 5, 64, 130, 201])
+def test_emulated_surface_routines(emu_lib, transr, uplo, n):
+    emu = emu_lib
+    emu.lib.emu_set_sms(152)
+    rng = np.random.default_rng(n)
+    nt = n * (n + 1) // 2
+    # TPTTF / TFTTP: bit-exact
+    ap = rng.standard_normal(nt)
+    arf = np.zeros(nt)
+    back = np.zeros(nt)
+    _register(emu, ap, arf, back)
+    emu.rfp_dtpttf(transr, uplo, n, ap, arf, 0)
+    emu.rfp_dtfttp(transr, uplo, n, arf, back, 0)
+    _ok(emu)
+    np.testing.assert_array_equal(arf, oracle.tpttf(transr, uplo, n, ap))
+    np.testing.assert_array_equal(back, ap)
+    # TFTRI, both diagonal kinds
+    for diag in "NU":
+        tri = _triangle_arf(transr, uplo, n, seed=n + 1)
+        ref, ref_info = oracle.tftri(transr, uplo, diag, n, tri)
+        work = np.zeros(n)
+        info = np.zeros(1, dtype=np.int32)
+        _register(emu, tri, work, info)
+        emu.rfp_dtftri(transr, uplo, diag, n, tri, info, work, 0)
+        _ok(emu)
+        assert info[0] == ref_info == 0
+        assert np.max(np.abs(tri - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # SFRK
+    for trans, k in (("N", 7), ("T", 70)):
+        A = rng.standard_normal((n, k) if trans == "N" else (k, n))
+        Af = np.asfortranarray(A)
+        C = rng.standard_normal((n, n))
+        C = oracle.pack(transr, uplo, C + C.T)
+        ref = oracle.sfrk(transr, uplo, trans, n, k, 0.5, A, -2.0, C)
+        _register(emu, Af, C)
+        emu.rfp_dsfrk(transr, uplo, trans, n, k, 0.5, Af, A.shape[0], -2.0, C, 0)
+        _ok(emu)
+        assert np.max(np.abs(C - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # TFSM, every side / trans / diag
+    tri = _triangle_arf(transr, uplo, n, seed=n + 2)
+    for side in "LR":
+        for trans in "NT":
+            for diag in "NU":
+                m, nc = (n, 3) if side == "L" else (4, n)
+                B = rng.standard_normal((m, nc))
+                ldb = m + 2
+                Bw = np.zeros((ldb, nc), order="F")
+                Bw[:m] = B
+                ref = oracle.tfsm(transr, side, uplo, trans, diag, m, nc, 1.25, tri, B)
+                _register(emu, tri, Bw)
+                emu.rfp_dtfsm(transr, side, uplo, trans, diag, m, nc, 1.25, tri, Bw, ldb, 0)
+                _ok(emu)
+                assert np.max(np.abs(Bw[:m] - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref))), \
+                    (side, trans, diag)
+    # LANSF
+    S = rng.standard_normal((n, n))
+    sarf = oracle.pack(transr, uplo, S + S.T)
+    work = np.zeros(2 * n)
+    val = np.zeros(1)
+    for norm in "M1OIFE":
+        _register(emu, sarf, work, val)
+        emu.rfp_dlansf(norm, transr, uplo, n, sarf, work, val, 0)
+        _ok(emu)
+        ref = oracle.lansf(norm, transr, uplo, n, sarf)
+        assert abs(val[0] - ref) <= 1e-14 * ref, norm
