@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the PFTRF step-3 launch at
 # n = 16384 (one ncu capture of the unchanged kernel, summarized under
-# profiles/): 20.29 GB + 0.281 GB.
-SYRK_TRAFFIC_N16384 = 20.57e9
+# profiles/): 6.38 GB + 0.276 GB.
+SYRK_TRAFFIC_N16384 = 6.656e9
 METRIC = "PFTRF+PFTRS TFLOP/s & % peak; served solves/s, p50/p99 at ≤1e-12 bwd err"
 LAYOUTS = [(t, u) for t in "NT" for u in "LU"]
 
@@ -61,7 +61,7 @@ def parse():
                         "reference step)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["fp64", "mixed", "batched", "serve"], default="fp64",
+    p.add_argument("--mode", choices=["fp64", "mixed", "batched", "serve", "surface"], default="fp64",
                    help="fp64: the FP64 hot path (default line); mixed: the mixed-precision "
                         "solve at n = 32768 against the FP64 path (its own line)")
     p.add_argument("--mixed-n", type=int, default=32768)
@@ -742,6 +742,100 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_surface(args):
+    """The rest of the LAPACK 3.2 RFP surface at the bench's order (FP64, one
+    layout pair per routine): TPTTF / TFTTP and LANSF against HBM bandwidth
+    (their algorithmic bytes: read + write of the packed and RFP arrays; one
+    read of the RFP array per row pass of LANSF's two), SFRK and TFSM against
+    the FP64 pipe (n^2 k and m^2 nc flops times 2 / 1), TFTRI by time (n^3/3
+    flops).  Event-timed, median of `--steps` after `--warmup`."""
+    import numpy as np
+    import torch
+
+    import rfp_inputs as gen
+    from paper_0901_1696_gb300 import binding as rfp
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    n = args.n
+    nt = n * (n + 1) // 2
+    peaks = {}
+    mp = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        with open(mp) as f:
+            peaks = json.load(f)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    ap = torch.rand(nt, dtype=torch.float64, device=dev, generator=g)
+    arf = torch.empty(nt, dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps=None):
+        reps = reps or max(args.steps, 3)
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize(dev)
+            ts.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ts))
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = {}
+    ms = timed(lambda: lib.rfp_dtpttf("N", "L", n, ap, arf))
+    out["tpttf"] = {"ms": ms, "gbs": 16 * nt / (ms * 1e-3) / 1e9}
+    back = torch.empty_like(ap)
+    ms = timed(lambda: lib.rfp_dtfttp("T", "U", n, arf, back))
+    out["tfttp"] = {"ms": ms, "gbs": 16 * nt / (ms * 1e-3) / 1e9}
+    work = torch.empty(2 * n, dtype=torch.float64, device=dev)
+    val = torch.empty(1, dtype=torch.float64, device=dev)
+    for norm in ("M", "1", "F"):
+        ms = timed(lambda: lib.rfp_dlansf(norm, "N", "L", n, arf, work, val))
+        reads = 8 * nt * (2 if norm != "F" else 4)   # each row reads its full symmetric row once (twice for F)
+        out[f"lansf_{norm}"] = {"ms": ms, "gbs_algorithmic": 8 * nt / (ms * 1e-3) / 1e9,
+                                "gbs_touched": reads / (ms * 1e-3) / 1e9}
+    k = 256
+    A = torch.rand(n, k, dtype=torch.float64, device=dev, generator=g)   # row-major n x k = col-major k x n
+    ms = timed(lambda: lib.rfp_dsfrk("N", "L", "T", n, k, 1.0, A, k, 1.0, arf))
+    out["sfrk"] = {"ms": ms, "k": k, "tflops": float(n) * (n + 1) * k / (ms * 1e-3) / 1e12}
+    # TFSM with a well-conditioned triangle: the factor of the bench's matrix
+    Afull = gen.spd_butterfly(n, seed=0, kappa=1e4, device=dev) if n & (n - 1) == 0 else \
+        gen.spd_spectrum(n, seed=0, kappa=1e4, device=dev)
+    lib.rfp_dpack("N", "L", n, Afull, n, arf)
+    del Afull
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    lib.rfp_dpftrf("N", "L", n, arf, info)
+    nc = 256
+    B0 = torch.rand(nc, n, dtype=torch.float64, device=dev, generator=g)
+    B = B0.clone()
+    ms = timed(lambda: (B.copy_(B0), lib.rfp_dtfsm("N", "L", "L", "N", "N", n, nc, 1.0, arf, B, n)))
+    ms_copy = timed(lambda: B.copy_(B0))
+    out["tfsm"] = {"ms": ms - ms_copy, "nrhs": nc,
+                   "tflops": float(n) * n * nc / ((ms - ms_copy) * 1e-3) / 1e12}
+    fac = arf.clone()
+    ms = timed(lambda: (arf.copy_(fac), lib.rfp_dtftri("N", "L", "N", n, arf, info)), reps=3)
+    ms_copy = timed(lambda: arf.copy_(fac))
+    out["tftri"] = {"ms": ms - ms_copy, "tflops": n ** 3 / 3 / ((ms - ms_copy) * 1e-3) / 1e12}
+    clocks = sampler.stop()
+    fp64 = fp64_peak_tflops(clocks["sm_mhz"])
+    for key in ("tpttf", "tfttp"):
+        out[key]["frac_of_hbm"] = out[key]["gbs"] / hbm
+    for key in ("sfrk", "tfsm", "tftri"):
+        out[key]["frac_of_fp64_pipe"] = out[key]["tflops"] / fp64
+    line = {"mode": "surface", "metric": "LAPACK 3.2 RFP surface at n = %d (FP64)" % n,
+            "unit": "mixed (see each routine)", "n": n, "hbm_peak_gbs": hbm,
+            "fp64_peak_tflops": fp64, "routines": out, "clocks": clocks,
+            "data": "synthetic: uniform [0, 1) arrays; TFSM / TFTRI on the factor of the bench matrix"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.mode == "mixed":
@@ -752,6 +846,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "surface":
+        run_surface(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

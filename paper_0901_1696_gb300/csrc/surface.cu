@@ -135,6 +135,103 @@ __global__ void __launch_bounds__(1024) norm_final_kernel(const T *w, int64_t n,
     if (tid == 0) *out = mx * sqrt(red[0]);
 }
 
+// Flat pass over the RFP array for the max and Frobenius norms: every
+// element of the logical triangle once, coalesced (thread t of CTA b takes
+// elements b * 256 + t + k * G * 256).  CTA b < G writes w[b] = max |a| over
+// its elements and, for Frobenius, w[G + b] = sum (a / w[b])^2; CTA G (only
+// for Frobenius) does the same over the n diagonal elements (read through
+// the views) into w[2G], w[2G + 1].  Fixed-order block reductions.
+constexpr int kFlatThreads = 256, kFlatPerThread = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) flat_norm_kernel(const T *arf, int64_t nt,
+                                                                 LowerRfp<T> L, int64_t n, int ssq,
+                                                                 T *w, int64_t G)
+{
+    __shared__ T red[kFlatThreads];
+    const int tid = threadIdx.x;
+    const bool diag = (int64_t)blockIdx.x == G;
+    const int64_t total = diag ? n : nt;
+    const int64_t start = diag ? tid : (int64_t)blockIdx.x * kFlatThreads + tid;
+    const int64_t stride = diag ? kFlatThreads : G * kFlatThreads;
+    auto get = [&](int64_t e) -> T { return diag ? *L.at(e, e) : arf[e]; };
+    T v = T(0);
+    for (int64_t e = start; e < total; e += stride) v = nanmax(v, (T)fabs(get(e)));
+    red[tid] = v;
+    __syncthreads();
+    for (int h = kFlatThreads / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = nanmax(red[tid], red[tid + h]);
+        __syncthreads();
+    }
+    const T scale = red[0];
+    __syncthreads();
+    const int64_t slot = diag ? 2 * G : blockIdx.x, qslot = diag ? 2 * G + 1 : G + blockIdx.x;
+    if (!ssq) {
+        if (tid == 0) w[slot] = scale;
+        return;
+    }
+    T q = T(0);
+    if (scale > T(0))
+        for (int64_t e = start; e < total; e += stride) {
+            const T x = get(e) / scale;
+            q += x * x;
+        }
+    red[tid] = q;
+    __syncthreads();
+    for (int h = kFlatThreads / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] += red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        w[slot] = scale;
+        w[qslot] = red[0];
+    }
+}
+
+// Combine the flat partials: max, or sqrt(2 S_all - S_diag) from the scaled
+// sums (fixed order, one CTA).
+template <typename T>
+__global__ void __launch_bounds__(1024) flat_final_kernel(const T *w, int64_t G, int ssq, T *out)
+{
+    __shared__ T red[1024];
+    const int tid = threadIdx.x;
+    T v = T(0);
+    for (int64_t b = tid; b < G; b += blockDim.x) v = nanmax(v, w[b]);
+    red[tid] = v;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = nanmax(red[tid], red[tid + h]);
+        __syncthreads();
+    }
+    const T mx = red[0];
+    __syncthreads();
+    if (!ssq) {
+        if (tid == 0) *out = mx;
+        return;
+    }
+    T q = T(0);
+    if (mx > T(0))
+        for (int64_t b = tid; b < G; b += blockDim.x) {
+            const T r = w[b] / mx;
+            q += r * r * w[G + b];
+        }
+    red[tid] = q;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (tid < h) red[tid] += red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        T d = T(0);
+        if (mx > T(0)) {
+            const T r = w[2 * G] / mx;
+            d = r * r * w[2 * G + 1];
+        }
+        const T s = T(2) * red[0] - d;
+        *out = mx * sqrt(s > T(0) ? s : T(0));
+    }
+}
+
 // Unit diagonal for TFTRI: save = true copies the diagonal of L to work[0, n)
 // and sets it to 1; save = false puts the saved values back.
 template <typename T>
@@ -169,6 +266,22 @@ cudaError_t sym_norm(cudaStream_t st, const Layout &L, const T *arf, int which, 
 {
     if (L.n <= 0) return cudaMemsetAsync(out, 0, sizeof(T), st);
     T *a = const_cast<T *>(arf);   // read only
+    const int64_t nt = L.n * (L.n + 1) / 2;
+    if (which != 1 && L.n >= 8) {   // max / Frobenius: flat coalesced pass (work: 2G + 2 <= 2n)
+        const int64_t span = (int64_t)kFlatThreads * kFlatPerThread;
+        int64_t G = (nt + span - 1) / span;
+        const int64_t gmax = L.n - 1;   // 2G + 2 <= 2n
+        G = G < gmax ? G : gmax;
+        const int ssq = which == 2 ? 1 : 0;
+        flat_norm_kernel<T><<<(unsigned)(G + ssq), kFlatThreads, 0, st>>>(a, nt, lower_rfp(L, a),
+                                                                          L.n, ssq, work, G);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        flat_final_kernel<T><<<1, 1024, 0, st>>>(work, G, ssq, out);
+        note_launch();
+        return cudaGetLastError();
+    }
     row_norm_kernel<T><<<(unsigned)((L.n + 7) / 8), 256, 0, st>>>(lower_rfp(L, a), L.n, which, work);
     note_launch();
     cudaError_t e = cudaGetLastError();

@@ -53,6 +53,8 @@ __device__ __forceinline__ void load_vec(T *dst, const T *src, int n)
         if (i < n) dst[i] = src[i];
 }
 
+constexpr int64_t kGemmGroup = 16;   // row tiles per band of the grouped tile order
+
 template <typename T, typename Cfg>
 __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
 {
@@ -64,7 +66,20 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_nt_kernel(GemmArgs<T> g)
     __shared__ __align__(16) T Bs[2][BK][LDB_S];
 
     if (g.abort && *g.abort) return;
-    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+    // Grouped tile order: consecutive CTAs sweep the columns under a band of
+    // kGemmGroup row tiles (column by column), so the CTAs resident at one
+    // time share a few A and B strips and find them in L2.  A bijection of the
+    // grid: every tile is still computed exactly once, by the same arithmetic.
+    int64_t by = blockIdx.y, bx = blockIdx.x;
+    if (gridDim.y > kGemmGroup) {
+        const int64_t gx = gridDim.x, id = (int64_t)blockIdx.y * gx + blockIdx.x;
+        const int64_t first = id / (kGemmGroup * gx) * kGemmGroup;
+        const int64_t rows = gridDim.y - first < kGemmGroup ? gridDim.y - first : kGemmGroup;
+        const int64_t r = id - first * gx;
+        by = first + r % rows;
+        bx = r / rows;
+    }
+    const int64_t m0 = by * BM, n0 = bx * BN;
     if (g.cmode == MASK_LOWER && m0 + BM - 1 < n0) return;   // tile strictly above diagonal
 
     // K range that can hold non-zero products for this tile.

@@ -426,6 +426,45 @@ cudaError_t sym_norm(cudaStream_t, const Layout &Ly, const T *arf, int which, T 
     const int64_t n = Ly.n;
     if (n <= 0) { *out = T(0); return cudaSuccess; }
     EmuLower<T> Lw = emu_lower(Ly, const_cast<T *>(arf));
+    if (which != 1 && n >= 8) {   // flat pass: CTA b strides over the RFP array, CTA G the diagonal
+        const int64_t nt = n * (n + 1) / 2, span = 256 * 8;
+        const int64_t G = std::min((nt + span - 1) / span, n - 1);
+        const int ssq = which == 2;
+        {
+            Launch L;
+            for (int64_t b = 0; b < G + ssq; ++b) {
+                L.cta = (int)b;
+                const bool diag = b == G;
+                const int64_t total = diag ? n : nt;
+                std::vector<T> vals;
+                for (int64_t t = 0; t < 256; ++t)
+                    for (int64_t e = diag ? t : b * 256 + t; e < total; e += diag ? 256 : G * 256)
+                        vals.push_back(diag ? L.rd(Lw.at(e, e)) : L.rd(arf + e));
+                T mx = T(0), q = T(0);
+                for (T x : vals) mx = std::max(mx, (T)std::fabs(x));
+                if (ssq && mx > T(0))
+                    for (T x : vals) q += (x / mx) * (x / mx);
+                L.wr(w + (diag ? 2 * G : b), mx);
+                if (ssq) L.wr(w + (diag ? 2 * G + 1 : G + b), q);
+            }
+            cudaError_t e = L.commit();
+            if (e != cudaSuccess) return e;
+        }
+        Launch L;
+        T mx = T(0);
+        for (int64_t b = 0; b < G; ++b) mx = std::max(mx, L.rd(w + b));
+        T res = mx;
+        if (ssq) {
+            T q = T(0), d = T(0);
+            if (mx > T(0)) {
+                for (int64_t b = 0; b < G; ++b) q += (L.rd(w + b) / mx) * (L.rd(w + b) / mx) * L.rd(w + G + b);
+                d = (L.rd(w + 2 * G) / mx) * (L.rd(w + 2 * G) / mx) * L.rd(w + 2 * G + 1);
+            }
+            res = mx * std::sqrt(std::max(T(2) * q - d, T(0)));
+        }
+        L.wr(out, res);
+        return L.commit();
+    }
     {
         Launch L;
         for (int64_t i = 0; i < n; ++i) {
