@@ -112,128 +112,6 @@ cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View
     return cudaSuccess;
 }
 
-// ---- recursive forms (the 2 x 2 split of Section 3 applied recursively) ----------
-//
-// Splitting a triangle at m1 (a multiple of 64 near m/2) turns each routine
-// into two half-size calls plus one GEMM / SYRK whose K is m1: half of all the
-// flops run in the top-level product with long K, instead of n/64 products
-// with K = 64.  That pays where the K = 64 updates are bound by their C
-// traffic (the FP32 factorization of the mixed-precision solve); the FP64
-// routines keep the blocked forms, whose every update fills the GPU (the
-// deep levels of the recursion launch too few CTAs for the FP64 pipe).
-// Base case: one 64-wide diagonal tile.
-
-static int64_t split_point(int64_t m) { return std::max<int64_t>(kNb, (m / 2 + kNb - 1) / kNb * kNb); }
-
-// L X = B in place (B m x nrhs).
-template <typename T>
-cudaError_t trsm_left_lower_notrans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
-                                        const int32_t *abort)
-{
-    if (m <= 0 || nrhs <= 0) return cudaSuccess;
-    if (m <= kNb) return trsm_strip(st, B.t(), V, nrhs, (int)m, 1, T(1), abort);
-    const int64_t m1 = split_point(m), m2 = m - m1;
-    RFP_TRY(trsm_left_lower_notrans_rec(st, B, nrhs, V, m1, abort));
-    RFP_TRY(gemm_nt(st, B.sub(m1, 0), V.sub(m1, 0), B.t(), m2, nrhs, m1, T(-1), T(1), MASK_NONE,
-                    MASK_NONE, MASK_NONE, abort));
-    return trsm_left_lower_notrans_rec(st, B.sub(m1, 0), nrhs, V.sub(m1, m1), m2, abort);
-}
-
-// L^T X = B in place.
-template <typename T>
-cudaError_t trsm_left_lower_trans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
-                                      const int32_t *abort)
-{
-    if (m <= 0 || nrhs <= 0) return cudaSuccess;
-    if (m <= kNb) return trsm_strip(st, B.t(), V, nrhs, (int)m, 0, T(1), abort);
-    const int64_t m1 = split_point(m), m2 = m - m1;
-    RFP_TRY(trsm_left_lower_trans_rec(st, B.sub(m1, 0), nrhs, V.sub(m1, m1), m2, abort));
-    RFP_TRY(gemm_nt(st, B, V.sub(m1, 0).t(), B.sub(m1, 0).t(), m1, nrhs, m2, T(-1), T(1),
-                    MASK_NONE, MASK_NONE, MASK_NONE, abort));
-    return trsm_left_lower_trans_rec(st, B, nrhs, V, m1, abort);
-}
-
-// X L^T = B in place (X rows x m).
-template <typename T>
-cudaError_t trsm_right_lower_trans_rec(cudaStream_t st, View<T> X, int64_t rows, View<T> V, int64_t m,
-                                       const int32_t *abort)
-{
-    if (m <= 0 || rows <= 0) return cudaSuccess;
-    if (m <= kNb) return trsm_strip(st, X, V, rows, (int)m, 1, T(1), abort);
-    const int64_t m1 = split_point(m), m2 = m - m1;
-    RFP_TRY(trsm_right_lower_trans_rec(st, X, rows, V, m1, abort));
-    RFP_TRY(gemm_nt(st, X.sub(0, m1), X, V.sub(m1, 0), rows, m2, m1, T(-1), T(1), MASK_NONE,
-                    MASK_NONE, MASK_NONE, abort));
-    return trsm_right_lower_trans_rec(st, X.sub(0, m1), rows, V.sub(m1, m1), m2, abort);
-}
-
-// Cholesky of the m x m lower triangle V in place; failure index offset by base.
-template <typename T>
-cudaError_t potrf_rec(cudaStream_t st, View<T> V, int64_t m, int32_t *info, int64_t base)
-{
-    if (m <= 0) return cudaSuccess;
-    if (m <= kNb) return potrf_tile(st, V, (int)m, info, base);
-    const int64_t m1 = split_point(m), m2 = m - m1;
-    RFP_TRY(potrf_rec(st, V, m1, info, base));
-    RFP_TRY(trsm_right_lower_trans_rec(st, V.sub(m1, 0), m2, V, m1, info));
-    RFP_TRY(gemm_nt(st, V.sub(m1, m1), V.sub(m1, 0), V.sub(m1, 0), m2, m2, m1, T(-1), T(1),
-                    MASK_LOWER, MASK_NONE, MASK_NONE, info));
-    return potrf_rec(st, V.sub(m1, m1), m2, info, base + m1);
-}
-
-// ---- FP32 solves with inverted diagonal blocks ----------------------------------------
-//
-// For repeated solves with one factor (iterative refinement): the diagonal
-// blocks of width kInvBlock are inverted once (inv_diag_blocks), and each
-// recursive solve ends in leaves that are in-place products with those
-// inverses instead of substitutions.  With few right-hand sides a leaf
-// substitution is one long dependency chain per right-hand side; the
-// product with the inverse has none.
-
-static int64_t split_point_inv(int64_t m)
-{
-    return std::max<int64_t>(kInvBlock, (m / 2 + kInvBlock - 1) / kInvBlock * kInvBlock);
-}
-
-static View<float> inv_block(const float *Inv, int64_t b)
-{
-    return View<float>{const_cast<float *>(Inv) + b * kInvBlock * kInvBlock, 1, kInvBlock};
-}
-
-// L X = B in place (B m x nrhs); block blk0 is the inverse of V's first diagonal block.
-cudaError_t trsm_left_lower_notrans_inv(cudaStream_t st, View<float> B, int64_t nrhs,
-                                        View<float> V, int64_t m, const float *Inv, int64_t blk0,
-                                        const int32_t *abort)
-{
-    if (m <= 0 || nrhs <= 0) return cudaSuccess;
-    if (m <= kInvBlock)   // B <- W B, W = L^{-1} lower
-        return gemm_nt(st, B, inv_block(Inv, blk0), B.t(), m, nrhs, m, 1.f, 0.f, MASK_NONE,
-                       MASK_LOWER, MASK_NONE, abort, true);
-    const int64_t m1 = split_point_inv(m), m2 = m - m1;
-    RFP_TRY(trsm_left_lower_notrans_inv(st, B, nrhs, V, m1, Inv, blk0, abort));
-    RFP_TRY(gemm_nt(st, B.sub(m1, 0), V.sub(m1, 0), B.t(), m2, nrhs, m1, -1.f, 1.f, MASK_NONE,
-                    MASK_NONE, MASK_NONE, abort));
-    return trsm_left_lower_notrans_inv(st, B.sub(m1, 0), nrhs, V.sub(m1, m1), m2, Inv,
-                                       blk0 + m1 / kInvBlock, abort);
-}
-
-// L^T X = B in place.
-cudaError_t trsm_left_lower_trans_inv(cudaStream_t st, View<float> B, int64_t nrhs, View<float> V,
-                                      int64_t m, const float *Inv, int64_t blk0,
-                                      const int32_t *abort)
-{
-    if (m <= 0 || nrhs <= 0) return cudaSuccess;
-    if (m <= kInvBlock)   // B <- W^T B
-        return gemm_nt(st, B, inv_block(Inv, blk0).t(), B.t(), m, nrhs, m, 1.f, 0.f, MASK_NONE,
-                       MASK_UPPER, MASK_NONE, abort, true);
-    const int64_t m1 = split_point_inv(m), m2 = m - m1;
-    RFP_TRY(trsm_left_lower_trans_inv(st, B.sub(m1, 0), nrhs, V.sub(m1, m1), m2, Inv,
-                                      blk0 + m1 / kInvBlock, abort));
-    RFP_TRY(gemm_nt(st, B, V.sub(m1, 0).t(), B.sub(m1, 0).t(), m1, nrhs, m2, -1.f, 1.f,
-                    MASK_NONE, MASK_NONE, MASK_NONE, abort));
-    return trsm_left_lower_trans_inv(st, B, nrhs, V, m1, Inv, blk0, abort);
-}
-
 // In-place W = L^{-1} on an m x m lower triangle V.  Right-looking over the
 // block columns p: with X = C_{p-1}^{-1} ... C_1^{-1} held where L was
 // consumed, step p applies C_p^{-1} (block column p of L):
@@ -459,17 +337,6 @@ RFP_SURFACE_ORCH_INST(float)
 RFP_SURFACE_ORCH_INST(double)
 #undef RFP_SURFACE_ORCH_INST
 
-#define RFP_REC_INST(T)                                                                          \
-    template cudaError_t potrf_rec<T>(cudaStream_t, View<T>, int64_t, int32_t *, int64_t);         \
-    template cudaError_t trsm_right_lower_trans_rec<T>(cudaStream_t, View<T>, int64_t, View<T>,     \
-                                                       int64_t, const int32_t *);                  \
-    template cudaError_t trsm_left_lower_notrans_rec<T>(cudaStream_t, View<T>, int64_t, View<T>,    \
-                                                        int64_t, const int32_t *);                 \
-    template cudaError_t trsm_left_lower_trans_rec<T>(cudaStream_t, View<T>, int64_t, View<T>,      \
-                                                      int64_t, const int32_t *);
-RFP_REC_INST(float)
-RFP_REC_INST(double)
-#undef RFP_REC_INST
 
 #define RFP_BLOCKED_INST(T)                                                                      \
     template cudaError_t potrf_blocked<T>(cudaStream_t, View<T>, int64_t, int32_t *, int64_t);     \

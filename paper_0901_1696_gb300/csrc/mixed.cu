@@ -4,8 +4,8 @@
 // precision of its Level-3 steps).
 //
 //   1. W = fl32(A) (lower triangle of the logical matrix, FP32, full storage)
-//   2. W = L L^T in FP32 storage: the blocked Cholesky of Section 3 on W with
-//      the SYRK / GEMM updates in
+//   2. W = L L^T in FP32 storage: the blocked Cholesky of Section 3 on W by
+//      512-wide panels (factor_panels) with the SYRK updates in
 //        RFP_PREC_FP32: FP32 FMA (SIMT), the s-precision kernels,
 //        RFP_PREC_TF32 / RFP_PREC_BF16: tcgen05 tensor cores (rfp_ssyrk_tc's
 //        kernel) on 512-wide panels converted to TF32 / BF16, FP32 accumulate;
@@ -89,29 +89,55 @@ bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, Mi
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-// Blocked right-looking Cholesky of the FP32 working matrix with the trailing
-// update of each 512-wide panel on the tensor cores.
-static cudaError_t factor_tc(cudaStream_t st, View<float> W, int64_t n, int prec,
-                             const MixedWork &w, int32_t *info)
+// Blocked right-looking Cholesky of the FP32 working matrix by 512-wide
+// panels (Section 3's algorithm on W).  Per panel:
+//   1. Cholesky of the diagonal block (blocked by 64-wide tiles);
+//   2. inverses of its 128-wide diagonal blocks, kept in w.Inv (they serve
+//      the panel solve here and the refinement's block solves later);
+//   3. the panel solve L21 = A21 L11^{-T} by 128-column blocks: subtract the
+//      finished columns (GEMM), then multiply by the block's inverse (an
+//      in-place GEMM): every step is one wide launch;
+//   4. the trailing update A22 -= L21 L21^T: FP32 FMA for RFP_PREC_FP32,
+//      else on the tensor cores from the converted or split panel.
+static cudaError_t factor_panels(cudaStream_t st, View<float> W, int64_t n, int prec,
+                                 const MixedWork &w, int32_t *info)
 {
     for (int64_t j0 = 0; j0 < n; j0 += kMixedPanel) {
         const int64_t j1 = std::min(j0 + kMixedPanel, n), nb = j1 - j0;
-        RFP_TRY(potrf_rec<float>(st, W.sub(j0, j0), nb, info, j0));
+        View<float> L11 = W.sub(j0, j0);
+        float *inv0 = w.Inv + (j0 / kInvBlock) * kInvBlock * kInvBlock;
+        RFP_TRY(potrf_blocked<float>(st, L11, nb, info, j0));
+        RFP_TRY(inv_diag_blocks(st, L11, nb, inv0, info));
         if (j1 >= n) break;
         const int64_t m = n - j1;
-        RFP_TRY(trsm_right_lower_trans_rec<float>(st, W.sub(j1, j0), m, W.sub(j0, j0), nb, info));
+        View<float> X = W.sub(j1, j0);
+        for (int64_t c0 = 0; c0 < nb; c0 += kInvBlock) {
+            const int64_t cw = std::min(kInvBlock, nb - c0);
+            if (c0 > 0)   // X_c -= X(:, 0:c0) L11(c0:c0+cw, 0:c0)^T
+                RFP_TRY(gemm_nt(st, X.sub(0, c0), X, L11.sub(c0, 0), m, cw, c0, -1.0f, 1.0f,
+                                MASK_NONE, MASK_NONE, MASK_NONE, info));
+            // X_c <- X_c W_c^T with W_c = L11(c0.., c0..)^{-1} (lower): in place
+            View<float> Wc{inv0 + (c0 / kInvBlock) * kInvBlock * kInvBlock, 1, kInvBlock};
+            RFP_TRY(gemm_nt(st, X.sub(0, c0), X.sub(0, c0), Wc, m, cw, cw, 1.0f, 0.0f, MASK_NONE,
+                            MASK_NONE, MASK_LOWER, info, true));
+        }
+        if (prec == RFP_PREC_FP32) {
+            RFP_TRY(gemm_nt(st, W.sub(j1, j1), X, X, m, m, nb, -1.0f, 1.0f, MASK_LOWER, MASK_NONE,
+                            MASK_NONE, info));
+            continue;
+        }
         // panel -> K-contiguous low-precision copy P (row r, column k at P[r*pitch + k])
         if (prec == RFP_PREC_BF16) {
             View<__nv_bfloat16> P{static_cast<__nv_bfloat16 *>(w.P), kMixedPanel, 1};
-            RFP_TRY((convert<float, __nv_bfloat16>(st, W.sub(j1, j0), P, m, nb, false, info)));
+            RFP_TRY((convert<float, __nv_bfloat16>(st, X, P, m, nb, false, info)));
         } else if (prec == RFP_PREC_TF32) {
             View<float> P{static_cast<float *>(w.P), kMixedPanel, 1};
-            RFP_TRY((convert<float, float>(st, W.sub(j1, j0), P, m, nb, false, info)));
+            RFP_TRY((convert<float, float>(st, X, P, m, nb, false, info)));
         } else if (prec == RFP_PREC_TF32X3) {
-            RFP_TRY(split_tf32(st, W.sub(j1, j0), static_cast<float *>(w.P), m, nb, kMixedPanel, info));
+            RFP_TRY(split_tf32(st, X, static_cast<float *>(w.P), m, nb, kMixedPanel, info));
         } else {
             __nv_bfloat16 *QA = static_cast<__nv_bfloat16 *>(w.P), *QB = QA + (size_t)m * 6 * kMixedPanel;
-            RFP_TRY(split_bf16x3(st, W.sub(j1, j0), QA, QB, m, nb, kMixedPanel, info));
+            RFP_TRY(split_bf16x3(st, X, QA, QB, m, nb, kMixedPanel, info));
         }
         if (prec == RFP_PREC_BF16X6) {
             const __nv_bfloat16 *QA = static_cast<const __nv_bfloat16 *>(w.P),
@@ -189,10 +215,8 @@ cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf_
     stage_mark(st, "mixed.convert");
     // 2. factor
     int32_t *info = &status->info;
-    if (prec == RFP_PREC_FP32) RFP_TRY(potrf_rec<float>(st, W, n, info, 0));
-    else RFP_TRY(factor_tc(st, W, n, prec, w, info));
+    RFP_TRY(factor_panels(st, W, n, prec, w, info));
     RFP_TRY(stop_on_failure(st, status, w.tc_err, w.stop));
-    RFP_TRY(inv_diag_blocks(st, W, n, w.Inv, w.stop));
     stage_mark(st, "mixed.factor");
     // 3. refinement (step marks: "mixed.solve", "mixed.residual" per iteration)
     RFP_TRY(fill(st, X, n, nrhs, 0.0));

@@ -194,37 +194,15 @@ template <typename T>   // L^T X = B
 cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V, int64_t m,
                                   const int32_t *abort, bool unit = false);
 
-// Recursive forms (split at a multiple of 64 near m/2, one long-K product per
-// level); same contracts as the blocked forms above.
-template <typename T>
-cudaError_t potrf_rec(cudaStream_t st, View<T> V, int64_t m, int32_t *info, int64_t base);
-template <typename T>
-cudaError_t trsm_right_lower_trans_rec(cudaStream_t st, View<T> X, int64_t rows, View<T> V,
-                                       int64_t m, const int32_t *abort);
-template <typename T>
-cudaError_t trsm_left_lower_notrans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
-                                        int64_t m, const int32_t *abort);
-template <typename T>
-cudaError_t trsm_left_lower_trans_rec(cudaStream_t st, View<T> B, int64_t nrhs, View<T> V,
-                                      int64_t m, const int32_t *abort);
-
-// FP32 solves that reuse inverted diagonal blocks, for many solves with one
-// factor.  inv_diag_blocks writes Inv[b] = (diagonal block b of width
-// kInvBlock of the m x m lower triangle V)^{-1} for b = 0 .. ceil(m /
-// kInvBlock) - 1, each kInvBlock x kInvBlock column-major with zeros above
-// the diagonal and outside the block's order (one launch, one CTA per block).
-// The solves take the block index of their first row.  kInvBlock is the
-// height of the large FP32 GEMM tile, so that a leaf product with a block
-// inverse runs in place in one row of CTAs.
+// Inverses of the diagonal blocks of width kInvBlock of the m x m FP32 lower
+// triangle V: Inv[b] = (block b)^{-1} for b = 0 .. ceil(m / kInvBlock) - 1,
+// each kInvBlock x kInvBlock column-major with zeros above the diagonal and
+// outside the block's order (one launch, one CTA per block).  kInvBlock is the
+// height of the large FP32 GEMM tile, so a product with a block inverse runs
+// in place in one row of CTAs.
 constexpr int64_t kInvBlock = 128;
 cudaError_t inv_diag_blocks(cudaStream_t st, View<float> V, int64_t m, float *Inv,
                             const int32_t *abort);
-cudaError_t trsm_left_lower_notrans_inv(cudaStream_t st, View<float> B, int64_t nrhs,
-                                        View<float> V, int64_t m, const float *Inv, int64_t blk0,
-                                        const int32_t *abort);
-cudaError_t trsm_left_lower_trans_inv(cudaStream_t st, View<float> B, int64_t nrhs, View<float> V,
-                                      int64_t m, const float *Inv, int64_t blk0,
-                                      const int32_t *abort);
 
 // One-launch FP32 block triangular solve (trsm_wavefront.cu): L X = B
 // (trans = false) or L^T X = B (trans = true) in place on X (n x nrhs,

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kFlatThreads) flat_norm_kernel(const T *arf, i
     const int64_t stride = diag ? kFlatThreads : G * kFlatThreads;
     auto get = [&](int64_t e) -> T { return diag ? *L.at(e, e) : arf[e]; };
     T v = T(0);
+#pragma unroll 4
     for (int64_t e = start; e < total; e += stride) v = nanmax(v, (T)fabs(get(e)));
     red[tid] = v;
     __syncthreads();
@@ -171,11 +172,13 @@ __global__ void __launch_bounds__(kFlatThreads) flat_norm_kernel(const T *arf, i
         return;
     }
     T q = T(0);
-    if (scale > T(0))
+    if (scale > T(0)) {
+#pragma unroll 4
         for (int64_t e = start; e < total; e += stride) {
             const T x = get(e) / scale;
             q += x * x;
         }
+    }
     red[tid] = q;
     __syncthreads();
     for (int h = kFlatThreads / 2; h > 0; h >>= 1) {
