@@ -12,6 +12,7 @@
 // shared memory, which keeps one DFMA in flight per thread per cycle of
 // shared-memory traffic; memory traffic is far below the HBM roofline.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <climits>
 
@@ -264,13 +265,17 @@ cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M,
     return cudaGetLastError();
 }
 
+// Per-device caches of launch properties.  Several host threads may fill one
+// at the same time (the serving loop's scheduler and a caller's own thread):
+// they compute the same values; the small-tile figure is published before the
+// large-tile one, whose release store marks the entry complete.
 void gemm_occupancy(int elem_size, int *occ_big, int *occ_small)
 {
-    static int cache[64][2][2] = {};
+    static std::atomic<int> cache[64][2][2] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
     const int e = elem_size == 8 ? 0 : 1;
-    if (!cache[dev][e][0]) {
+    if (!cache[dev][e][0].load(std::memory_order_acquire)) {
         int b = 1, sm = 1;
         if (elem_size == 8) {
             using Cb = GemmBig<double>::C;
@@ -283,25 +288,25 @@ void gemm_occupancy(int elem_size, int *occ_big, int *occ_small)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gemm_nt_kernel<float, Cb>, Cb::NT, 0);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sm, gemm_nt_kernel<float, Cs>, Cs::NT, 0);
         }
-        cache[dev][e][0] = b > 0 ? b : 1;
-        cache[dev][e][1] = sm > 0 ? sm : 1;
+        cache[dev][e][1].store(sm > 0 ? sm : 1, std::memory_order_relaxed);
+        cache[dev][e][0].store(b > 0 ? b : 1, std::memory_order_release);
     }
-    *occ_big = cache[dev][e][0];
-    *occ_small = cache[dev][e][1];
+    *occ_big = cache[dev][e][0].load(std::memory_order_acquire);
+    *occ_small = cache[dev][e][1].load(std::memory_order_relaxed);
 }
 
 int device_sm_count()
 {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (!cache[dev]) {
-        int sms = 0;
+    int sms = cache[dev].load(std::memory_order_relaxed);
+    if (!sms) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
             return 152;
-        cache[dev] = sms;
+        cache[dev].store(sms, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return sms;
 }
 
 // ---------------------------------------------------------------------------
