@@ -192,6 +192,22 @@ def fp64_peak_tflops(sm_mhz: float | None) -> float:
     return SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
 
 
+def replica_max(dist, device, *ms):
+    """Each time (ms) maximised over the ranks of the process group (the
+    slowest replica bounds the job); the times unchanged without one."""
+    if dist is None:
+        return [float(x) for x in ms]
+    import torch
+    t = torch.tensor([float(x) for x in ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def replica_value(world: int, flops_per_rank: float, max_ms: float) -> float:
+    """Whole-job rate (TFLOP/s): every replica did flops_per_rank within max_ms."""
+    return world * flops_per_rank / (max_ms * 1e-3) / 1e12
+
+
 def run_ours(args, rank: int, world: int):
     import numpy as np
     import torch
@@ -276,11 +292,8 @@ def run_ours(args, rank: int, world: int):
     orders = [step_layout(args.warmup + k, n)[2] for k in range(K)]
     metric_ms = per_row["pftrf"] + per_row["pftrs"]
     metric_flops = sum(pftrf_flops(m) + pftrs_flops(m, nrhs) for m in orders)
-    if dist:
-        t = torch.tensor([metric_ms, total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        metric_ms, total_ms = float(t[0]), float(t[1])
-    value = world * metric_flops / (metric_ms * 1e-3) / 1e12
+    metric_ms, total_ms = replica_max(dist, dev, metric_ms, total_ms)
+    value = replica_value(world, metric_flops, metric_ms)
 
     # steps of the paper's Fig. 4 (PFTRF) and the dominant kernel's launch:
     # step 3 (T2 -= S S^T) is a single gemm_nt_kernel<double> launch
@@ -331,7 +344,11 @@ def run_ours(args, rank: int, world: int):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e_leg(args, lib, A, B0, dev, stream)
+        e2e = e2e_leg(args, lib, A, B0, dev, stream)
+        e2e_ms, = replica_max(dist, dev, e2e["ms_per_step"])
+        e2e["ms_per_step"] = e2e_ms
+        e2e["value"] = replica_value(world, pftrf_flops(n) + pftrs_flops(n, nrhs), e2e_ms)
+        line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
         args.cpu_n = args.cpu_n or 10240
         rate, dt, threads = oracle_sample(args.cpu_n, max(1, nrhs * args.cpu_n // n), args.kappa)
