@@ -158,6 +158,9 @@ private:
         Done *d = static_cast<Done *>(p);
         const double t = now_s(d->srv->t0_);
         {
+            // Notify while holding the lock: once it is released the scheduler
+            // may retire this last job and the server may be destroyed, so the
+            // callback must not touch the server after unlocking.
             std::lock_guard<std::mutex> lk(d->srv->mu_);
             if (d->job) {
                 d->job->t_done = t;
@@ -166,8 +169,8 @@ private:
                 d->batch->t_done = t;
                 d->srv->done_batches_.push_back(d->batch);
             }
+            d->srv->cv_.notify_all();
         }
-        d->srv->cv_.notify_all();
         delete d;
     }
 
