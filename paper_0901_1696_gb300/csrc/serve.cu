@@ -428,8 +428,11 @@ private:
         b->info_off = b->plan_off >= 0 ? alloc((size_t)count * sizeof(int32_t)) : -1;
         if (b->plan_off < 0 || b->info_off < 0) {   // give the jobs back to the queue
             if (b->plan_off >= 0) arena_.release(b->plan_off);
-            for (Job *j : b->jobs) {
+            for (auto it = b->jobs.rbegin(); it != b->jobs.rend(); ++it) {   // keep their order
+                Job *j = *it;
                 unreserve(j);
+                free_slots_.push_back(j->slot);
+                j->slot = -1;
                 pending_.push_front(j);
             }
             return;
