@@ -356,3 +356,51 @@ def test_emulated_surface_routines(emu_lib, transr, uplo, n):
         _ok(emu)
         ref = oracle.lansf(norm, transr, uplo, n, sarf)
         assert abs(val[0] - ref) <= 1e-14 * ref, norm
+
+
+def test_emulated_surface_edge_cases(emu_lib):
+    """Empty sizes return at once without touching memory; alpha = 0 and
+    k = 0 follow LAPACK (B := 0, C := beta C); leading dimensions above the
+    order leave the padding untouched."""
+    emu = emu_lib
+    emu.lib.emu_set_sms(152)
+    z = np.zeros(4)
+    info = np.zeros(1, dtype=np.int32)
+    _register(emu, z, info)
+    for f in (lambda: emu.rfp_dtpttf("N", "L", 0, z, z, 0),
+              lambda: emu.rfp_dtfttp("T", "U", 0, z, z, 0),
+              lambda: emu.rfp_dtfsm("N", "L", "L", "N", "N", 0, 3, 1.0, z, z, 1, 0),
+              lambda: emu.rfp_dtfsm("N", "R", "U", "T", "U", 3, 0, 1.0, z, z, 3, 0),
+              lambda: emu.rfp_dsfrk("N", "L", "N", 0, 5, 1.0, z, 1, 0.0, z, 0)):
+        assert f() == 0
+    emu.rfp_dtftri("N", "L", "N", 0, z, info, None, 0)
+    _ok(emu)
+    assert info[0] == 0
+    # SFRK with k = 0: C := beta C, A not read (null)
+    n = 9
+    rng = np.random.default_rng(1)
+    S = rng.standard_normal((n, n))
+    for t, u in LAYOUTS:
+        C = oracle.pack(t, u, S + S.T)
+        ref = oracle.sfrk(t, u, "N", n, 0, 1.0, np.zeros((n, 0)), -0.5, C)
+        _register(emu, C)
+        emu.rfp_dsfrk(t, u, "N", n, 0, 1.0, None, n, -0.5, C, 0)
+        _ok(emu)
+        np.testing.assert_allclose(C, ref, rtol=0, atol=1e-15)
+    # TFSM with alpha = 0: B := 0 and A is not read (null); ldb padding untouched
+    m, nc, ldb = 7, 3, 10
+    Bw = np.full((ldb, nc), 5.0, order="F")
+    _register(emu, Bw)
+    emu.rfp_dtfsm("T", "L", "U", "N", "N", m, nc, 0.0, None, Bw, ldb, 0)
+    _ok(emu)
+    assert np.array_equal(Bw[:m], np.zeros((m, nc))) and np.array_equal(Bw[m:], np.full((ldb - m, nc), 5.0))
+    # SFRK with lda above the order
+    k, lda = 4, n + 3
+    A = np.zeros((lda, k), order="F")
+    A[:n] = rng.standard_normal((n, k))
+    C = oracle.pack("N", "U", np.eye(n))
+    ref = oracle.sfrk("N", "U", "N", n, k, 2.0, A[:n], 1.0, C)
+    _register(emu, A, C)
+    emu.rfp_dsfrk("N", "U", "N", n, k, 2.0, A, lda, 1.0, C, 0)
+    _ok(emu)
+    np.testing.assert_allclose(C, ref, rtol=0, atol=1e-13)
