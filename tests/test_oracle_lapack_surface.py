@@ -205,3 +205,51 @@ def test_planted_mistakes_are_rejected(monkeypatch):
     W, _ = ls.tftri("N", "L", "N", 4, oracle.pack("N", "L", L0))
     assert not np.array_equal(oracle.unpack("N", "L", 4, W)[np.tril(np.ones((4, 4), bool))],
                               _exact_inverse(L0)[np.tril(np.ones((4, 4), bool))])
+
+
+def _rejects(check):
+    """True when the pin `check` fails (an assertion or an error) on the mutant."""
+    try:
+        check()
+    except Exception:
+        return True
+    return False
+
+
+def test_more_planted_mistakes_are_rejected(monkeypatch):
+    rng = np.random.default_rng(21)
+    n, k = 7, 4
+    # SFRK that drops the beta C term
+    A = rng.standard_normal((k, n))
+    C = rng.standard_normal((n, n))
+    arf = oracle.pack("N", "L", C + C.T)
+    ref = lapack.dsfrk(n, k, 1.0, np.asfortranarray(A), 1.0, arf.copy(), transr="N", uplo="L",
+                       trans="T")
+    real_sfrk = ls.sfrk
+    monkeypatch.setattr(ls, "sfrk", lambda transr, uplo, trans, n_, k_, alpha, A_, beta, arf_:
+                        real_sfrk(transr, uplo, trans, n_, k_, alpha, A_, 0.0, arf_))
+    assert _rejects(lambda: np.testing.assert_allclose(
+        ls.sfrk("N", "L", "T", n, k, 1.0, A, 1.0, arf), ref, atol=1e-12))
+    monkeypatch.undo()
+    # TFSM that solves from the wrong side (A^{-1} B where B A^{-1} is asked for)
+    T = np.tril(rng.standard_normal((n, n)), -1) + np.diag(rng.uniform(1, 2, n))
+    tri = oracle.pack("N", "L", T)
+    B = rng.standard_normal((3, n))
+    ref = lapack.dtfsm(1.0, tri, np.asfortranarray(B), transr="N", side="R", uplo="L", trans="N",
+                       diag="N")
+    wrong = lambda: ls.tfsm("N", "L", "L", "N", "N", n, 3, 1.0, tri, B.T).T   # noqa: E731
+    assert _rejects(lambda: np.testing.assert_allclose(wrong(), ref, atol=1e-10))
+    # LANSF one-norm summed over the stored triangle only (off-diagonal half missing)
+    S = rng.standard_normal((n, n))
+    S = S + S.T
+    sarf = oracle.pack("T", "U", S)
+    half = float(np.max(np.sum(np.abs(np.triu(S)), axis=0)))
+    assert half != oracle.lansf("1", "T", "U", n, sarf)
+    assert oracle.lansf("1", "T", "U", n, sarf) == float(np.max(np.sum(np.abs(S), axis=0)))
+    # TFTRI with a unit diagonal that still reads the stored diagonal
+    L0 = np.tril(rng.integers(-2, 3, (5, 5))).astype(float)
+    np.fill_diagonal(L0, 2.0)
+    Wu, _ = oracle.tftri("N", "L", "U", 5, oracle.pack("N", "L", L0))
+    Wn, _ = oracle.tftri("N", "L", "N", 5, oracle.pack("N", "L", L0))
+    low = np.tril(np.ones((5, 5), bool), -1)
+    assert not np.array_equal(oracle.unpack("N", "L", 5, Wu)[low], oracle.unpack("N", "L", 5, Wn)[low])
