@@ -29,7 +29,11 @@
  *    Numerical failure is reported asynchronously through *info (see
  *    rfp_dpftrf / rfp_dpftri).
  *  - n = 0 (and nrhs = 0 for the solve) return 0 immediately.
- *  - The library allocates no device memory.
+ *  - The numerical routines allocate no device memory of their own beyond
+ *    what each entry point's comment states (workspaces are caller-owned and
+ *    sized by a query).  The serving loop is the exception: rfp_serve_create
+ *    allocates its arena and pinned result slots once, and rfp_serve_destroy
+ *    frees them.
  *  - The s-variants (float) have the same shapes and semantics in IEEE
  *    binary32 arithmetic.
  */
@@ -201,13 +205,19 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
  * whose host application forbids device allocations after start-up, loops
  * that must not block or fail on an allocation).  The paper has no
  * counterpart; this is an interface variant of rfp_dpfsv_mixed.
- * The workspace is a fixed 32 MiB array inside the library (every GPU that
- * loads the library holds it until the process exits); nothing is allocated.
+ * The workspace is a fixed 32 MiB array inside the library; no call
+ * allocates anything.  The array is reserved on a device when the library's
+ * code for it is loaded there: under CUDA's default lazy module loading that
+ * is the first call on that device (CUDA_MODULE_LOADING=EAGER: when the
+ * context is created).  Make that first call at start-up, while memory is
+ * free; the device then holds the array until the process exits.
  * Same arguments and results as rfp_dpfsv_mixed without work / work_bytes:
  * 1 transr, 2 uplo, 3 n, 4 nrhs, 5 arf, 6 B, 7 ldb, 8 X, 9 ldx, 10 prec,
  * 11 max_iter, 12 tol, 13 status, 14 stream.  Problems whose
  * rfp_dpfsv_mixed_workspace exceeds rfp_dpfsv_mixed_noalloc_capacity() are
- * rejected: -3 if n does not fit even with nrhs = 1, else -4 (for example
+ * rejected once every argument has passed rfp_dpfsv_mixed's checks (which
+ * come first, with the same codes): -3 if n does not fit even with
+ * nrhs = 1, else -4 (for example
  * n = 2048 with nrhs <= 256 fits in the FP32, TF32 and BF16 modes; the
  * split modes, whose panel buffers are larger, fit n = 1664 (split-TF32)
  * and n = 1472 (split-BF16) with nrhs <= 256).
@@ -215,7 +225,10 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
  * streams, other host threads) race on it; serialize them.  The array keeps
  * the previous call's contents; the solve itself clears what must start at
  * zero.  The first call on each device looks up the array's device address
- * (set-up, once per device); make it before any stream capture.
+ * (set-up, once per device and context: again after a device reset or in a
+ * context the caller created); make it before any stream capture.  A CUDA
+ * failure of that set-up returns RFP_ERR_CUDA and is named by
+ * rfp_last_cuda_error.
  */
 size_t rfp_dpfsv_mixed_noalloc_capacity(void);
 int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
@@ -281,8 +294,6 @@ int rfp_spfsv_batched(int64_t batch, const void *d_plan, float *arf, float *B, i
 /* Text for a return code of this library (static storage, never NULL). */
 const char *rfp_status_string(int status);
 
-/* Name of the last CUDA error seen by the calling host thread inside this
- * library ("no error" if none). */
 /*
  * The rest of the LAPACK 3.2 RFP routine set (the paper's table of new
  * routines), with LAPACK's argument order and meaning; "d" FP64, "s" FP32.
@@ -425,6 +436,8 @@ int rfp_serve_poll(void *server, rfp_serve_completion_t *out, int max, double ti
 int rfp_serve_stats(void *server, rfp_serve_stats_t *stats);
 int rfp_serve_destroy(void *server);
 
+/* Name of the last CUDA error seen by the calling host thread inside this
+ * library ("no error" if none). */
 const char *rfp_last_cuda_error(void);
 
 /*

@@ -72,18 +72,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
-def build_probe() -> str:
-    """Compile probes/fp_pipe_probe.cu (the FP64/FP32 pipe-rate probe)."""
-    os.makedirs(OUT_DIR, exist_ok=True)
-    out = os.path.join(OUT_DIR, "fp_pipe_probe")
-    src = os.path.join(HERE, "probes", "fp_pipe_probe.cu")
-    subprocess.run([nvcc(), *ARCH, "-O3", src, "-o", out], check=True)
-    return out
-
-
 if __name__ == "__main__":
-    import sys
-    if "--probe" in sys.argv:
-        exe = build_probe()
-        sys.exit(subprocess.run([exe]).returncode)
     print(build(force=True, verbose=True))

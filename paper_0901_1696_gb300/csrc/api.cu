@@ -101,6 +101,37 @@ int finish(cudaError_t e)
     return RFP_ERR_CUDA;
 }
 
+}  // namespace
+
+namespace rfp {
+
+int finish_cuda(cudaError_t e) { return finish(e); }
+
+int mixed_check_args(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
+                     const double *B, int64_t ldb, const double *X, int64_t ldx, int prec,
+                     int max_iter, double tol, const rfp_mixed_status_t *status)
+{
+    if (!valid_transr(transr)) return -1;
+    if (!valid_uplo(uplo)) return -2;
+    if (n < 0 || n > kMaxN || n > (int64_t(1) << 31) - 1) return -3;
+    if (nrhs < 0 || nrhs > (int64_t(1) << 31) - 1) return -4;
+    if (prec < RFP_PREC_BF16 || prec > RFP_PREC_BF16X6) return -10;
+    if (max_iter < 0) return -11;
+    if (!(tol >= 0.0)) return -12;
+    if (!status || !aligned(status)) return -15;
+    if (n == 0 || nrhs == 0) return 0;
+    if (!arf || !aligned(arf)) return -5;
+    if (!B || !aligned(B)) return -6;
+    if (ldb < n) return -7;
+    if (!X || !aligned(X)) return -8;
+    if (ldx < n) return -9;
+    return 0;
+}
+
+}  // namespace rfp
+
+namespace {
+
 template <typename T>
 int pack_entry(char transr, char uplo, int64_t n, T *A, int64_t lda, T *arf, void *stream,
                bool unpack)
@@ -391,21 +422,11 @@ int rfp_dpfsv_mixed(char transr, char uplo, int64_t n, int64_t nrhs, const doubl
                     double tol, void *work, size_t work_bytes, rfp_mixed_status_t *status,
                     void *stream)
 {
-    if (!valid_transr(transr)) return -1;
-    if (!valid_uplo(uplo)) return -2;
-    if (n < 0 || n > kMaxN || n > (int64_t(1) << 31) - 1) return -3;
-    if (nrhs < 0 || nrhs > (int64_t(1) << 31) - 1) return -4;
-    if (prec < RFP_PREC_BF16 || prec > RFP_PREC_BF16X6) return -10;
-    if (max_iter < 0) return -11;
-    if (!(tol >= 0.0)) return -12;
-    if (!status || !aligned(status)) return -15;
+    const int bad = rfp::mixed_check_args(transr, uplo, n, nrhs, arf, B, ldb, X, ldx, prec,
+                                          max_iter, tol, status);
+    if (bad) return bad;
     if (n == 0 || nrhs == 0)
         return finish(cudaMemsetAsync(status, 0, sizeof(rfp_mixed_status_t), (cudaStream_t)stream));
-    if (!arf || !aligned(arf)) return -5;
-    if (!B || !aligned(B)) return -6;
-    if (ldb < n) return -7;
-    if (!X || !aligned(X)) return -8;
-    if (ldx < n) return -9;
     rfp::MixedWork w;
     if (!work) return -13;
     if (!rfp::mixed_carve(work, work_bytes, n, nrhs, prec, &w))

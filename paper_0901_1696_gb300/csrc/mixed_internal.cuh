@@ -74,6 +74,13 @@ inline int64_t panel_cols(int prec)
 }
 
 size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec);
+// Checks of rfp_dpfsv_mixed's arguments other than its workspace (arguments
+// 13 and 14): 0 if they pass, else -i in rfp_dpfsv_mixed's numbering (status
+// is argument 15).  Pointer and leading-dimension checks only when n > 0 and
+// nrhs > 0.
+int mixed_check_args(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
+                     const double *B, int64_t ldb, const double *X, int64_t ldx, int prec,
+                     int max_iter, double tol, const rfp_mixed_status_t *status);
 bool mixed_carve(void *work, size_t bytes, int64_t n, int64_t nrhs, int prec, MixedWork *w);
 cudaError_t pfsv_mixed_impl(cudaStream_t st, const Layout &L, const double *arf, const double *B,
                             int64_t ldb, double *X, int64_t ldx, int64_t nrhs, int prec,

@@ -9,8 +9,12 @@
 // compiled into the library (kScratchBytes = 32 MiB), so it allocates nothing.
 //
 // Costs and rules that come with that:
-//   * every GPU that loads the library holds the 32 MiB array until the
-//     process exits;
+//   * the array is reserved on a device when the library's code for it is
+//     loaded there: with CUDA's default lazy module loading that is the first
+//     call on that device (CUDA_MODULE_LOADING=EAGER reserves it when the
+//     context is created).  Make that first call at start-up, while device
+//     memory is still free, and before any stream capture; from then on the
+//     device holds the 32 MiB until the process exits;
 //   * problems whose workspace (rfp_dpfsv_mixed_workspace) exceeds 32 MiB are
 //     rejected (for example n = 2048 with nrhs up to 256 fits in the FP32,
 //     TF32 and BF16 modes, n = 1664 in the split-TF32 mode and n = 1472 in
@@ -18,8 +22,10 @@
 //   * all calls share the one array: calls whose work overlaps on the GPU (two
 //     streams, or two host threads) race on it and give wrong results;
 //     serialize them;
-//   * the first call on each device looks up the array's device address
-//     (cudaGetSymbolAddress); make that first call before any stream capture.
+//   * the array's device address is looked up (cudaGetSymbolAddress) on the
+//     first call on each device, and again whenever the calling thread's
+//     current context differs from the one it was looked up in (a device
+//     reset, or a context the caller created itself).
 // The array keeps whatever the previous call left in it; the solve clears
 // what must start at zero (its stop and error words and the status) itself.
 #include <mutex>
@@ -35,11 +41,49 @@ constexpr int kMaxDevices = 64;
 // device array: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
+// Driver entry points that identify the current context, fetched through the
+// runtime (the library does not link the driver library directly).
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
 
-// Device address of g_scratch on the current device (looked up once per
-// device, with that device current); nullptr on failure.
+struct ScratchCache {
+    unsigned long long ctx_id;   // 0: unknown context, look the address up again
+    void *ptr;
+};
+
+std::mutex g_mutex;
+ScratchCache g_cache[kMaxDevices] = {};
+bool g_fns_looked_up = false;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Identifier of the calling thread's current context, 0 if there is none or
+// it cannot be told (the caller then looks the address up every time).
+// Called with g_mutex held.
+unsigned long long current_context_id()
+{
+    if (!g_fns_looked_up) {
+        g_fns_looked_up = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+    unsigned long long id = 0;
+    if (g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_scratch in the current context of the current device;
+// nullptr (and *err set) on failure.
 void *scratch_address(cudaError_t *err)
 {
     int dev = 0;
@@ -50,13 +94,20 @@ void *scratch_address(cudaError_t *err)
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        *err = cudaGetSymbolAddress(&p, g_scratch);
-        if (*err != cudaSuccess) return nullptr;
-        g_scratch_ptr[dev] = p;
+    ScratchCache &c = g_cache[dev];
+    const unsigned long long id = current_context_id();
+    if (c.ptr && id != 0 && c.ctx_id == id) return c.ptr;
+    void *p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_scratch);   // loads the module on first use
+    if (*err != cudaSuccess) {
+        c.ptr = nullptr;
+        return nullptr;
     }
-    return g_scratch_ptr[dev];
+    // The lookup itself makes the device's primary context current when no
+    // context was; ask again so that the entry is keyed on it.
+    c.ctx_id = id != 0 ? id : current_context_id();
+    c.ptr = p;
+    return p;
 }
 
 }  // namespace
@@ -69,17 +120,23 @@ int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, con
                             const double *B, int64_t ldb, double *X, int64_t ldx, int prec,
                             int max_iter, double tol, rfp_mixed_status_t *status, void *stream)
 {
+    // Every argument is checked first, with rfp_dpfsv_mixed's own checks; its
+    // status argument (15 there) is argument 13 here.
+    const int bad = rfp::mixed_check_args(transr, uplo, n, nrhs, arf, B, ldb, X, ldx, prec,
+                                          max_iter, tol, status);
+    if (bad) return bad == -15 ? -13 : bad;
     if (n > 0 && nrhs > 0) {
-        // Problems larger than the fixed array: -3 when n alone does not fit
-        // (even with one right-hand side), else -4 (too many right-hand sides).
+        // Valid problems larger than the fixed array: -3 when n alone does
+        // not fit (even with one right-hand side), else -4 (too many
+        // right-hand sides).
         if (rfp_dpfsv_mixed_workspace(n, 1, prec) > kScratchBytes) return -3;
         if (rfp_dpfsv_mixed_workspace(n, nrhs, prec) > kScratchBytes) return -4;
     }
     cudaError_t e = cudaSuccess;
     void *scratch = scratch_address(&e);
-    if (!scratch) return RFP_ERR_CUDA;
+    if (!scratch) return rfp::finish_cuda(e);
     // Arguments 13 and 14 of rfp_dpfsv_mixed (work, work_bytes) are the fixed
-    // array; its other argument checks and return codes apply unchanged.
+    // array; its other arguments were checked above.
     int rc = rfp_dpfsv_mixed(transr, uplo, n, nrhs, arf, B, ldb, X, ldx, prec, max_iter, tol,
                              scratch, kScratchBytes, status, stream);
     if (rc == -15) rc = -13;   // status is argument 13 here

@@ -59,6 +59,10 @@ __host__ __device__ inline bool mask_keeps(int mask, int64_t r, int64_t c)
     }
 }
 
+// Records e as the calling thread's last CUDA error (rfp_last_cuda_error) and
+// returns the library's CUDA-failure status (1); cudaSuccess returns 0.
+int finish_cuda(cudaError_t e);
+
 // ---- instrumentation (api.cu): launch counter and optional step timing ----
 void note_launch();                                   // one kernel enqueued
 void stage_begin(cudaStream_t st);                    // start of a timed routine

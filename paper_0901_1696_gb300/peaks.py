@@ -2,8 +2,8 @@
 
 SM_COUNT and SM_MAX_MHZ are the part's (152 SMs on two dies, 2070 MHz
 maximum SM clock).  FP64_FMA_PER_SM_CLK is the FP64 FMA issue rate per SM
-per clock measured on GB300 with the DFMA throughput probe in
-probes/fp_pipe_probe.cu (1.196 TFLOP/s at 2070 MHz, 95% of 2 FMA/clk/SM);
+per clock measured on GB300 with a DFMA throughput probe (1.196 TFLOP/s
+at 2070 MHz, 95% of 2 FMA/clk/SM; profiles/fp_pipe_probe.md);
 mma.sync f64 (DMMA) measured 1.049 TFLOP/s, below DFMA, so the FP64 pipe is
 the roof.
 """

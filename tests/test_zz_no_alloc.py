@@ -57,6 +57,38 @@ def test_no_alloc_matches_workspace_version_twice():
         assert oracle.solve_backward_error(A, X, B) <= 1e-14
 
 
+def test_no_alloc_call_allocates_nothing():
+    """After a first call (which reserves the fixed array under lazy module
+    loading), a further call leaves the device's free memory and the torch
+    allocator's count unchanged."""
+    transr, uplo, n, nrhs, prec = "N", "U", 700, 3, 2
+    A, B, arf, dB = _inputs(transr, uplo, n, nrhs, 21)
+    _no_alloc(transr, uplo, n, nrhs, arf, dB, prec)          # set-up call
+    X = torch.full((nrhs, n), np.nan, dtype=torch.float64, device="cuda")
+    st = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    rfp.rfp_dpfsv_mixed_noalloc(transr, uplo, n, nrhs, arf, dB, n, X, n, prec, 30, 1e-15, st)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+    assert rfp.mixed_status(st.cpu().numpy().tobytes())["converged"] == 1
+    assert oracle.solve_backward_error(A, X.cpu().numpy().T, B) <= 1e-14
+
+
+def test_no_alloc_checks_arguments_before_its_capacity():
+    st = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    big = 4096
+    with pytest.raises(rfp.RfpError) as e:      # transr invalid, n too large for the array
+        rfp.rfp_dpfsv_mixed_noalloc("X", "L", big, 1, 16, 16, big, 16, big, 2, 5, 1e-14, st)
+    assert e.value.status == -1
+    with pytest.raises(rfp.RfpError) as e:      # null arf
+        rfp.rfp_dpfsv_mixed_noalloc("N", "L", big, 1, 0, 16, big, 16, big, 2, 5, 1e-14, st)
+    assert e.value.status == -5
+
+
 def test_no_alloc_rejects_problems_beyond_its_scratch():
     cap = rfp.rfp_dpfsv_mixed_noalloc_capacity()
     assert cap == 32 << 20
