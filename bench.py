@@ -79,6 +79,9 @@ def parse():
                    help="batched mode: re-run the panel-width autotuner even if cached")
     p.add_argument("--no-fp64-ref", action="store_true",
                    help="mixed mode: skip the FP64 PFTRF + PFTRS reference run")
+    p.add_argument("--legs", default="c1,mixed,batched,serve",
+                   help="fp64 mode at N = 1: the other configurations measured after the main "
+                        "timed region and reported under breakdown (empty: none)")
     return p.parse_args()
 
 
@@ -352,14 +355,65 @@ def run_ours(args, rank: int, world: int):
     if rank == 0 and not args.no_cpu_baseline:
         args.cpu_n = args.cpu_n or 10240
         rate, dt, threads = oracle_sample(args.cpu_n, max(1, nrhs * args.cpu_n // n), args.kappa)
+        line["config"]["cpu_baseline_sample"] = (
+            f"oracle timed on a smaller sample of the same recipe: n={args.cpu_n}, nrhs="
+            f"{max(1, nrhs * args.cpu_n // n)} (the oracle's rate is roughly flat in n; n={n} "
+            "would take about a minute of host time)")
         line["cpu_baseline"] = {
             "value": rate, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
             "sample": f"plain C oracle PFTRF+PFTRS at n={args.cpu_n}, nrhs="
                       f"{max(1, nrhs * args.cpu_n // n)}, layout N/L, same recipe ({dt:.1f} s)"}
+    if world == 1 and args.legs:
+        del A, Ainv, arf, X, B0
+        torch.cuda.empty_cache()
+        line["breakdown"].update(other_legs(args, lib, dev, stream))
     if dist:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def other_legs(args, lib, dev, stream):
+    """The other configurations of the metric, each after the main timed
+    region (its own clocks and timing; nothing here enters `value`):
+      c1: n = 1001 latencies of PFTRF / PFTRS / PFTRI;
+      mixed: n = 32768, nrhs = 64, kappa = 1e6, split-BF16 and split-TF32
+             mixed-precision solves against FP64 PFTRF + PFTRS on the same
+             matrix;
+      batched: 4096 uneven matrices (n ~ U{32..512}), FP64 and FP32;
+      serve: the request stream, saturation then Poisson arrivals at 0.7 of
+             the measured capacity (2000 requests, at most 45 s of arrivals).
+    A leg that fails records its error instead of its numbers."""
+    import torch
+    out = {}
+    for leg in [x for x in args.legs.split(",") if x]:
+        t0 = time.time()
+        try:
+            if leg == "c1":
+                out["c1"] = c1_leg(lib, dev, stream)
+            elif leg == "mixed":
+                sampler = ClockSampler(0)
+                sampler.start()
+                fp64, res = mixed_leg(lib, dev, stream, 32768, 64, [1e6], ["bf16x6", "tf32x3"],
+                                      30, True)
+                out["mixed"] = {"workload": "n=32768, nrhs=64, kappa=1e6, A = Q diag(lam) Q^T "
+                                            "(random butterfly Q, lam log-uniform on [1, 1e6])",
+                                "fp64": fp64, "results": res, "clocks": sampler.stop()}
+            elif leg == "batched":
+                legs, arf_len, flops = batched_leg(lib, dev, 4096, ("f64", "f32"), 3, 10)
+                out["batched"] = {"workload": "4096 SPD matrices, n ~ U{32..512}, 8 layouts, "
+                                              "nrhs ~ U{1..8}; one graph-captured launch",
+                                  "flops_per_batch": flops, **legs}
+            elif leg == "serve":
+                out["serve"] = serve_leg(lib, dev, 1000, 2000, 64, [0.7], resident_requests=500,
+                                         load_time_cap_s=45.0)
+            else:
+                out[leg] = {"error": "unknown leg"}
+        except Exception as exc:    # keep the main line; say what failed
+            out[leg] = {"error": f"{type(exc).__name__}: {exc}"}
+        out.setdefault(leg, {})["leg_wall_s"] = time.time() - t0
+        torch.cuda.empty_cache()
+    return out
 
 
 def e2e_leg(args, lib, A, B0, dev, stream):
@@ -398,6 +452,79 @@ def e2e_leg(args, lib, A, B0, dev, stream):
             "d2h_bytes_per_step": n * nrhs * 8, "ms_per_step": ms}
 
 
+def c1_leg(lib, dev, stream, reps: int = 30, oracle_too: bool = True):
+    """The small latency-bound configuration: n = 1001 (odd), TRANSR = 'N',
+    UPLO = 'L', A = B B^T / n + I (B ~ U[-1, 1], seed 0), PFTRF, PFTRS with
+    nrhs = 16, PFTRI.  Each call is timed alone with CUDA events on the
+    launching stream (median of `reps`, after 5 warm-up rounds); the 4 MB
+    RFP array would stay in L2, so a 256 MB buffer is written (untimed)
+    before every timed call.  The same three calls of the plain oracle on
+    the host are timed once beside them."""
+    import numpy as np
+    import torch
+
+    import rfp_inputs as gen
+    n, nrhs = 1001, 16
+    A, rng = gen.spd_bbt(n, seed=0, return_rng=True)
+    Bh = gen.rhs(n, nrhs, rng)
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev)
+    arf0 = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
+    lib.rfp_dpack("N", "L", n, dA, n, arf0, stream)
+    arf = torch.empty_like(arf0)
+    fac = torch.empty_like(arf0)
+    B0 = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev)
+    X = torch.empty_like(B0)
+    info = torch.zeros(2, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = {"pftrf": [], "pftrs": [], "pftri": []}
+
+    def timed(key, fn, record):
+        flush.fill_(1)
+        ev[0].record(stream)
+        fn()
+        ev[1].record(stream)
+        if record:
+            torch.cuda.synchronize(dev)
+            times[key].append(ev[0].elapsed_time(ev[1]) * 1e3)
+
+    for r in range(5 + reps):
+        rec = r >= 5
+        arf.copy_(arf0)
+        timed("pftrf", lambda: lib.rfp_dpftrf("N", "L", n, arf, info[0:1], stream), rec)
+        if r == 0:
+            fac.copy_(arf)
+        X.copy_(B0)
+        timed("pftrs", lambda: lib.rfp_dpftrs("N", "L", n, nrhs, arf, X, n, stream), rec)
+        timed("pftri", lambda: lib.rfp_dpftri("N", "L", n, arf, info[1:2], stream), rec)
+    torch.cuda.synchronize(dev)
+    assert int(info.abs().sum().item()) == 0
+    Xh = X.cpu().numpy().T
+    from paper_0901_1696_gb300.flops import pftrf_flops, pftri_flops, pftrs_flops
+    med = {k: float(np.median(v)) for k, v in times.items()}
+    out = {"workload": "n=1001 N/L, A = B B^T/n + I (seed 0), nrhs=16; L2 flushed before each call",
+           **{f"{k}_us": v for k, v in med.items()},
+           **{f"{k}_us_min": float(np.min(v)) for k, v in times.items()},
+           "pftrf_gflops": pftrf_flops(n) / (med["pftrf"] * 1e-6) / 1e9,
+           "pftrs_gflops": pftrs_flops(n, nrhs) / (med["pftrs"] * 1e-6) / 1e9,
+           "pftri_gflops": pftri_flops(n) / (med["pftri"] * 1e-6) / 1e9,
+           "bwd_err": sampled_backward_error(A, Xh, Bh), "reps": reps}
+    if oracle_too:
+        import oracle
+        packed = oracle.pack("N", "L", A)
+        t0 = time.perf_counter()
+        ofac, oinfo = oracle.pftrf("N", "L", n, packed)
+        t1 = time.perf_counter()
+        oracle.pftrs("N", "L", n, ofac, Bh)
+        t2 = time.perf_counter()
+        oracle.pftri("N", "L", n, ofac)
+        t3 = time.perf_counter()
+        out["oracle_us"] = {"pftrf": (t1 - t0) * 1e6, "pftrs": (t2 - t1) * 1e6,
+                            "pftri": (t3 - t2) * 1e6}
+        out["max_abs_diff_factor_vs_oracle"] = float(np.max(np.abs(fac.cpu().numpy() - ofac)))
+    return out
+
+
 def sampled_backward_error(A, X, B):
     """max_j ||b_j - A x_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) with a
     plain host FP64 residual (numpy) on the given columns."""
@@ -411,21 +538,38 @@ def sampled_backward_error(A, X, B):
 def run_mixed(args):
     """Mixed-precision solve (low-precision factor + FP64 refinement) of an
     n = 32768 FP64 RFPF system with nrhs = 64, for each condition number and
-    precision, against FP64 PFTRF + PFTRS on the same GPU.  Errors: the
-    device's backward error, a host FP64 residual on 4 sampled columns, and
-    the max-norm distance to the FP64 solution."""
+    precision, against FP64 PFTRF + PFTRS on the same GPU (its own line)."""
+    import torch
+
+    from paper_0901_1696_gb300 import binding as rfp
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    n, nrhs = args.mixed_n, args.mixed_nrhs
+    fp64, results = mixed_leg(lib, dev, torch.cuda.current_stream(dev), n, nrhs,
+                              [float(k) for k in args.kappas.split(",")], args.precs.split(","),
+                              args.max_iter, not args.no_fp64_ref)
+    line = {"mode": "mixed", "metric": "mixed-precision RFPF solve: time and backward error "
+                                        "vs FP64 PFTRF+PFTRS",
+            "unit": "ms", "higher_is_better": False, "n": n, "nrhs": nrhs, "dtype": "f64 in/out",
+            "data": "synthetic: A = Q diag(lam) Q^T, Q random butterfly (n power of two) else "
+                    "Haar, lam log-uniform on [1, kappa] with endpoints pinned",
+            "tol": 1e-15, "fp64": fp64, "results": results}
+    print(json.dumps(line), flush=True)
+
+
+def mixed_leg(lib, dev, stream, n, nrhs, kappas, precs_wanted, max_iter, fp64_ref=True):
+    """For each condition number: FP64 PFTRF + PFTRS (unless fp64_ref is
+    False) and the mixed-precision solve in each precision, on the same
+    matrix.  Errors: the device's backward error, a host FP64 residual on 4
+    sampled columns, and the max-norm distance to the FP64 solution.
+    Returns (fp64 rows, mixed rows)."""
     import numpy as np
     import torch
 
     import rfp_inputs as gen
     from paper_0901_1696_gb300 import binding as rfp
     from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    lib = rfp.library()
-    stream = torch.cuda.current_stream(dev)
-    n, nrhs = args.mixed_n, args.mixed_nrhs
     precs = {"fp32": rfp.RFP_PREC_FP32, "tf32": rfp.RFP_PREC_TF32, "bf16": rfp.RFP_PREC_BF16,
              "tf32x3": rfp.RFP_PREC_TF32X3, "bf16x6": rfp.RFP_PREC_BF16X6}
     results, fp64 = [], []
@@ -435,7 +579,7 @@ def run_mixed(args):
     status = torch.zeros(24, dtype=torch.uint8, device=dev)
     sample = [0, nrhs // 3, 2 * nrhs // 3, nrhs - 1]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for kappa in [float(k) for k in args.kappas.split(",")]:
+    for kappa in kappas:
         A = gen.spd_butterfly(n, seed=0, kappa=kappa, device=dev) if n & (n - 1) == 0 else \
             gen.spd_spectrum(n, seed=0, kappa=kappa, device=dev)
         arf = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
@@ -443,10 +587,10 @@ def run_mixed(args):
         Ah = A.cpu().numpy()
         del A
         X64h = None
-        if args.no_fp64_ref:
+        if not fp64_ref:
             fp64.append({"kappa": kappa, "skipped": True})
         # FP64 reference path on a copy
-        fac = arf.clone() if not args.no_fp64_ref else None
+        fac = arf.clone() if fp64_ref else None
         ms64 = None
         if fac is not None:
             X64 = dB.clone()
@@ -463,7 +607,7 @@ def run_mixed(args):
                          "tflops": (pftrf_flops(n) + pftrs_flops(n, nrhs)) / (ms64 * 1e-3) / 1e12,
                          "bwd_sampled": sampled_backward_error(Ah, X64h[:, sample], Bh[:, sample])})
             del fac, X64
-        for name in args.precs.split(","):
+        for name in precs_wanted:
             prec = precs[name]
             wb = lib.rfp_dpfsv_mixed_workspace(n, nrhs, prec)
             work = torch.empty(wb, dtype=torch.uint8, device=dev)
@@ -471,7 +615,7 @@ def run_mixed(args):
                 torch.cuda.synchronize(dev)
                 lib.rfp_stage_timing(True)
                 ev[0].record(stream)
-                lib.rfp_dpfsv_mixed("N", "L", n, nrhs, arf, dB, n, X, n, prec, args.max_iter,
+                lib.rfp_dpfsv_mixed("N", "L", n, nrhs, arf, dB, n, X, n, prec, max_iter,
                                     1e-15, work, wb, status, stream)
                 ev[1].record(stream)
                 torch.cuda.synchronize(dev)
@@ -498,13 +642,7 @@ def run_mixed(args):
             del work
         del arf, Ah
         torch.cuda.empty_cache()
-    line = {"mode": "mixed", "metric": "mixed-precision RFPF solve: time and backward error "
-                                        "vs FP64 PFTRF+PFTRS",
-            "unit": "ms", "higher_is_better": False, "n": n, "nrhs": nrhs, "dtype": "f64 in/out",
-            "data": "synthetic: A = Q diag(lam) Q^T, Q random butterfly (n power of two) else "
-                    "Haar, lam log-uniform on [1, kappa] with endpoints pinned",
-            "tol": 1e-15, "fp64": fp64, "results": results}
-    print(json.dumps(line), flush=True)
+    return fp64, results
 
 
 def run_batched(args):
@@ -512,21 +650,43 @@ def run_batched(args):
     order n ~ U{32..512}, each in one of the 8 layouts (uniform), nrhs ~
     U{1..8}, A_k = B B^T / n + I (rfp_inputs.spd_bbt, seed 1000 + k), in
     FP64 and in FP32, one graph-captured launch per batch.  The panel width
-    per n-bucket comes from the autotuner's cache (tuned on first use)."""
+    per n-bucket comes from the autotuner's cache, else from the table
+    shipped for the GPU model, else it is tuned on first use."""
+    import torch
+
+    from paper_0901_1696_gb300 import binding as rfp
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    count = args.batch
+    legs, arf_len, flops = batched_leg(lib, dev, count, ("f64", "f32"), args.warmup, args.steps,
+                                       args.retune)
+    line = {"mode": "batched", "metric": "batched PFTRF+PFTRS TFLOP/s (uneven SPD RFPF batch)",
+            "value": legs["f64"]["tflops"], "unit": "TFLOP/s", "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+            "data": "synthetic: A_k = B B^T / n + I, B ~ U[-1,1] (numpy PCG64, seed 1000 + k)",
+            "config": {"workload": f"{count} SPD matrices, n ~ U{{32..512}}, 8 layouts uniform, "
+                                   "nrhs ~ U{1..8}; one graph-captured launch per batch",
+                       "batch": count, "flops_per_batch": flops,
+                       "l2": "inputs restored before every replay (untimed copy of "
+                             f"{arf_len * 8 / 1e9:.2f} GB FP64 > L2)"},
+            **legs}
+    print(json.dumps(line), flush=True)
+
+
+def batched_leg(lib, dev, count, precs, warmup, steps, retune=False):
+    """Batched PFTRF + PFTRS of `count` uneven matrices in each precision of
+    `precs` ("f64", "f32"); returns ({prec: leg}, arf_len, flops)."""
     import numpy as np
     import torch
 
     import rfp_inputs as gen
     from paper_0901_1696_gb300 import batched as bt
-    from paper_0901_1696_gb300 import binding as rfp
     from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
     from paper_0901_1696_gb300.peaks import FP32_FMA_PER_SM_CLK, SM_COUNT, SM_MAX_MHZ
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    lib = rfp.library()
     gpu = torch.cuda.get_device_properties(dev).name
-    count = args.batch
     rng = np.random.default_rng(0)
     ns = [int(x) for x in rng.integers(32, 513, count)]
     lay = rng.integers(0, 8, count)
@@ -541,6 +701,8 @@ def run_batched(args):
     kept = {}
     legs = {}
     for prec, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        if prec not in precs:
+            continue
         arf = torch.empty(max(arf_len, 1), dtype=dtype, device=dev)
         B = torch.empty(max(b_len, 1), dtype=dtype, device=dev)
         pack = lib.rfp_dpack if dtype == torch.float64 else lib.rfp_spack
@@ -559,17 +721,17 @@ def run_batched(args):
         t_gen = time.time() - t_gen
         cache = bt.TuningCache()
         tuned = False
-        if args.retune or not cache.get(gpu, prec):
+        if retune or not cache.get(gpu, prec):
             bt.autotune(prec, cache=cache)
             tuned = True
         cache.fill_nb(entries, gpu, prec)
         # warm-up replays, then timed replays; inputs restored before each (not timed)
         sampler = ClockSampler(0)
         t0 = time.time()
-        bt.time_batch(torch, lib, entries, arf, B, dtype, reps=max(args.warmup, 1))
+        bt.time_batch(torch, lib, entries, arf, B, dtype, reps=max(warmup, 1))
         sampler.start()
         ms, out_a, out_b, info = bt.time_batch(torch, lib, entries, arf, B, dtype,
-                                               reps=max(args.steps, 1))
+                                               reps=max(steps, 1))
         clocks = sampler.stop()
         wall = time.time() - t0
         info_h = info.cpu().numpy()
@@ -594,43 +756,58 @@ def run_batched(args):
                          "frac": tflops / peak, "traffic": None, "kernel": "batched_kernel",
                          "peak_source": bound},
             "info_nonzero": int(np.count_nonzero(info_h)), "bwd_sampled_max": bwd,
-            "nb_table": cache.get(gpu, prec), "autotuned_now": tuned,
-            "clocks": clocks, "gen_s": t_gen, "wall_s": wall}
+            "nb_table": cache.get(gpu, prec), "nb_table_source": cache.source(gpu, prec),
+            "autotuned_now": tuned, "clocks": clocks, "gen_s": t_gen, "wall_s": wall}
         del arf, B, out_a, out_b
         torch.cuda.empty_cache()
-    line = {"mode": "batched", "metric": "batched PFTRF+PFTRS TFLOP/s (uneven SPD RFPF batch)",
-            "value": legs["f64"]["tflops"], "unit": "TFLOP/s", "higher_is_better": True,
-            "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
-            "data": "synthetic: A_k = B B^T / n + I, B ~ U[-1,1] (numpy PCG64, seed 1000 + k)",
-            "config": {"workload": f"{count} SPD matrices, n ~ U{{32..512}}, 8 layouts uniform, "
-                                   "nrhs ~ U{1..8}; one graph-captured launch per batch",
-                       "batch": count, "flops_per_batch": flops,
-                       "l2": "inputs restored before every replay (untimed copy of "
-                             f"{arf_len * 8 / 1e9:.2f} GB FP64 > L2)"},
-            "f64": legs["f64"], "f32": legs["f32"]}
-    print(json.dumps(line), flush=True)
+    return legs, arf_len, flops
 
 
 def run_serve(args):
-    """Serving loop (rfp_serve_*): a stream of factor+solve requests, n
+    """Serving loop (rfp_serve_*) on its own line: closed-loop saturation to
+    measure capacity, Poisson arrivals at the given fractions of it, then
+    solve requests on resident factors (serve_leg)."""
+    import torch
+
+    from paper_0901_1696_gb300 import binding as rfp
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = rfp.library()
+    R, P = args.serve_requests, args.serve_pool
+    loads = [float(x) for x in args.serve_loads.split(",") if x]
+    out = serve_leg(lib, dev, R, R, P, loads, resident_requests=min(R, 1000))
+    line = {"mode": "serve", "metric": "served solves/s, p50/p99 at <=1e-12 bwd err",
+            "value": out["runs"]["saturation"]["solves_per_s"], "unit": "solves/s (right-hand sides)",
+            "higher_is_better": True, "dtype": "f64 in/out (FP64 or split-TF32 + FP64 refinement)",
+            "data": "synthetic: A = Q diag(lam) Q^T, Q = 8 Householder reflectors, lam log-uniform "
+                    "on [1, kappa]",
+            "config": {"workload": out["workload"], "requests": R, "pool": P},
+            **{k: v for k, v in out.items() if k != "workload"}}
+    print(json.dumps(line), flush=True)
+
+
+def serve_leg(lib, dev, sat_requests, load_requests, pool_size, loads, resident_requests=0,
+              load_time_cap_s=None):
+    """A stream of factor+solve requests through the serving loop: n
     log-uniform in [64, 8192], kappa log-uniform in [1e1, 1e6], nrhs ~
     U{1..32}, layouts uniform, FP64 / mixed-precision modes uniform, host
-    inputs in pinned memory.  Runs: closed-loop saturation (all requests at
-    t = 0) to measure capacity, then Poisson arrivals at the given fractions
-    of it, then solve requests on resident factors.  Latency = done - submit
-    on the server's host clock."""
+    inputs in pinned memory, drawn from a pool of `pool_size` matrices.
+    Runs: closed-loop saturation (`sat_requests` submitted at t = 0) to
+    measure capacity, then Poisson arrivals at each fraction in `loads` of it
+    (`load_requests` each, fewer if the arrivals would last longer than
+    `load_time_cap_s`), then `resident_requests` solves on resident factors.
+    Latency = done - submit on the server's host clock.  Backward errors of
+    48 sampled requests of the saturation run are checked by a plain FP64
+    residual on the device against the unpacked matrix."""
     import numpy as np
     import torch
 
     import rfp_inputs as gen
     from paper_0901_1696_gb300 import batched as bt
-    from paper_0901_1696_gb300 import binding as rfp
     from paper_0901_1696_gb300 import serve as sv
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    lib = rfp.library()
-    R, P = args.serve_requests, args.serve_pool
+    R = max(sat_requests, load_requests, resident_requests)
+    P = pool_size
     rng = np.random.default_rng(0)
     layouts = [("N", "L"), ("N", "U"), ("T", "L"), ("T", "U")]
     pool = []
@@ -657,13 +834,14 @@ def run_serve(args):
     nb = [[(table or {}).get(t, [16] * 8)[b] for b in range(8)] for t in ("N", "T")]
     arena = 150 << 30
 
-    def one_run(arrivals, key_base):
-        """arrivals: submit times (s) relative to the start, or None (all at once)."""
+    def one_run(count, arrivals, key_base):
+        """The first `count` requests; arrivals: submit times (s) relative to
+        the start, or None (all at once)."""
         Xh.zero_()
         with sv.Server(arena_bytes=arena, streams=8, batch_max=1024, small_n=512,
                        max_iter=30, tol=1e-15, batch_nb=nb) as s:
             t0 = time.perf_counter()
-            for k in range(R):
+            for k in range(count):
                 if arrivals is not None:
                     dt = arrivals[k] - (time.perf_counter() - t0)
                     if dt > 0:
@@ -674,32 +852,34 @@ def run_serve(args):
                          arf=pm["arf_h"].data_ptr(),
                          B=Bh.data_ptr() + 8 * int(offs[k]), X=Xh.data_ptr() + 8 * int(offs[k]),
                          key=key_base + k)
-            done = s.wait(R, timeout=1800)
+            done = s.wait(count, timeout=1800)
             st = s.stats()
         done.sort(key=lambda c: c["id"])
         lat = np.array([c["t_done"] - c["t_submit"] for c in done]) * 1e3
         span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
         ok = [c["status"] == 0 for c in done]
-        fp64 = modes == 0
-        return {"requests_per_s": R / span, "solves_per_s": float(nrhs.sum()) / span,
+        fp64 = modes[:count] == 0
+        return {"requests": count, "requests_per_s": count / span,
+                "solves_per_s": float(nrhs[:count].sum()) / span,
                 "span_s": span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                 "p50_fp64_ms": float(np.percentile(lat[fp64], 50)),
+                "p99_fp64_ms": float(np.percentile(lat[fp64], 99)),
                 "p50_mixed_ms": float(np.percentile(lat[~fp64], 50)),
-                "ok": int(sum(ok)), "failed": int(R - sum(ok)),
+                "p99_mixed_ms": float(np.percentile(lat[~fp64], 99)),
+                "ok": int(sum(ok)), "failed": int(count - sum(ok)),
                 "statuses": sorted(set(int(c["status"]) for c in done)),
-                "batched_fraction": st["batched_requests"] / R,
+                "batched_fraction": st["batched_requests"] / count,
                 "mean_batch": st["batched_requests"] / max(st["batches"], 1),
                 "evictions": st["evictions"], "cache_gb": st["cache_bytes"] / 1e9}, done
 
     runs = {}
     sampler = ClockSampler(0)
     sampler.start()
-    sat, done = one_run(None, 0)
-    clocks = sampler.stop()
+    sat, done = one_run(sat_requests, None, 0)
     runs["saturation"] = sat
-    # sampled backward errors of the saturation run: host-side checker, FP64 residual on the GPU
-    check = sorted(set(int(x) for x in np.linspace(0, R - 1, 48)))
+    # sampled backward errors of the saturation run: FP64 residual on the GPU
+    check = sorted(set(int(x) for x in np.linspace(0, sat_requests - 1, 48)))
     bwd = []
     for k in check:
         pm = pool[int(which[k])]
@@ -714,49 +894,51 @@ def run_serve(args):
         bwd.append(dict(k=k, n=n, mode=int(modes[k]), bwd=float((res / den).max())))
         del Af
     cap = sat["requests_per_s"]
-    for f in [float(x) for x in args.serve_loads.split(",") if x]:
-        gaps = np.random.default_rng(7).exponential(1.0 / (f * cap), R)
-        runs[f"load_{f:g}"] = one_run(np.cumsum(gaps) - gaps[0], 10 ** 7 * (1 + len(runs)))[0]
-    # solve requests on resident factors (cache hits): FP64 factors of the pool
-    with sv.Server(arena_bytes=arena, streams=8, batch_max=1024, small_n=512, batch_nb=nb) as s:
-        prime_x = torch.zeros(sum(pm["n"] for pm in pool), dtype=torch.float64).pin_memory()
-        po = np.concatenate([[0], np.cumsum([pm["n"] for pm in pool])])
-        for i, pm in enumerate(pool):
-            s.submit(i, sv.OP_FACTOR_SOLVE, sv.MODE_FP64, pm["t"], pm["u"], pm["n"], 1,
-                     arf=pm["arf_h"].data_ptr(), B=Bh.data_ptr(),
-                     X=prime_x.data_ptr() + 8 * int(po[i]), key=i)
-        s.wait(P)
-        m = min(R, 1000)
-        for k in range(m):
-            i = int(which[k])
-            pm = pool[i]
-            s.submit(P + k, sv.OP_SOLVE, sv.MODE_FP64, pm["t"], pm["u"], pm["n"], int(nrhs[k]),
-                     B=Bh.data_ptr() + 8 * int(offs[k]), X=Xh.data_ptr() + 8 * int(offs[k]), key=i)
-        hits = s.wait(m)
-    hl = np.array([c["t_done"] - c["t_submit"] for c in hits]) * 1e3
-    hspan = max(c["t_done"] for c in hits) - min(c["t_submit"] for c in hits)
-    runs["resident_solves"] = {"requests": m, "submitted": "all at once (latency includes queueing)",
-                               "solves_per_s": float(nrhs[:m].sum()) / hspan,
-                               "requests_per_s": m / hspan,
-                               "cache_hit_fraction": float(np.mean([c["cache_hit"] for c in hits])),
-                               "p50_ms": float(np.percentile(hl, 50)), "p99_ms": float(np.percentile(hl, 99)),
-                               "ok": int(sum(c["status"] == 0 for c in hits))}
+    for f in loads:
+        count = load_requests
+        if load_time_cap_s:
+            count = max(1, min(count, int(f * cap * load_time_cap_s)))
+        gaps = np.random.default_rng(7).exponential(1.0 / (f * cap), count)
+        runs[f"load_{f:g}"] = one_run(count, np.cumsum(gaps) - gaps[0],
+                                      10 ** 7 * (1 + len(runs)))[0]
+        runs[f"load_{f:g}"]["offered_requests_per_s"] = f * cap
+    if resident_requests:
+        # solve requests on resident factors (cache hits): FP64 factors of the pool
+        with sv.Server(arena_bytes=arena, streams=8, batch_max=1024, small_n=512,
+                       batch_nb=nb) as s:
+            prime_x = torch.zeros(sum(pm["n"] for pm in pool), dtype=torch.float64).pin_memory()
+            po = np.concatenate([[0], np.cumsum([pm["n"] for pm in pool])])
+            for i, pm in enumerate(pool):
+                s.submit(i, sv.OP_FACTOR_SOLVE, sv.MODE_FP64, pm["t"], pm["u"], pm["n"], 1,
+                         arf=pm["arf_h"].data_ptr(), B=Bh.data_ptr(),
+                         X=prime_x.data_ptr() + 8 * int(po[i]), key=i)
+            s.wait(P)
+            m = resident_requests
+            for k in range(m):
+                i = int(which[k])
+                pm = pool[i]
+                s.submit(P + k, sv.OP_SOLVE, sv.MODE_FP64, pm["t"], pm["u"], pm["n"],
+                         int(nrhs[k]), B=Bh.data_ptr() + 8 * int(offs[k]),
+                         X=Xh.data_ptr() + 8 * int(offs[k]), key=i)
+            hits = s.wait(m)
+        hl = np.array([c["t_done"] - c["t_submit"] for c in hits]) * 1e3
+        hspan = max(c["t_done"] for c in hits) - min(c["t_submit"] for c in hits)
+        runs["resident_solves"] = {
+            "requests": m, "submitted": "all at once (latency includes queueing)",
+            "solves_per_s": float(nrhs[:m].sum()) / hspan, "requests_per_s": m / hspan,
+            "cache_hit_fraction": float(np.mean([c["cache_hit"] for c in hits])),
+            "p50_ms": float(np.percentile(hl, 50)), "p99_ms": float(np.percentile(hl, 99)),
+            "ok": int(sum(c["status"] == 0 for c in hits))}
+    clocks = sampler.stop()
     worst = max(b["bwd"] for b in bwd)
-    line = {"mode": "serve", "metric": "served solves/s, p50/p99 at <=1e-12 bwd err",
-            "value": sat["solves_per_s"], "unit": "solves/s (right-hand sides)",
-            "higher_is_better": True, "dtype": "f64 in/out (FP64 or split-TF32 + FP64 refinement)",
-            "data": "synthetic: A = Q diag(lam) Q^T, Q = 8 Householder reflectors, lam log-uniform "
-                    "on [1, kappa]",
-            "config": {"workload": f"{R} factor+solve requests per run over {P} matrices, n "
-                                   "log-uniform [64, 8192], kappa log-uniform [1e1, 1e6], nrhs ~ "
-                                   "U{1..32}, layouts uniform, FP64 / mixed uniform; arena 150 GB, "
-                                   "8 streams + batched launches for FP64 n <= 512, nrhs <= 8",
-                       "requests": R, "pool": P},
-            "runs": runs, "bwd_sampled": {"count": len(bwd), "max": worst,
-                                          "all_le_1e-12": bool(worst <= 1e-12),
-                                          "max_mixed": max([b["bwd"] for b in bwd if b["mode"] == 1] or [0.0])},
+    return {"workload": f"factor+solve requests over {P} matrices, n log-uniform [64, 8192], "
+                        "kappa log-uniform [1e1, 1e6], nrhs ~ U{1..32}, layouts uniform, FP64 / "
+                        "mixed uniform; arena 150 GB, 8 streams + batched launches for small "
+                        "FP64 requests",
+            "runs": runs,
+            "bwd_sampled": {"count": len(bwd), "max": worst, "all_le_1e-12": bool(worst <= 1e-12),
+                            "max_mixed": max([b["bwd"] for b in bwd if b["mode"] == 1] or [0.0])},
             "clocks": clocks}
-    print(json.dumps(line), flush=True)
 
 
 def run_surface(args):

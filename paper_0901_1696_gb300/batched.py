@@ -25,6 +25,10 @@ BUCKETS = (64, 128, 192, 256, 320, 384, 448, 512)   # upper ends of the n-bucket
 PANEL_WIDTHS = (16, 24, 32)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
                              "batched_tuning.json")
+# Tables measured by `autotune` on each listed GPU model and shipped with the
+# package, so that a fresh machine of that model needs no tuning run.
+SHIPPED_TABLES = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                              "batched_tuning_shipped.json")
 
 
 def bucket_of(n: int) -> int:
@@ -55,6 +59,13 @@ def make_entries(ns, transrs, uplos, nrhss, nb=None):
     return e, int(nt.sum()), int((ns * nrhss).sum())
 
 
+def _shipped() -> dict:
+    if os.path.exists(SHIPPED_TABLES):
+        with open(SHIPPED_TABLES) as f:
+            return json.load(f)
+    return {}
+
+
 class TuningCache:
     """{gpu name: {"f64" | "f32": {"N" | "T": [nb per bucket]}}} in a JSON file."""
 
@@ -66,7 +77,15 @@ class TuningCache:
                 self.data = json.load(f)
 
     def get(self, gpu: str, prec: str):
-        return self.data.get(gpu, {}).get(prec)
+        """The table tuned on this machine, else the shipped one, else None."""
+        return self.data.get(gpu, {}).get(prec) or _shipped().get(gpu, {}).get(prec)
+
+    def source(self, gpu: str, prec: str):
+        if self.data.get(gpu, {}).get(prec):
+            return "tuned on this machine"
+        if _shipped().get(gpu, {}).get(prec):
+            return "shipped table for this GPU model"
+        return None
 
     def put(self, gpu: str, prec: str, table: dict):
         self.data.setdefault(gpu, {})[prec] = table
