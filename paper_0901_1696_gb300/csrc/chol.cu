@@ -191,6 +191,21 @@ cudaError_t pftrs_impl(cudaStream_t st, const Layout &L, const T *arf_c, T *Bp, 
     View<T> B{Bp, 1, ldb};
     View<T> B1 = B, B2 = B.sub(L.n1, 0);
     stage_begin(st);
+    if constexpr (sizeof(T) == 8) {
+        // One launch per direction over the whole factor (rfp_solve.cu);
+        // the multi-launch form below when no scratch can be had (stream
+        // capture).
+        int32_t *sync = nullptr;
+        if (solve_scratch_acquire(st, rfp_solve_sync_words(nrhs), &sync) == cudaSuccess) {
+            cudaError_t e = rfp_solve(st, t1, s, t2, L.n1, L.n2, Bp, ldb, nrhs, false, sync);
+            stage_mark(st, "pftrs.forward");
+            if (e == cudaSuccess) e = rfp_solve(st, t1, s, t2, L.n1, L.n2, Bp, ldb, nrhs, true, sync);
+            stage_mark(st, "pftrs.backward");
+            const cudaError_t e2 = solve_scratch_release(st, sync);
+            return e != cudaSuccess ? e : e2;
+        }
+        (void)cudaGetLastError();   // the failed scratch request is not the caller's error
+    }
     // L Y = B
     RFP_TRY(trsm_left_lower_notrans(st, B1, nrhs, t1, L.n1, (const int32_t *)nullptr));
     RFP_TRY(gemm_nt(st, B2, s, B1.t(), L.n2, nrhs, L.n1, T(-1), T(1), MASK_NONE, MASK_NONE,

@@ -221,6 +221,20 @@ cudaError_t trsm_wavefront(cudaStream_t st, View<float> Lv, int64_t n, const flo
                            int64_t ldx, int64_t nrhs, bool trans, int32_t *sync, int32_t *err,
                            const int32_t *stop);
 
+// One-launch FP64 block substitution with the whole logical lower factor
+// (rfp_solve.cu): L Y = X (trans = false) or L^T Y = X (trans = true) in
+// place on X (n x nrhs, column-major, ldx), n = n1 + n2, L given by its three
+// RFP block views.  sync: device scratch of rfp_solve_sync_words(nrhs) int32
+// (cleared by the call, stream-ordered).  If a wait between tasks expires
+// (2 s), the blocks of X not computed are set to NaN.
+size_t rfp_solve_sync_words(int64_t nrhs);
+cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
+                      int64_t n2, double *X, int64_t ldx, int64_t nrhs, bool trans, int32_t *sync);
+// Stream-ordered scratch for the sync words, from a library-private memory
+// pool.  cudaErrorNotSupported while `st` is being captured into a graph.
+cudaError_t solve_scratch_acquire(cudaStream_t st, size_t words, int32_t **out);
+cudaError_t solve_scratch_release(cudaStream_t st, int32_t *p);
+
 // The rest of the LAPACK 3.2 RFP routine set (surface.cu kernels, chol.cu
 // orchestration), all on the logical lower triangle's three block views.
 // TP <-> RFP copy (lowerTP: the packed array holds the lower triangle).

@@ -1,0 +1,402 @@
+// One-launch FP64 triangular solves with the whole RFP factor (PFTRS).
+//
+// Section 4 solves A X = B with the factor L = [L11 0; L21 L22] held in the
+// RFP array's three blocks, as three steps each way (Fig. 4, "solve"):
+//   forward:  L11 Y1 = B1;  B2 -= L21 Y1;  L22 Y2 = B2
+//   backward: L22^T X2 = Y2;  Y1 -= L21^T X2;  L11^T X1 = Y1.
+// Both directions are block substitutions on the n x n lower triangle L,
+// whose 64-row blocks are cut separately in T1 (rows [0, n1)) and T2 (rows
+// [n1, n)), so every block of L lies inside one of T1, S or T2:
+//   forward, block row b:   X_b = L_bb^{-1} (B_b - sum_{j<b} L_bj X_j)
+//   backward, block row b:  X_b = L_bb^{-T} (Y_b - sum_{j>b} L_jb^T X_j).
+// One launch per direction computes all of it.  A task is (block row b,
+// group g of 16 right-hand-side columns).  Tasks take tickets from a device
+// counter in solve order (block rows in solve order, then column groups).
+// For each group, blocks complete in solve order (block b needs every
+// earlier one), so one progress word per group says how many of its blocks
+// are final; a task reads X_j only once that count has passed j.  A CTA
+// waits only on lower tickets, held by CTAs that are already running and
+// that wait only on lower tickets in turn, so every wait ends.  Each wait is
+// also bounded in time: on expiry the CTA raises the error word, every task
+// that sees it gives up, and each task that gives up writes NaN into its own
+// block of X, so an incomplete solve cannot pass for a result.
+//
+// Per task: 128 threads, each owning 4 rows x 2 columns of the 64 x 16
+// block in registers.  Blocks of L are streamed through shared memory in
+// 64 x 16 chunks (register-staged, double-buffered); X_j is read from L2
+// (ld.global.cg: other SMs wrote it during this launch).  The diagonal block
+// is then solved in shared memory by substitution, one warp per 4 columns,
+// each lane holding two rows, the solved value broadcast by shuffles.
+#include <cmath>
+#include <mutex>
+
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+namespace {
+
+constexpr int kR = 64;              // rows per block
+constexpr int kG = 16;              // right-hand sides per task
+constexpr int kKc = 16;             // K chunk staged in shared memory
+constexpr int kThreads = 128;
+constexpr int kAsLd = kR + 2;       // doubles
+constexpr int kXsLd = kG + 2;
+constexpr int kLdLd = kR + 1;
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr int kErrWait = 4;
+
+struct SolveArgs {
+    View<double> t1, s, t2;
+    int64_t n1, n2;
+    int nb1, nb;                    // row blocks in T1, in total
+    double *X;
+    int64_t ldx, nrhs;
+    int ng;
+    int32_t *counter, *prog, *err;
+};
+
+__device__ __forceinline__ uint64_t rs_globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// First row (global) and row count of block b.
+__device__ __forceinline__ void block_rows(const SolveArgs &a, int b, int64_t &r0, int &rows)
+{
+    if (b < a.nb1) {
+        r0 = (int64_t)b * kR;
+        rows = (int)(int)(a.n1 - r0 < kR ? a.n1 - r0 : kR);
+    } else {
+        const int64_t lr = (int64_t)(b - a.nb1) * kR;
+        r0 = a.n1 + lr;
+        rows = (int)(int)(a.n2 - lr < kR ? a.n2 - lr : kR);
+    }
+}
+
+// View of block (bi, bj) of L, bi >= bj, at the block's first element.
+__device__ __forceinline__ View<double> lblock(const SolveArgs &a, int bi, int bj)
+{
+    const int64_t ri = bi < a.nb1 ? (int64_t)bi * kR : (int64_t)(bi - a.nb1) * kR;
+    const int64_t cj = bj < a.nb1 ? (int64_t)bj * kR : (int64_t)(bj - a.nb1) * kR;
+    if (bi < a.nb1) return a.t1.sub(ri, cj);
+    if (bj < a.nb1) return a.s.sub(ri, cj);
+    return a.t2.sub(ri, cj);
+}
+
+// Thread 0 waits until *prog >= need; false if the error word is (or becomes) set.
+__device__ __forceinline__ bool wait_progress(const int32_t *prog, int need, int32_t *err)
+{
+    const uint64_t t0 = rs_globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (*(volatile const int32_t *)prog >= need) return true;
+        if (*(volatile int32_t *)err != 0) return false;
+        __nanosleep(32);
+        if ((it & 63) == 63 && rs_globaltimer() - t0 > kWaitNs) {
+            atomicCAS(err, 0, kErrWait);
+            return false;
+        }
+    }
+}
+
+// Staging of one 64 x 16 chunk of op(L_jb) (rows r < rv of the task's block,
+// k in [k0, k0 + 16) < kv) and of the matching 16 x 16 chunk of X_j.
+// A(r, k) = V(r, k) for a view V; the loader reads along V's unit stride.
+struct ChunkRegs {
+    double a[kR * kKc / kThreads];   // 8
+    double x[kKc * kG / kThreads];   // 2
+
+    __device__ __forceinline__ void load(View<double> V, int rv, int k0, int kv, const double *Xj,
+                                         int64_t ldx, int cols)
+    {
+        const int tid = threadIdx.x;
+        if (V.rs == 1) {      // rows contiguous
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int r = tid % kR, k = k0 + tid / kR + 2 * q;
+                a[q] = (r < rv && k < kv) ? __ldg(&V.p[r + (int64_t)k * V.cs]) : 0.0;
+            }
+        } else {              // k contiguous
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + tid % kKc, r = tid / kKc + 8 * q;
+                a[q] = (r < rv && k < kv) ? __ldg(&V.p[(int64_t)r * V.rs + k * V.cs]) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k = k0 + tid % kKc, c = tid / kKc + 8 * q;
+            x[q] = (k < kv && c < cols) ? __ldcg(Xj + (int64_t)c * ldx + k) : 0.0;
+        }
+    }
+    __device__ __forceinline__ void store(const View<double> &V, double (*As)[kAsLd],
+                                          double (*Xs)[kXsLd]) const
+    {
+        const int tid = threadIdx.x;
+        if (V.rs == 1) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) As[tid / kR + 2 * q][tid % kR] = a[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) As[tid % kKc][tid / kKc + 8 * q] = a[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) Xs[tid % kKc][tid / kKc + 8 * q] = x[q];
+    }
+};
+
+struct UpdateSmem {
+    double As[2][kKc][kAsLd];
+    double Xs[2][kKc][kXsLd];
+};
+struct DiagSmem {
+    double Ld[kR][kLdLd];       // lower triangle of L_bb
+    double Bs[kR][kG + 1];      // the block's right-hand side, redistributed
+};
+union SolveSmem {
+    UpdateSmem u;
+    DiagSmem d;
+};
+
+template <bool TRANS>
+__global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
+{
+    __shared__ __align__(16) SolveSmem sm;
+    __shared__ int s_ticket, s_ok;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_ticket = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int ticket = s_ticket;
+    const int g = ticket % a.ng, p = ticket / a.ng;          // p: position in solve order
+    const int b = TRANS ? a.nb - 1 - p : p;
+    int64_t r0;
+    int rows;
+    block_rows(a, b, r0, rows);
+    const int64_t c0 = (int64_t)g * kG;
+    const int cols = (int)(a.nrhs - c0 < kG ? a.nrhs - c0 : kG);
+    double *Xb = a.X + r0 + c0 * a.ldx;
+    int32_t *prog = a.prog + g;
+
+    const int tx = tid % 8, ty = tid / 8;                    // 2 columns x 4 rows each
+    double acc[4][2];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int r = ty * 4 + m, cc = tx * 2 + c;
+            acc[m][c] = (r < rows && cc < cols) ? __ldcg(Xb + (int64_t)cc * a.ldx + r) : 0.0;
+        }
+
+    bool ok = true;
+    // Off-diagonal blocks in solve order: forward j = 0 .. b-1, backward j = nb-1 .. b+1.
+    const int nblk = p;
+    for (int q = 0; q < nblk && ok; ++q) {
+        const int j = TRANS ? a.nb - 1 - q : q;
+        if (tid == 0) {
+            s_ok = wait_progress(prog, q + 1, a.err) ? 1 : 0;
+            __threadfence();
+        }
+        __syncthreads();
+        if (!s_ok) {
+            ok = false;
+            break;
+        }
+        int64_t j0;
+        int kv;
+        block_rows(a, j, j0, kv);
+        // op(L) for this task: forward A = L_bj (rows b, k over j);
+        // backward A = L_jb^T (rows b, k over j).
+        const View<double> V = TRANS ? lblock(a, j, b).t() : lblock(a, b, j);
+        const double *Xj = a.X + j0 + c0 * a.ldx;
+        const int nch = (kv + kKc - 1) / kKc;
+        ChunkRegs st;
+        st.load(V, rows, 0, kv, Xj, a.ldx, cols);
+        for (int ch = 0; ch < nch; ++ch) {
+            const int buf = ch & 1;
+            st.store(V, sm.u.As[buf], sm.u.Xs[buf]);
+            __syncthreads();
+            if (ch + 1 < nch) st.load(V, rows, (ch + 1) * kKc, kv, Xj, a.ldx, cols);
+#pragma unroll
+            for (int kk = 0; kk < kKc; ++kk) {
+                const double2 a01 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * 4]);
+                const double2 a23 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * 4 + 2]);
+                const double2 x = *reinterpret_cast<const double2 *>(&sm.u.Xs[buf][kk][tx * 2]);
+                const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    acc[m][0] = fma(-av[m], x.x, acc[m][0]);
+                    acc[m][1] = fma(-av[m], x.y, acc[m][1]);
+                }
+            }
+            // the next store overwrites the other buffer, last read two chunks ago
+        }
+        __syncthreads();   // all reads of this block's buffers done before the next block
+    }
+
+    if (!ok) {             // a wait gave up: mark this block of X as not computed
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int r = ty * 4 + m, cc = tx * 2 + c;
+                if (r < rows && cc < cols) Xb[(int64_t)cc * a.ldx + r] = __longlong_as_double(0x7ff8000000000000ll);
+            }
+        return;
+    }
+
+    // Diagonal block: the lower triangle of L_bb into shared memory, the
+    // right-hand side from the accumulators, then substitution.
+    {
+        const View<double> D = lblock(a, b, b);
+        const bool rowfast = D.rs == 1;
+        for (int e = tid; e < kR * kR; e += kThreads) {
+            const int u = e % kR, v = e / kR;
+            const int i = rowfast ? u : v, jj = rowfast ? v : u;
+            if (i < rows && jj <= i) sm.d.Ld[i][jj] = D(i, jj);
+        }
+    }
+    // The right-hand side is redistributed through shared memory: lane l of
+    // warp w takes rows l and l + 32 of columns 4w .. 4w + 3.
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) sm.d.Bs[ty * 4 + m][tx * 2 + c] = acc[m][c];
+    __syncthreads();
+    double v[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[h][c] = sm.d.Bs[lane + 32 * h][warp * 4 + c];
+
+    // Step j: the owner lane of row j divides it by the pivot and broadcasts
+    // it; every lane then removes x_j from its later (forward) or earlier
+    // (backward) rows.  Indices into v are compile-time (no local memory).
+    for (int q = 0; q < rows; ++q) {
+        const int j = TRANS ? rows - 1 - q : q;
+        const int owner = j & 31;
+        const bool hi = j >= 32;
+        const double d = sm.d.Ld[j][j];
+        double xj[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double own = hi ? v[1][c] : v[0][c];
+            xj[c] = __shfl_sync(0xffffffffu, own / d, owner);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int r = lane + 32 * hh;
+            if (r == j) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[hh][c] = xj[c];
+            } else if (TRANS ? r < j : (r > j && r < rows)) {
+                const double l = TRANS ? sm.d.Ld[j][r] : sm.d.Ld[r][j];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[hh][c] = fma(-l, xj[c], v[hh][c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int cc = warp * 4 + c;
+        if (cc >= cols) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;
+            if (r < rows) Xb[(int64_t)cc * a.ldx + r] = v[h][c];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicExch(prog, p + 1);
+}
+
+}  // namespace
+
+size_t rfp_solve_sync_words(int64_t nrhs)
+{
+    return (size_t)(2 + (nrhs + kG - 1) / kG);
+}
+
+cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
+                      int64_t n2, double *X, int64_t ldx, int64_t nrhs, bool trans, int32_t *sync)
+{
+    const int64_t n = n1 + n2;
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    const int64_t nb1 = (n1 + kR - 1) / kR, nb2 = (n2 + kR - 1) / kR, ng = (nrhs + kG - 1) / kG;
+    const int64_t tasks = (nb1 + nb2) * ng;
+    if (tasks > INT32_MAX) return cudaErrorInvalidValue;
+    // sync: [0] ticket counter, [1] error word, [2 .. 2 + ng) progress per
+    // column group; all start at zero.
+    cudaError_t e = cudaMemsetAsync(sync, 0, rfp_solve_sync_words(nrhs) * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, ldx, nrhs, (int)ng,
+                sync, sync + 2, sync + 1};
+    if (trans) rfp_solve_kernel<true><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+    else rfp_solve_kernel<false><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- stream-ordered scratch for the sync words ------------------------------
+//
+// A library-private memory pool per device (created on first use, never
+// destroyed) from which each solve takes its few sync words with
+// cudaMallocFromPoolAsync and returns them with cudaFreeAsync on the same
+// stream, so concurrent solves on different streams never share them.  The
+// pool keeps up to 1 MiB between calls instead of returning it to the driver.
+// Under stream capture the caller does not use it (it runs the multi-launch
+// form instead).
+
+namespace {
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaError_t solve_scratch_acquire(cudaStream_t st, size_t words, int32_t **out)
+{
+    *out = nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap != cudaStreamCaptureStatusNone) return cudaErrorNotSupported;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorNotSupported;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t p;
+            e = cudaMemPoolCreate(&p, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = 1u << 20;
+            e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(p);
+                return e;
+            }
+            g_pool[dev] = p;
+        }
+        pool = g_pool[dev];
+    }
+    void *ptr = nullptr;
+    e = cudaMallocFromPoolAsync(&ptr, words * sizeof(int32_t), pool, st);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<int32_t *>(ptr);
+    return cudaSuccess;
+}
+
+cudaError_t solve_scratch_release(cudaStream_t st, int32_t *p)
+{
+    return p ? cudaFreeAsync(p, st) : cudaSuccess;
+}
+
+}  // namespace rfp

@@ -12,7 +12,8 @@
 
 typedef int cudaError_t;
 typedef void *cudaStream_t;
-enum { cudaSuccess = 0, cudaErrorInvalidValue = 1, cudaErrorIllegalAddress = 700 };
+enum { cudaSuccess = 0, cudaErrorInvalidValue = 1, cudaErrorIllegalAddress = 700,
+       cudaErrorNotSupported = 801 };
 
 typedef void *cudaEvent_t;
 cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t s);
@@ -21,3 +22,4 @@ cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s);
 cudaError_t cudaEventSynchronize(cudaEvent_t e);
 cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b);
 const char *cudaGetErrorName(cudaError_t e);
+cudaError_t cudaGetLastError(void);

@@ -123,6 +123,7 @@ cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t)
     return cudaSuccess;
 }
 const char *cudaGetErrorName(cudaError_t e) { return e ? "emulated error" : "cudaSuccess"; }
+cudaError_t cudaGetLastError(void) { return cudaSuccess; }
 cudaError_t cudaEventCreate(cudaEvent_t *e) { *e = nullptr; return cudaSuccess; }
 cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
@@ -375,6 +376,103 @@ cudaError_t trsm_wavefront(cudaStream_t, View<float> Lv, int64_t n, const float 
         L.wr(sync + 1 + i * ng + g, 1);
     }
     return L.commit();
+}
+
+// rfp_solve: one ordered launch of (block row, 16-column group) tasks in
+// ticket order (block rows in solve order, then column groups).  Each task
+// reads its rows of X, the blocks of L to the left of its diagonal block
+// (forward) or below it (backward), transposed for the backward solve, and the
+// final X blocks of the earlier tasks of its group; it writes its X block
+// and its group's progress word.  L is addressed through the three RFP block
+// views exactly as the kernel addresses it.
+size_t rfp_solve_sync_words(int64_t nrhs) { return (size_t)(2 + (nrhs + 15) / 16); }
+
+cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double> t2, int64_t n1,
+                      int64_t n2, double *X, int64_t ldx, int64_t nrhs, bool trans, int32_t *sync)
+{
+    const int64_t n = n1 + n2;
+    if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    const int64_t R = 64, nb1 = (n1 + R - 1) / R, nb = nb1 + (n2 + R - 1) / R, ng = (nrhs + 15) / 16;
+    Launch L;
+    L.ordered = true;
+    for (size_t w = 0; w < rfp_solve_sync_words(nrhs); ++w) L.wr(sync + w, 0);   // the memset
+    auto rows_of = [&](int64_t b, int64_t &r0, int64_t &rows) {
+        if (b < nb1) { r0 = b * R; rows = std::min(R, n1 - r0); }
+        else { const int64_t lr = (b - nb1) * R; r0 = n1 + lr; rows = std::min(R, n2 - lr); }
+    };
+    // element (i, j), i >= j, of block (bi, bj) of L
+    auto lel = [&](int64_t bi, int64_t bj, int64_t i, int64_t j) -> const double * {
+        const int64_t ri = (bi < nb1 ? bi * R : (bi - nb1) * R) + i;
+        const int64_t cj = (bj < nb1 ? bj * R : (bj - nb1) * R) + j;
+        if (bi < nb1) return &t1(ri, cj);
+        if (bj < nb1) return &s(ri, cj);
+        return &t2(ri, cj);
+    };
+    int32_t *prog = sync + 2;
+    for (int64_t t = 0; t < nb * ng; ++t) {
+        L.cta = (int)t;
+        L.wr(sync, (int32_t)(t + 1));                       // ticket counter
+        const int64_t g = t % ng, p = t / ng, b = trans ? nb - 1 - p : p;
+        int64_t r0, rows;
+        rows_of(b, r0, rows);
+        const int64_t c0 = g * 16, cols = std::min<int64_t>(16, nrhs - c0);
+        std::vector<double> acc(rows * cols);
+        for (int64_t c = 0; c < cols; ++c)
+            for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = L.rd(&X[(c0 + c) * ldx + r0 + r]);
+        for (int64_t q = 0; q < p; ++q) {
+            const int64_t j = trans ? nb - 1 - q : q;
+            if (L.rd(prog + g) < q + 1) violation("X block read before its group's progress", prog + g);
+            int64_t j0, kv;
+            rows_of(j, j0, kv);
+            for (int64_t c = 0; c < cols; ++c)
+                for (int64_t r = 0; r < rows; ++r) {
+                    double sum = acc[c * rows + r];
+                    for (int64_t k = 0; k < kv; ++k) {
+                        const double a = trans ? L.rd(lel(j, b, k, r)) : L.rd(lel(b, j, r, k));
+                        sum -= a * L.rd(&X[(c0 + c) * ldx + j0 + k]);
+                    }
+                    acc[c * rows + r] = sum;
+                }
+        }
+        for (int64_t c = 0; c < cols; ++c) {     // substitution with the diagonal block
+            double *v = &acc[c * rows];
+            if (!trans) {
+                for (int64_t j = 0; j < rows; ++j) {
+                    v[j] /= L.rd(lel(b, b, j, j));
+                    for (int64_t r = j + 1; r < rows; ++r) v[r] -= L.rd(lel(b, b, r, j)) * v[j];
+                }
+            } else {
+                for (int64_t j = rows - 1; j >= 0; --j) {
+                    v[j] /= L.rd(lel(b, b, j, j));
+                    for (int64_t r = 0; r < j; ++r) v[r] -= L.rd(lel(b, b, j, r)) * v[j];
+                }
+            }
+            for (int64_t r = 0; r < rows; ++r) L.wr(&X[(c0 + c) * ldx + r0 + r], v[r]);
+        }
+        L.wr(prog + g, (int32_t)(p + 1));
+    }
+    return L.commit();
+}
+
+// The emulated scratch: heap memory registered as a device buffer for the
+// duration of the call.
+cudaError_t solve_scratch_acquire(cudaStream_t, size_t words, int32_t **out)
+{
+    int32_t *p = new int32_t[words];
+    emu_register(p, words * sizeof(int32_t));
+    *out = p;
+    return cudaSuccess;
+}
+
+cudaError_t solve_scratch_release(cudaStream_t, int32_t *p)
+{
+    for (size_t i = 0; i < g_regions.size(); ++i)
+        if (g_regions[i].lo == (uintptr_t)p) {
+            g_regions.erase(g_regions.begin() + (long)i);
+            break;
+        }
+    delete[] p;
+    return cudaSuccess;
 }
 
 // ---- the rest of the LAPACK 3.2 RFP routine set ----
