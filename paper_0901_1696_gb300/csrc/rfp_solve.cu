@@ -154,6 +154,7 @@ struct UpdateSmem {
 struct DiagSmem {
     double Ld[kR][kLdLd];       // lower triangle of L_bb
     double Bs[kR][kG + 1];      // the block's right-hand side, redistributed
+    double rinv[kR];            // 1 / L_bb(j, j)
 };
 union SolveSmem {
     UpdateSmem u;
@@ -257,6 +258,10 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
             const int i = rowfast ? u : v, jj = rowfast ? v : u;
             if (i < rows && jj <= i) sm.d.Ld[i][jj] = D(i, jj);
         }
+        // Reciprocals of the pivots, formed once in parallel: on GB300's
+        // narrow FP64 pipe a division per lane per step would cost more
+        // than the substitution's multiply-adds.
+        if (tid < rows) sm.d.rinv[tid] = 1.0 / D(tid, tid);
     }
     // The right-hand side is redistributed through shared memory: lane l of
     // warp w takes rows l and l + 32 of columns 4w .. 4w + 3.
@@ -271,19 +276,20 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[h][c] = sm.d.Bs[lane + 32 * h][warp * 4 + c];
 
-    // Step j: the owner lane of row j divides it by the pivot and broadcasts
-    // it; every lane then removes x_j from its later (forward) or earlier
-    // (backward) rows.  Indices into v are compile-time (no local memory).
+    // Step j: row j is broadcast from its owner lane and scaled by the
+    // pivot's reciprocal; every lane then removes x_j from its later
+    // (forward) or earlier (backward) rows.  Indices into v are compile-time
+    // (no local memory).
     for (int q = 0; q < rows; ++q) {
         const int j = TRANS ? rows - 1 - q : q;
         const int owner = j & 31;
         const bool hi = j >= 32;
-        const double d = sm.d.Ld[j][j];
+        const double ri = sm.d.rinv[j];
         double xj[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const double own = hi ? v[1][c] : v[0][c];
-            xj[c] = __shfl_sync(0xffffffffu, own / d, owner);
+            xj[c] = __shfl_sync(0xffffffffu, own, owner) * ri;
         }
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {

@@ -374,9 +374,14 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
 
     const int row = tid % kStripRows, grp = tid / kStripRows;   // 4 column groups
     T *xr = Xs + row * kTileLd;
+    // Reciprocals of the pivots, formed once (row tid of the diagonal): a
+    // division per row per step would dominate on GB300's narrow FP64 pipe.
+    T *rinv = Xs + kTileMax * kTileLd;
+    if (tid < w) rinv[tid] = T(1) / Ls[tid * kTileLd + tid];
+    __syncthreads();
     if (a.transL) {                  // X L^T = B: columns in increasing order
         for (int j = 0; j < w; ++j) {
-            if (grp == 0) xr[j] = xr[j] / Ls[j * kTileLd + j];
+            if (grp == 0) xr[j] = xr[j] * rinv[j];
             __syncthreads();
             const T xj = xr[j];
             for (int c = j + 1 + grp; c < w; c += 4) xr[c] -= xj * Ls[c * kTileLd + j];
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(256) trsm_right_kernel(TrsmArgs<T> a)
         }
     } else {                         // X L = B: columns in decreasing order
         for (int j = w - 1; j >= 0; --j) {
-            if (grp == 0) xr[j] = xr[j] / Ls[j * kTileLd + j];
+            if (grp == 0) xr[j] = xr[j] * rinv[j];
             __syncthreads();
             const T xj = xr[j];
             for (int c = grp; c < j; c += 4) xr[c] -= xj * Ls[j * kTileLd + c];
@@ -473,7 +478,7 @@ cudaError_t trsm_strip(cudaStream_t st, View<T> X, View<T> Ltri, int64_t M, int 
         note_launch();
         return cudaGetLastError();
     }
-    const int smem = 2 * kTileMax * kTileLd * (int)sizeof(T);
+    const int smem = (2 * kTileMax * kTileLd + kTileMax) * (int)sizeof(T);
     cudaError_t e = set_smem_once<T>((const void *)trsm_right_kernel<T>, smem);
     if (e != cudaSuccess) return e;
     TrsmArgs<T> a{X, Ltri, M, w, transL, alpha, abort, unit ? 1 : 0};
@@ -506,45 +511,61 @@ __device__ __forceinline__ void store_lower_tile(View<T> A, const T *S, int w)
     }
 }
 
-// Unblocked right-looking Cholesky of one tile.  At step j every thread reads
-// the (final) pivot S[j][j] itself and uses l_ij = S[i][j] * (1 / sqrt(pivot))
+// Unblocked right-looking Cholesky of one tile, l_ij = a_ij * (1 / sqrt(pivot))
 // (LAPACK's unblocked Cholesky also scales a column by the reciprocal of its
-// diagonal).  FP32: one barrier per column, each thread forms the scaled
-// values it needs and the columns are scaled on write-back.  FP64: the
-// column is scaled in place first (two barriers per column), so a trailing
-// element costs one DFMA.
+// diagonal).
+// FP64: at step j one thread forms the pivot's square root and reciprocal
+// (on GB300's narrow FP64 pipe a square root and a division in every thread
+// would cost more than the step's multiply-adds), the column is scaled in
+// place, and the trailing triangle is updated by a 16 x 16 grid of threads
+// (one DFMA per element); three barriers per column.
+// FP32: one barrier per column; each thread forms the pivot's reciprocal and
+// the scaled values it needs, and the columns are scaled on write-back.
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32_t *info,
                                                          int64_t base)
 {
     __shared__ __align__(16) T S[kTileMax * kTileLd];
     __shared__ T rinv[kTileMax], sq[kTileMax];
+    __shared__ int s_fail;
     if (*info != 0) return;
     load_lower_tile(S, A, w);
     __syncthreads();
     int fail = -1;
-    for (int j = 0; j < w; ++j) {
-        const T d = S[j * kTileLd + j];
-        if (!(d > T(0))) { fail = j; break; }      // every thread sees the same d
-        const T r = sqrt(d), ri = T(1) / r;
-        if (threadIdx.x == 0) { sq[j] = r; rinv[j] = ri; }
-        const int rem = w - j - 1;
-        if constexpr (sizeof(T) == 8) {
-            // FP64: scale the column once (one extra barrier) so that each
-            // trailing element costs one DFMA on the FP64 pipe
+    if constexpr (sizeof(T) == 8) {
+        const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+        for (int j = 0; j < w; ++j) {
+            if (threadIdx.x == 0) {
+                const T d = S[j * kTileLd + j];
+                s_fail = (d > T(0)) ? -1 : j;              // pivot <= 0 or NaN fails
+                const T r = sqrt(d);
+                sq[j] = r;
+                rinv[j] = T(1) / r;
+            }
+            __syncthreads();
+            if (s_fail >= 0) { fail = s_fail; break; }
+            const T ri = rinv[j];
             for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) S[i * kTileLd + j] *= ri;
             __syncthreads();
-            for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-                const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-                if (k <= i) S[i * kTileLd + k] -= S[i * kTileLd + j] * S[k * kTileLd + j];
+            for (int i = j + 1 + ty; i < w; i += 16) {
+                const T lij = S[i * kTileLd + j];
+                for (int k = j + 1 + tx; k <= i; k += 16) S[i * kTileLd + k] -= lij * S[k * kTileLd + j];
             }
-        } else {
+            __syncthreads();
+        }
+    } else {
+        for (int j = 0; j < w; ++j) {
+            const T d = S[j * kTileLd + j];
+            if (!(d > T(0))) { fail = j; break; }      // every thread sees the same d
+            const T r = sqrt(d), ri = T(1) / r;
+            if (threadIdx.x == 0) { sq[j] = r; rinv[j] = ri; }
+            const int rem = w - j - 1;
             for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
                 const int i = j + 1 + e / rem, k = j + 1 + e % rem;
                 if (k <= i) S[i * kTileLd + k] -= (S[i * kTileLd + j] * ri) * (S[k * kTileLd + j] * ri);
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
     if (fail >= 0) {
         if (threadIdx.x == 0) *info = (int32_t)(base + fail + 1);
