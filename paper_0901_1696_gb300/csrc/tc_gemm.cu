@@ -5,17 +5,23 @@
 //
 // This is the SYRK / GEMM of the paper's step 3 (Fig. 4, T2 <- T2 - S S^T)
 // and of the trailing updates inside the Cholesky of a triangle, run on the
-// 5th-generation tensor cores:
-//   * one 128 x 128 output tile per CTA (TMEM: 128 lanes x 128 FP32 columns),
+// 5th-generation tensor cores.  The kernel is persistent: one CTA per SM
+// walks the list of 128 x 128 output tiles (lower-triangular tiles only for
+// a SYRK), tiles b, b + grid, b + 2 grid, ...
 //   * warp 4 issues TMA loads (cp.async.bulk.tensor.2d, 128-byte swizzle) of
-//     128-byte K slices of A and B into a 4-stage shared-memory ring,
+//     128-byte K slices of A and B into a 4-stage shared-memory ring that
+//     runs on across tile boundaries,
 //   * warp 5 (one thread) issues tcgen05.mma (K = 32 bytes per instruction)
-//     and tcgen05.commit to release each stage and finally the accumulator,
-//   * warps 0-3 read the accumulator with tcgen05.ld (one TMEM lane per
-//     thread = one C row) and apply the masked epilogue to C.
+//     into one of two TMEM accumulators (2 x 128 FP32 columns), alternating
+//     between consecutive tiles, and tcgen05.commit to release each stage
+//     and to hand each finished accumulator to the epilogue,
+//   * warps 0-3 read an accumulator with tcgen05.ld (one TMEM lane per
+//     thread = one C row), hand it back, and apply the masked epilogue to C;
+//     meanwhile the MMAs of the next tile fill the other accumulator.
 // Every mbarrier wait is bounded by time; on expiry the kernel records an
-// error code in *err, stops issuing work, waits (bounded) for its in-flight
-// copies and MMAs, frees its tensor memory and returns.
+// error code in *err and every role stops issuing work; the producer then
+// waits (bounded) for its copies in flight, the MMA issuer for its MMAs, and
+// the CTA frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -33,7 +39,7 @@ constexpr int kRowBytes = 128;                    // one K slice per row (swizzl
 constexpr int kTileBytes = kBM * kRowBytes;       // 16 KB per operand per stage
 constexpr int kThreads = 192;                     // 4 epilogue warps + TMA warp + MMA warp
 constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s bound on any single wait
-constexpr int kSmemBytes = 1024 /*align*/ + 2 * kStages * kTileBytes + 256;
+constexpr int kSmemBytes = 1024 /*align*/ + 2 * kStages * kTileBytes + 256;   // + barriers, TMEM slot
 
 struct Args {
     float *C;
@@ -43,7 +49,8 @@ struct Args {
     float alpha, beta;
     int cmode;              // MASK_LOWER: write only i >= j (C-local)
     int tiles_n;            // column tiles
-    int lower_tiles;        // 1: blockIdx.x enumerates the lower-triangular tile set
+    int lower_tiles;        // 1: the tile list is the lower-triangular tile set
+    int64_t num_tiles;      // tiles in the list
     int *err;
 };
 
@@ -100,6 +107,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
             }
         }
     }
+}
+
+// Wait bounded by time only (not by the error word): used to let work
+// already issued finish before the CTA tears down.
+__device__ __forceinline__ bool mbar_wait_quiet(uint64_t *bar, uint32_t parity)
+{
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -186,6 +209,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Tile t of the launch's tile list: (row tile, column tile).
+__device__ __forceinline__ void tile_coords(const Args &a, int64_t t, int64_t &tm, int64_t &tn)
+{
+    if (a.lower_tiles) {   // row-major lower-triangular tile list
+        int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+        while (r * (r + 1) / 2 > t) --r;
+        tm = r;
+        tn = t - r * (r + 1) / 2;
+    } else {
+        tm = t / a.tiles_n;
+        tn = t % a.tiles_n;
+    }
+}
+
+// Persistent: CTA b computes tiles b, b + gridDim.x, ... of the tile list.
+// Two accumulators of kBN TMEM columns alternate between consecutive tiles
+// of a CTA, so the epilogue of one tile overlaps the loads and MMAs of the
+// next; the shared-memory ring runs on across tile boundaries.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -198,32 +240,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sB = base + kStages * kTileBytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(sB + kStages * kTileBytes);
     uint64_t *empty = full + kStages;
-    uint64_t *accf = empty + kStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+    uint64_t *accf = empty + kStages;     // [2] accumulator ready (MMA commit)
+    uint64_t *acce = accf + 2;            // [2] accumulator drained (4 epilogue warps)
+    uint64_t *drain = acce + 2;           // every MMA of this CTA completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-
-    // Tile coordinates.
-    int64_t tm, tn;
-    if (a.lower_tiles) {   // row-major lower-triangular tile list
-        const int64_t t = blockIdx.x;
-        int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((r + 1) * (r + 2) / 2 <= t) ++r;
-        while (r * (r + 1) / 2 > t) --r;
-        tm = r;
-        tn = t - r * (r + 1) / 2;
-    } else {
-        tm = blockIdx.x / a.tiles_n;
-        tn = blockIdx.x % a.tiles_n;
-    }
-    const int64_t m0 = tm * kBM, n0 = tn * kBN;
     const int bk = kRowBytes / (KIND == 0 ? 2 : 4);                 // K elements per stage
     const int nk = (int)((a.K + bk - 1) / bk);
 
-    if (warp == 0) {   // one warp allocates the accumulator columns
+    if (warp == 0) {   // one warp allocates both accumulators
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kBN)
+                     "r"(2 * kBN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -232,86 +261,121 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int64_t ntiles = a.num_tiles;
 
-    int issued = 0;     // stages loaded by the producer (producer thread only)
     if (warp == 4 && lane == 0) {
-        // ---- TMA producer
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % kStages, r = kt / kStages;
-            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, a.err, 1)) break;
-            mbar_expect_tx(&full[s], 2 * kTileBytes);
-            tma_load_2d(sA + s * kTileBytes, &tmA, &full[s], kt * bk, a.a_row0 + (int)m0);
-            tma_load_2d(sB + s * kTileBytes, &tmB, &full[s], kt * bk, a.b_row0 + (int)n0);
-            issued = kt + 1;
+        // ---- TMA producer: stage it of the ring holds K slice kt of a tile
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int64_t tm, tn;
+            tile_coords(a, t, tm, tn);
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                const int s = (int)(it % kStages);
+                const int64_t r = it / kStages;
+                if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1), a.err, 1)) { ok = false; break; }
+                mbar_expect_tx(&full[s], 2 * kTileBytes);
+                tma_load_2d(sA + s * kTileBytes, &tmA, &full[s], kt * bk, a.a_row0 + (int)(tm * kBM));
+                tma_load_2d(sB + s * kTileBytes, &tmB, &full[s], kt * bk, a.b_row0 + (int)(tn * kBN));
+            }
         }
-        // On failure, let the copies already issued land before the CTA exits.
-        if (issued < nk)
-            for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
-                mbar_wait(&full[kt % kStages], (kt / kStages) & 1, a.err, 1);
+        // On failure, let the copies still in flight land before the CTA exits
+        // (the last kStages stages issued, each waited on its own phase).
+        if (!ok)
+            for (int64_t q = (it > kStages ? it - kStages : 0); q < it; ++q)
+                mbar_wait_quiet(&full[q % kStages], (uint32_t)((q / kStages) & 1));
     } else if (warp == 5 && lane == 0) {
         // ---- MMA issuer
+        int64_t it = 0, lt = 0;
         bool ok = true;
-        int kt = 0;
-        for (; kt < nk; ++kt) {
-            const int s = kt % kStages, r = kt / kStages;
-            if (!mbar_wait(&full[s], r & 1, a.err, 2)) { ok = false; break; }
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+            const int buf = (int)(lt & 1);
+            const int64_t u = lt >> 1;
+            if (u > 0 && !mbar_wait(&acce[buf], (uint32_t)((u - 1) & 1), a.err, 2)) { ok = false; break; }
             fence_after();
-            const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+            const uint32_t acc = tmem + (uint32_t)(buf * kBN);
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                const int s = (int)(it % kStages);
+                if (!mbar_wait(&full[s], (uint32_t)((it / kStages) & 1), a.err, 2)) { ok = false; break; }
+                fence_after();
+                const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
 #pragma unroll
-            for (int kk = 0; kk < kRowBytes / 32; ++kk)
-                mma<KIND>(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
-                          (kt | kk) != 0 ? 1u : 0u);
-            mma_commit(&empty[s]);
+                for (int kk = 0; kk < kRowBytes / 32; ++kk)
+                    mma<KIND>(acc, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
+                              (kt | kk) != 0 ? 1u : 0u);
+                mma_commit(&empty[s]);
+            }
+            if (ok) mma_commit(&accf[buf]);
         }
-        mma_commit(accf);   // arrives once every MMA issued above has completed
-        (void)ok;
+        // Every MMA issued above completes before the CTA tears down.
+        mma_commit(drain);
+        mbar_wait_quiet(drain, 0);
     } else if (warp < 4) {
         // ---- epilogue: lane = row of the tile
-        // warp-uniform decision: tcgen05.ld is a .sync.aligned warp instruction
-        const bool have = __all_sync(0xffffffffu, nk > 0 && mbar_wait(accf, 0, a.err, 3));
-        fence_after();
-        const int64_t i = m0 + warp * 32 + lane;
-        const bool row_ok = i < a.M && *(volatile int *)a.err == 0;
+        int64_t lt = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int buf = (int)(lt & 1);
+            const int64_t u = lt >> 1;
+            int64_t tm, tn;
+            tile_coords(a, t, tm, tn);
+            const int64_t m0 = tm * kBM, n0 = tn * kBN;
+            // warp-uniform decision: tcgen05.ld is a .sync.aligned warp instruction
+            const bool have = __all_sync(0xffffffffu, nk > 0 &&
+                                                          mbar_wait(&accf[buf], (uint32_t)(u & 1), a.err, 3));
+            if (nk > 0 && !have) break;
+            fence_after();
+            const int64_t i = m0 + warp * 32 + lane;
+            const bool row_ok = i < a.M;
+            const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kBN);
 #pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
-            float v[32];
-            if (have) tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            else {
+            for (int c0 = 0; c0 < kBN; c0 += 32) {
+                float v[32];
+                if (have) tmem_ld32(acc + (uint32_t)c0, v);
+                else {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = 0.f;
-            }
-            if (!row_ok || (nk > 0 && !have)) continue;
-            // All loads of the chunk are issued before any store (the stores
-            // could alias the loads as far as the compiler knows).
-            float cv[32];
-            float *prow = a.C + i * a.crs + (n0 + c0) * a.ccs;
-            const int64_t jmax = (a.cmode == MASK_LOWER && i < a.N - 1) ? i : a.N - 1;
-            const int cnt = (int)(jmax - (n0 + c0) + 1 < 32 ? jmax - (n0 + c0) + 1 : 32);
-            if (a.beta != 0.f) {
+                    for (int q = 0; q < 32; ++q) v[q] = 0.f;
+                }
+                if (!row_ok) continue;
+                // All loads of the chunk are issued before any store (the stores
+                // could alias the loads as far as the compiler knows).
+                float cv[32];
+                float *prow = a.C + i * a.crs + (n0 + c0) * a.ccs;
+                const int64_t jmax = (a.cmode == MASK_LOWER && i < a.N - 1) ? i : a.N - 1;
+                const int cnt = (int)(jmax - (n0 + c0) + 1 < 32 ? jmax - (n0 + c0) + 1 : 32);
+                if (a.beta != 0.f) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
-            }
+                    for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
+                }
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                if (q >= cnt) continue;
-                float out = a.alpha * v[q];
-                if (a.beta != 0.f) out = fmaf(a.beta, cv[q], out);
-                prow[q * a.ccs] = out;
+                for (int q = 0; q < 32; ++q) {
+                    if (q >= cnt) continue;
+                    float out = a.alpha * v[q];
+                    if (a.beta != 0.f) out = fmaf(a.beta, cv[q], out);
+                    prow[q * a.ccs] = out;
+                }
             }
+            // this warp's lanes of the accumulator are read: hand it back
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
         }
     }
     fence_before();
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kBN)
                      : "memory");
     }
 }
@@ -378,7 +442,10 @@ cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows,
     args.tiles_n = (int)tiles_n;
     args.lower_tiles = (cmode == MASK_LOWER && M == N) ? 1 : 0;
     args.err = err;
-    const int64_t grid = args.lower_tiles ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+    args.num_tiles = args.lower_tiles ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+    // one CTA per SM (shared memory and TMEM fit one), never more than tiles
+    const int64_t sms = device_sm_count();
+    const int64_t grid = args.num_tiles < sms ? args.num_tiles : sms;
     if (kind == 0) {
         e = cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;

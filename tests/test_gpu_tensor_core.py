@@ -63,6 +63,21 @@ def test_tc_syrk_tf32(n, k):
     np.testing.assert_array_equal(C[~low], Cin[~low])
 
 
+@pytest.mark.parametrize("n,k,prec", [(4000, 96, 0), (2600, 64, 1), (3001, 200, 0)])
+def test_tc_syrk_several_tiles_per_cta(n, k, prec):
+    """More lower-triangular 128 x 128 tiles than SMs: every CTA of the
+    persistent kernel walks several tiles, alternating its two accumulators
+    (their barriers go through several phases), with ragged edge tiles."""
+    p = rfp.RFP_PREC_BF16 if prec == 0 else rfp.RFP_PREC_TF32
+    C, Cin, ref, mag, err = _case(n, k, p, seed=n)
+    assert err == 0
+    low = np.tril(np.ones((n, n), bool))
+    rel = 4 * 2.0 ** -10 if p == rfp.RFP_PREC_TF32 else 0.0
+    tol = (rel + 4 * k * 2.0 ** -23) * mag + 4 * 2.0 ** -23 * np.abs(ref)
+    assert not np.any((np.abs(C - ref) > tol) & low), np.max(np.abs(C - ref)[low])
+    np.testing.assert_array_equal(C[~low], Cin[~low])
+
+
 def test_tc_syrk_beta_zero_ignores_c():
     n, k = 160, 96
     g = torch.Generator().manual_seed(3)
