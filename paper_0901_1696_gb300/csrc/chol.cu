@@ -168,8 +168,23 @@ cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     RFP_TRY(potrf_blocked(st, t1, L.n1, info, 0));
     stage_mark(st, "pftrf.potrf_t1");
     if (L.n2 > 0 && L.n1 > 0) {
-        // step 2: L21 L11^T = A21
-        RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
+        // step 2: L21 L11^T = A21, i.e. L11 L21^T = A21^T: in FP64 one launch
+        // of the block substitution with T1 and the n2 columns of S^T
+        // (rfp_solve.cu); the multi-launch form when no scratch can be had.
+        bool done = false;
+        if constexpr (sizeof(T) == 8) {
+            int32_t *sync = nullptr;
+            if (solve_scratch_acquire(st, rfp_solve_sync_words(L.n2), &sync) == cudaSuccess) {
+                const cudaError_t e = rfp_solve(st, t1, s, t2, L.n1, 0, s.t(), L.n2, false, sync, info);
+                const cudaError_t e2 = solve_scratch_release(st, sync);
+                RFP_TRY(e);
+                RFP_TRY(e2);
+                done = true;
+            } else {
+                (void)cudaGetLastError();   // the failed scratch request is not the caller's error
+            }
+        }
+        if (!done) RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
         stage_mark(st, "pftrf.trsm_s");
         // step 3: A22 <- A22 - L21 L21^T (lower triangle of T2)
         RFP_TRY(gemm_nt(st, t2, s, s, L.n2, L.n2, L.n1, T(-1), T(1), MASK_LOWER, MASK_NONE,
@@ -197,9 +212,9 @@ cudaError_t pftrs_impl(cudaStream_t st, const Layout &L, const T *arf_c, T *Bp, 
         // capture).
         int32_t *sync = nullptr;
         if (solve_scratch_acquire(st, rfp_solve_sync_words(nrhs), &sync) == cudaSuccess) {
-            cudaError_t e = rfp_solve(st, t1, s, t2, L.n1, L.n2, Bp, ldb, nrhs, false, sync);
+            cudaError_t e = rfp_solve(st, t1, s, t2, L.n1, L.n2, B, nrhs, false, sync);
             stage_mark(st, "pftrs.forward");
-            if (e == cudaSuccess) e = rfp_solve(st, t1, s, t2, L.n1, L.n2, Bp, ldb, nrhs, true, sync);
+            if (e == cudaSuccess) e = rfp_solve(st, t1, s, t2, L.n1, L.n2, B, nrhs, true, sync);
             stage_mark(st, "pftrs.backward");
             const cudaError_t e2 = solve_scratch_release(st, sync);
             return e != cudaSuccess ? e : e2;

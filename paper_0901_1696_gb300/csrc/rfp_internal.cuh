@@ -221,15 +221,18 @@ cudaError_t trsm_wavefront(cudaStream_t st, View<float> Lv, int64_t n, const flo
                            int64_t ldx, int64_t nrhs, bool trans, int32_t *sync, int32_t *err,
                            const int32_t *stop);
 
-// One-launch FP64 block substitution with the whole logical lower factor
+// One-launch FP64 block substitution with a logical lower factor
 // (rfp_solve.cu): L Y = X (trans = false) or L^T Y = X (trans = true) in
-// place on X (n x nrhs, column-major, ldx), n = n1 + n2, L given by its three
-// RFP block views.  sync: device scratch of rfp_solve_sync_words(nrhs) int32
-// (cleared by the call, stream-ordered).  If a wait between tasks expires
-// (2 s), the blocks of X not computed are set to NaN.
+// place on X (n x nrhs, any strides), n = n1 + n2, L = [T1 0; S T2] given by
+// its RFP block views (n2 = 0: L is T1 alone).  sync: device scratch of
+// rfp_solve_sync_words(nrhs) int32 (cleared by the call, stream-ordered).
+// abort: if non-null and non-zero when the launch starts, nothing is done.
+// If a wait between tasks expires (2 s), the blocks of X not computed are
+// set to NaN.
 size_t rfp_solve_sync_words(int64_t nrhs);
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
-                      int64_t n2, double *X, int64_t ldx, int64_t nrhs, bool trans, int32_t *sync);
+                      int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
+                      const int32_t *abort = nullptr);
 // Stream-ordered scratch for the sync words, from a library-private memory
 // pool.  cudaErrorNotSupported while `st` is being captured into a graph.
 cudaError_t solve_scratch_acquire(cudaStream_t st, size_t words, int32_t **out);

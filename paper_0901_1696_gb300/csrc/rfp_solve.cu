@@ -50,10 +50,11 @@ struct SolveArgs {
     View<double> t1, s, t2;
     int64_t n1, n2;
     int nb1, nb;                    // row blocks in T1, in total
-    double *X;
-    int64_t ldx, nrhs;
+    View<double> X;                 // n x nrhs, any strides
+    int64_t nrhs;
     int ng;
     int32_t *counter, *prog, *err;
+    const int32_t *abort;           // if set (non-zero) at launch, nothing is done
 };
 
 __device__ __forceinline__ uint64_t rs_globaltimer()
@@ -103,13 +104,15 @@ __device__ __forceinline__ bool wait_progress(const int32_t *prog, int need, int
 
 // Staging of one 64 x 16 chunk of op(L_jb) (rows r < rv of the task's block,
 // k in [k0, k0 + 16) < kv) and of the matching 16 x 16 chunk of X_j.
-// A(r, k) = V(r, k) for a view V; the loader reads along V's unit stride.
+// A(r, k) = V(r, k) for a view V; both loaders read along their view's unit
+// stride (X's rows for a right-hand-side block, its columns for a
+// transposed RFP block).
 struct ChunkRegs {
     double a[kR * kKc / kThreads];   // 8
     double x[kKc * kG / kThreads];   // 2
 
-    __device__ __forceinline__ void load(View<double> V, int rv, int k0, int kv, const double *Xj,
-                                         int64_t ldx, int cols)
+    __device__ __forceinline__ void load(View<double> V, int rv, int k0, int kv, View<double> Xj,
+                                         int cols)
     {
         const int tid = threadIdx.x;
         if (V.rs == 1) {      // rows contiguous
@@ -125,14 +128,22 @@ struct ChunkRegs {
                 a[q] = (r < rv && k < kv) ? __ldg(&V.p[(int64_t)r * V.rs + k * V.cs]) : 0.0;
             }
         }
+        if (Xj.rs == 1) {     // X rows contiguous
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int k = k0 + tid % kKc, c = tid / kKc + 8 * q;
-            x[q] = (k < kv && c < cols) ? __ldcg(Xj + (int64_t)c * ldx + k) : 0.0;
+            for (int q = 0; q < 2; ++q) {
+                const int k = k0 + tid % kKc, c = tid / kKc + 8 * q;
+                x[q] = (k < kv && c < cols) ? __ldcg(&Xj(k, c)) : 0.0;
+            }
+        } else {              // X columns contiguous
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c = tid % kG, k = k0 + tid / kG + 8 * q;
+                x[q] = (k < kv && c < cols) ? __ldcg(&Xj(k, c)) : 0.0;
+            }
         }
     }
-    __device__ __forceinline__ void store(const View<double> &V, double (*As)[kAsLd],
-                                          double (*Xs)[kXsLd]) const
+    __device__ __forceinline__ void store(const View<double> &V, bool xrowfast,
+                                          double (*As)[kAsLd], double (*Xs)[kXsLd]) const
     {
         const int tid = threadIdx.x;
         if (V.rs == 1) {
@@ -142,8 +153,13 @@ struct ChunkRegs {
 #pragma unroll
             for (int q = 0; q < 8; ++q) As[tid % kKc][tid / kKc + 8 * q] = a[q];
         }
+        if (xrowfast) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) Xs[tid % kKc][tid / kKc + 8 * q] = x[q];
+            for (int q = 0; q < 2; ++q) Xs[tid % kKc][tid / kKc + 8 * q] = x[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) Xs[tid / kG + 8 * q][tid % kG] = x[q];
+        }
     }
 };
 
@@ -168,6 +184,9 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     __shared__ int s_ticket, s_ok;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // The abort word is written before this launch and not during it, so
+    // every CTA sees the same value and none is left waiting.
+    if (a.abort && *a.abort) return;
     if (tid == 0) s_ticket = atomicAdd(a.counter, 1);
     __syncthreads();
     const int ticket = s_ticket;
@@ -178,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     block_rows(a, b, r0, rows);
     const int64_t c0 = (int64_t)g * kG;
     const int cols = (int)(a.nrhs - c0 < kG ? a.nrhs - c0 : kG);
-    double *Xb = a.X + r0 + c0 * a.ldx;
+    const View<double> Xb = a.X.sub(r0, c0);
     int32_t *prog = a.prog + g;
 
     const int tx = tid % 8, ty = tid / 8;                    // 2 columns x 4 rows each
@@ -188,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int r = ty * 4 + m, cc = tx * 2 + c;
-            acc[m][c] = (r < rows && cc < cols) ? __ldcg(Xb + (int64_t)cc * a.ldx + r) : 0.0;
+            acc[m][c] = (r < rows && cc < cols) ? __ldcg(&Xb(r, cc)) : 0.0;
         }
 
     bool ok = true;
@@ -211,15 +230,15 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
         // op(L) for this task: forward A = L_bj (rows b, k over j);
         // backward A = L_jb^T (rows b, k over j).
         const View<double> V = TRANS ? lblock(a, j, b).t() : lblock(a, b, j);
-        const double *Xj = a.X + j0 + c0 * a.ldx;
+        const View<double> Xj = a.X.sub(j0, c0);
         const int nch = (kv + kKc - 1) / kKc;
         ChunkRegs st;
-        st.load(V, rows, 0, kv, Xj, a.ldx, cols);
+        st.load(V, rows, 0, kv, Xj, cols);
         for (int ch = 0; ch < nch; ++ch) {
             const int buf = ch & 1;
-            st.store(V, sm.u.As[buf], sm.u.Xs[buf]);
+            st.store(V, Xj.rs == 1, sm.u.As[buf], sm.u.Xs[buf]);
             __syncthreads();
-            if (ch + 1 < nch) st.load(V, rows, (ch + 1) * kKc, kv, Xj, a.ldx, cols);
+            if (ch + 1 < nch) st.load(V, rows, (ch + 1) * kKc, kv, Xj, cols);
 #pragma unroll
             for (int kk = 0; kk < kKc; ++kk) {
                 const double2 a01 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * 4]);
@@ -243,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int r = ty * 4 + m, cc = tx * 2 + c;
-                if (r < rows && cc < cols) Xb[(int64_t)cc * a.ldx + r] = __longlong_as_double(0x7ff8000000000000ll);
+                if (r < rows && cc < cols) Xb(r, cc) = __longlong_as_double(0x7ff8000000000000ll);
             }
         return;
     }
@@ -304,14 +323,28 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
             }
         }
     }
+    if (Xb.rs == 1) {      // lanes along X's rows: coalesced as held
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int cc = warp * 4 + c;
-        if (cc >= cols) continue;
+        for (int c = 0; c < 4; ++c) {
+            const int cc = warp * 4 + c;
+            if (cc >= cols) continue;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = lane + 32 * h;
-            if (r < rows) Xb[(int64_t)cc * a.ldx + r] = v[h][c];
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r < rows) Xb(r, cc) = v[h][c];
+            }
+        }
+    } else {               // X's columns contiguous: regroup through shared memory
+        __syncthreads();   // every lane is done reading Bs
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) sm.d.Bs[lane + 32 * h][warp * 4 + c] = v[h][c];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kR * kG / kThreads; ++q) {
+            const int cc = tid % kG, r = tid / kG + (kThreads / kG) * q;
+            if (r < rows && cc < cols) Xb(r, cc) = sm.d.Bs[r][cc];
         }
     }
     __threadfence();
@@ -327,7 +360,8 @@ size_t rfp_solve_sync_words(int64_t nrhs)
 }
 
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
-                      int64_t n2, double *X, int64_t ldx, int64_t nrhs, bool trans, int32_t *sync)
+                      int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
+                      const int32_t *abort)
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
@@ -338,8 +372,8 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
     // column group; all start at zero.
     cudaError_t e = cudaMemsetAsync(sync, 0, rfp_solve_sync_words(nrhs) * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, ldx, nrhs, (int)ng,
-                sync, sync + 2, sync + 1};
+    SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, nrhs, (int)ng,
+                sync, sync + 2, sync + 1, abort};
     if (trans) rfp_solve_kernel<true><<<(unsigned)tasks, kThreads, 0, st>>>(a);
     else rfp_solve_kernel<false><<<(unsigned)tasks, kThreads, 0, st>>>(a);
     note_launch();

@@ -388,7 +388,8 @@ cudaError_t trsm_wavefront(cudaStream_t, View<float> Lv, int64_t n, const float 
 size_t rfp_solve_sync_words(int64_t nrhs) { return (size_t)(2 + (nrhs + 15) / 16); }
 
 cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double> t2, int64_t n1,
-                      int64_t n2, double *X, int64_t ldx, int64_t nrhs, bool trans, int32_t *sync)
+                      int64_t n2, View<double> Xv, int64_t nrhs, bool trans, int32_t *sync,
+                      const int32_t *abort)
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
@@ -396,6 +397,8 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
     Launch L;
     L.ordered = true;
     for (size_t w = 0; w < rfp_solve_sync_words(nrhs); ++w) L.wr(sync + w, 0);   // the memset
+    if (aborted(L, abort)) return L.commit();
+    auto xat = [&](int64_t r, int64_t c) { return &Xv(r, c); };
     auto rows_of = [&](int64_t b, int64_t &r0, int64_t &rows) {
         if (b < nb1) { r0 = b * R; rows = std::min(R, n1 - r0); }
         else { const int64_t lr = (b - nb1) * R; r0 = n1 + lr; rows = std::min(R, n2 - lr); }
@@ -418,7 +421,7 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
         const int64_t c0 = g * 16, cols = std::min<int64_t>(16, nrhs - c0);
         std::vector<double> acc(rows * cols);
         for (int64_t c = 0; c < cols; ++c)
-            for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = L.rd(&X[(c0 + c) * ldx + r0 + r]);
+            for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = L.rd(xat(r0 + r, c0 + c));
         for (int64_t q = 0; q < p; ++q) {
             const int64_t j = trans ? nb - 1 - q : q;
             if (L.rd(prog + g) < q + 1) violation("X block read before its group's progress", prog + g);
@@ -429,7 +432,7 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
                     double sum = acc[c * rows + r];
                     for (int64_t k = 0; k < kv; ++k) {
                         const double a = trans ? L.rd(lel(j, b, k, r)) : L.rd(lel(b, j, r, k));
-                        sum -= a * L.rd(&X[(c0 + c) * ldx + j0 + k]);
+                        sum -= a * L.rd(xat(j0 + k, c0 + c));
                     }
                     acc[c * rows + r] = sum;
                 }
@@ -447,7 +450,7 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
                     for (int64_t r = 0; r < j; ++r) v[r] -= L.rd(lel(b, b, j, r)) * v[j];
                 }
             }
-            for (int64_t r = 0; r < rows; ++r) L.wr(&X[(c0 + c) * ldx + r0 + r], v[r]);
+            for (int64_t r = 0; r < rows; ++r) L.wr(xat(r0 + r, c0 + c), v[r]);
         }
         L.wr(prog + g, (int32_t)(p + 1));
     }
