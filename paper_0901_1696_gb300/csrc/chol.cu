@@ -34,6 +34,22 @@ template <typename T>
 cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info,
                                  int64_t base)
 {
+    if constexpr (sizeof(T) == 8) {
+        // FP64: panel 0 as below, then one lookahead launch per panel step
+        // (potrf_step.cu); the multi-launch form when no scratch can be had.
+        int32_t *sync = nullptr;
+        if (m > kNb && solve_scratch_acquire(st, potrf_step_sync_words(m), &sync) == cudaSuccess) {
+            cudaError_t e = cudaMemsetAsync(sync, 0, potrf_step_sync_words(m) * sizeof(int32_t), st);
+            if (e == cudaSuccess) e = potrf_tile(st, V, (int)kNb, info, base);
+            if (e == cudaSuccess)
+                e = trsm_strip(st, V.sub(kNb, 0), V, m - kNb, (int)kNb, 1, T(1), info);
+            for (int64_t k0 = 0; e == cudaSuccess && k0 + kNb < m; k0 += kNb)
+                e = potrf_step(st, V, m, k0, info, base, sync + 2 * (k0 / kNb));
+            const cudaError_t e2 = solve_scratch_release(st, sync);
+            return e != cudaSuccess ? e : e2;
+        }
+        if (m > kNb) (void)cudaGetLastError();   // the failed scratch request is not the caller's error
+    }
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
         RFP_TRY(potrf_tile(st, V.sub(k0, k0), (int)w, info, base + k0));

@@ -1,0 +1,306 @@
+// FP64 Cholesky of one RFP triangle (PFTRF steps 1 and 4, Section 3) with a
+// one-panel lookahead, one launch per panel step.
+//
+// Right-looking blocked Cholesky of the m x m lower triangle V with 64-wide
+// panels: after panel k (columns [k0, k1)) is factored, the trailing matrix
+// A(k1:m, k1:m) receives -= L(:, k0:k1) L(:, k0:k1)^T, and panel k+1
+// (columns [k1, k2)) is then factored: POTRF of its diagonal tile, and the
+// rows below solved against that tile (TRSM).  Launch k does all of this:
+//   ticket 0             the diagonal tile of panel k+1: its update, then
+//                        POTRF in shared memory; writes L and raises a flag;
+//   tickets 1 .. P       64-row strips of panel k+1 below the diagonal: the
+//                        update, then (once the flag is up) the solve
+//                        X L_D^T = strip with the new diagonal tile;
+//   the other tickets    64 x 64 lower tiles of A(k2:m, k2:m): the update.
+// The strips wait only on ticket 0, which is running whenever they hold a
+// ticket, so every wait ends; each wait is also bounded in time (2 s).  The
+// diagonal chain of the factorization (tile POTRF, strip solve) thus runs
+// beside the bulk of the trailing update instead of between launches.  No
+// element is written by one CTA and read by another except the diagonal
+// tile, which is read only after its flag.
+#include "rfp_internal.cuh"
+
+namespace rfp {
+
+namespace {
+
+constexpr int kT = 64;              // tile / panel width
+constexpr int kTh = 256;            // threads per CTA
+constexpr int kBk = 16;             // K step of the tile update
+constexpr int kSLd = kT + 2;        // staging rows (doubles; 16-byte aligned)
+constexpr int kTLd = kT + 1;        // factor / solve tiles
+constexpr uint64_t kStepWaitNs = 2000000000ull;
+
+struct StepArgs {
+    View<double> V;                 // the m x m lower triangle
+    int64_t m, k0, k1, k2;          // panel k = [k0, k1), panel k+1 = [k1, k2)
+    int nstrip;                     // 64-row strips of panel k+1 in rows [k2, m)
+    int64_t nbulk;                  // lower 64 x 64 tiles of A(k2:m, k2:m)
+    int32_t *info;                  // failure index (1-based, global); also the abort word
+    int64_t base;                   // global index of V's first row
+    int32_t *sync;                  // [0] ticket counter, [1] diagonal flag (1 ok, 2 failed)
+};
+
+struct Smem {
+    double As[2][kBk][kSLd];        // staged panel rows of the C tile
+    double Bs[2][kBk][kSLd];        // staged panel rows of the C tile's columns
+    double T[kT][kTLd];             // updated tile (diagonal / strip)
+    double Ld[kT][kTLd];            // new diagonal factor tile (strips)
+    double rinv[kT], sq[kT];
+    int ticket, flag;
+};
+
+__device__ __forceinline__ uint64_t step_globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// acc(64 x 64, 4 x 4 per thread) = P_rows(64 x w) P_cols(64 x w)^T with
+// P_rows(i, k) = V(r0 + i, k0 + k) for i < nr (zero beyond), likewise
+// P_cols with c0 / nc.  w <= 64.  Register-staged, double-buffered K steps
+// of 16 read along V's unit stride.
+__device__ __forceinline__ void panel_product(const StepArgs &a, Smem &sm, int64_t r0, int nr,
+                                              int64_t c0, int nc, int w, double (&acc)[4][4])
+{
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const bool rowfast = a.V.rs == 1;
+    const View<double> Pr = a.V.sub(r0, a.k0), Pc = a.V.sub(c0, a.k0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    double ra[4], rb[4];
+    auto load = [&](int kb) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i, k;
+            if (rowfast) { i = tid % kT; k = kb + tid / kT + 4 * q; }
+            else { k = kb + tid % kBk; i = tid / kBk + 16 * q; }
+            ra[q] = (i < nr && k < w) ? Pr(i, k) : 0.0;
+            rb[q] = (i < nc && k < w) ? Pc(i, k) : 0.0;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i, k;
+            if (rowfast) { i = tid % kT; k = tid / kT + 4 * q; }
+            else { k = tid % kBk; i = tid / kBk + 16 * q; }
+            sm.As[buf][k][i] = ra[q];
+            sm.Bs[buf][k][i] = rb[q];
+        }
+    };
+    const int nsteps = (w + kBk - 1) / kBk;
+    load(0);
+    for (int s = 0; s < nsteps; ++s) {
+        const int buf = s & 1;
+        store(buf);
+        __syncthreads();
+        if (s + 1 < nsteps) load((s + 1) * kBk);
+#pragma unroll
+        for (int kk = 0; kk < kBk; ++kk) {
+            const double2 a01 = *reinterpret_cast<const double2 *>(&sm.As[buf][kk][ty * 4]);
+            const double2 a23 = *reinterpret_cast<const double2 *>(&sm.As[buf][kk][ty * 4 + 2]);
+            const double2 b01 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][tx * 4]);
+            const double2 b23 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][tx * 4 + 2]);
+            const double av[4] = {a01.x, a01.y, a23.x, a23.y}, bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+    }
+    __syncthreads();   // staging buffers free for the next product
+}
+
+// T = V(r0.., c0..) - acc for the nr x nc tile (lower part only when `lower`),
+// into shared memory; entries outside are zero.
+__device__ __forceinline__ void updated_tile_to_smem(const StepArgs &a, Smem &sm, int64_t r0, int nr,
+                                                     int64_t c0, int nc, bool lower,
+                                                     const double (&acc)[4][4])
+{
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = ty * 4 + i, c = tx * 4 + j;
+            const bool in = r < nr && c < nc && (!lower || c <= r);
+            sm.T[r][c] = in ? a.V(r0 + r, c0 + c) - acc[i][j] : 0.0;
+        }
+}
+
+__global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char step_smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(step_smem_raw);
+    if (*a.info != 0) return;   // an earlier panel failed (written before this launch)
+    const int tid = threadIdx.x;
+    if (tid == 0) sm.ticket = atomicAdd(a.sync, 1);
+    __syncthreads();
+    const int64_t t = sm.ticket;
+    const int w = (int)(a.k1 - a.k0);            // panel k width
+    const int wn = (int)(a.k2 - a.k1);           // panel k+1 width
+    double acc[4][4];
+    int32_t *flag = a.sync + 1;
+
+    if (t == 0) {
+        // ---- diagonal tile of panel k+1: update, then unblocked Cholesky
+        panel_product(a, sm, a.k1, wn, a.k1, wn, w, acc);
+        updated_tile_to_smem(a, sm, a.k1, wn, a.k1, wn, true, acc);
+        __syncthreads();
+        const int tx = tid % 16, ty = tid / 16;
+        int fail = -1;
+        for (int j = 0; j < wn; ++j) {
+            if (tid == 0) {
+                const double d = sm.T[j][j];
+                sm.flag = (d > 0.0) ? -1 : j;            // pivot <= 0 or NaN fails
+                const double r = sqrt(d);
+                sm.sq[j] = r;
+                sm.rinv[j] = 1.0 / r;
+            }
+            __syncthreads();
+            if (sm.flag >= 0) { fail = sm.flag; break; }
+            const double ri = sm.rinv[j];
+            for (int i = j + 1 + tid; i < wn; i += kTh) sm.T[i][j] *= ri;
+            __syncthreads();
+            for (int i = j + 1 + ty; i < wn; i += 16) {
+                const double lij = sm.T[i][j];
+                for (int k = j + 1 + tx; k <= i; k += 16) sm.T[i][k] -= lij * sm.T[k][j];
+            }
+            __syncthreads();
+        }
+        if (fail >= 0) {
+            if (tid == 0) {
+                atomicCAS(a.info, 0, (int32_t)(a.base + a.k1 + fail + 1));
+                __threadfence();
+                atomicExch(flag, 2);
+            }
+            return;
+        }
+        for (int e = tid; e < kT * kT; e += kTh) {
+            const int u = e % kT, v = e / kT;
+            const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;   // along the unit stride
+            if (i < wn && j <= i) a.V(a.k1 + i, a.k1 + j) = (i == j) ? sm.sq[j] : sm.T[i][j];
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(flag, 1);
+        return;
+    }
+
+    if (t <= a.nstrip) {
+        // ---- a 64-row strip of panel k+1: update, wait for the diagonal tile, solve
+        const int64_t r0 = a.k2 + (t - 1) * kT;
+        const int nr = (int)(a.m - r0 < kT ? a.m - r0 : kT);
+        panel_product(a, sm, r0, nr, a.k1, wn, w, acc);
+        updated_tile_to_smem(a, sm, r0, nr, a.k1, wn, false, acc);
+        if (tid == 0) {
+            const uint64_t t0 = step_globaltimer();
+            int f = 0;
+            for (uint32_t it = 0;; ++it) {
+                f = *(volatile int32_t *)flag;
+                if (f != 0) break;
+                __nanosleep(64);
+                if ((it & 63) == 63 && step_globaltimer() - t0 > kStepWaitNs) break;
+            }
+            __threadfence();
+            sm.flag = f;
+        }
+        __syncthreads();
+        if (sm.flag != 1) {
+            // The diagonal tile failed (info is set) or never came: the strip is
+            // left as NaN so that the failure cannot pass unnoticed.
+            if (sm.flag == 0)
+                for (int e = tid; e < kT * kT; e += kTh) {
+                    const int u = e % kT, v = e / kT;
+                    const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
+                    if (i < nr && j < wn) a.V(r0 + i, a.k1 + j) = __longlong_as_double(0x7ff8000000000000ll);
+                }
+            return;
+        }
+        // the new diagonal factor tile, from L2 (another SM wrote it in this launch)
+        for (int e = tid; e < kT * kT; e += kTh) {
+            const int u = e % kT, v = e / kT;
+            const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
+            if (i < wn && j <= i) sm.Ld[i][j] = __ldcg(&a.V(a.k1 + i, a.k1 + j));
+        }
+        __syncthreads();
+        if (tid < wn) sm.rinv[tid] = 1.0 / sm.Ld[tid][tid];
+        __syncthreads();
+        // X L_D^T = T, columns in increasing order; rows are independent
+        const int row = tid % kT, grp = tid / kT;
+        double *xr = sm.T[row];
+        for (int j = 0; j < wn; ++j) {
+            if (grp == 0) xr[j] *= sm.rinv[j];
+            __syncthreads();
+            const double xj = xr[j];
+            for (int c = j + 1 + grp; c < wn; c += 4) xr[c] -= xj * sm.Ld[c][j];
+            __syncthreads();
+        }
+        for (int e = tid; e < kT * kT; e += kTh) {
+            const int u = e % kT, v = e / kT;
+            const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
+            if (i < nr && j < wn) a.V(r0 + i, a.k1 + j) = sm.T[i][j];
+        }
+        return;
+    }
+
+    // ---- a lower 64 x 64 tile of A(k2:m, k2:m): the update only
+    const int64_t b = t - 1 - a.nstrip;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= b) ++ti;
+    while (ti * (ti + 1) / 2 > b) --ti;
+    const int64_t tj = b - ti * (ti + 1) / 2;
+    const int64_t r0 = a.k2 + ti * kT, c0 = a.k2 + tj * kT;
+    const int nr = (int)(a.m - r0 < kT ? a.m - r0 : kT), nc = (int)(a.m - c0 < kT ? a.m - c0 : kT);
+    panel_product(a, sm, r0, nr, c0, nc, w, acc);
+    const int tx = tid % 16, ty = tid / 16;
+    double cin[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = ty * 4 + i, c = tx * 4 + j;
+            const bool in = r < nr && c < nc && (ti != tj || c <= r);
+            cin[i][j] = in ? a.V(r0 + r, c0 + c) : 0.0;
+        }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = ty * 4 + i, c = tx * 4 + j;
+            if (r < nr && c < nc && (ti != tj || c <= r)) a.V(r0 + r, c0 + c) = cin[i][j] - acc[i][j];
+        }
+}
+
+}  // namespace
+
+size_t potrf_step_sync_words(int64_t m)
+{
+    const int64_t np = (m + kT - 1) / kT;
+    return (size_t)(2 * (np > 1 ? np - 1 : 1));
+}
+
+cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, int32_t *info,
+                       int64_t base, int32_t *sync)
+{
+    const int64_t k1 = k0 + kT < m ? k0 + kT : m;
+    if (k1 >= m) return cudaSuccess;                  // no next panel
+    const int64_t k2 = k1 + kT < m ? k1 + kT : m;
+    const int64_t rest = (m - k2 + kT - 1) / kT;      // row tiles of A(k2:m, k2:m)
+    StepArgs a{V, m, k0, k1, k2, (int)rest, rest * (rest + 1) / 2, info, base, sync};
+    const int64_t grid = 1 + a.nstrip + a.nbulk;
+    if (grid > INT32_MAX) return cudaErrorInvalidValue;
+    const int smem = (int)sizeof(Smem);
+    cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    potrf_step_kernel<<<(unsigned)grid, kTh, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace rfp

@@ -233,6 +233,16 @@ size_t rfp_solve_sync_words(int64_t nrhs);
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
                       const int32_t *abort = nullptr);
+// One panel step of the FP64 lookahead Cholesky of an m x m lower triangle V
+// (potrf_step.cu), panel k = [k0, k0 + 64) already factored: the trailing
+// update with it, and the factorization of panel k + 1 (its diagonal tile
+// and the rows below), in one launch.  sync: 2 int32 per step, zero before
+// the launch (potrf_step_sync_words(m) for all steps of one factorization).
+// info as for potrf_tile (global index base + column + 1; the launch does
+// nothing if *info is already non-zero).
+size_t potrf_step_sync_words(int64_t m);
+cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, int32_t *info,
+                       int64_t base, int32_t *sync);
 // Stream-ordered scratch for the sync words, from a library-private memory
 // pool.  cudaErrorNotSupported while `st` is being captured into a graph.
 cudaError_t solve_scratch_acquire(cudaStream_t st, size_t words, int32_t **out);

@@ -457,6 +457,115 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
     return L.commit();
 }
 
+// potrf_step: one ordered launch (ticket order: the diagonal tile of panel
+// k+1, its 64-row strips, then the lower tiles of A(k2:m, k2:m)) with the
+// kernel's own tile decomposition.  Besides the bounds checks, every element
+// one task writes is recorded, and a read of it by another task is a
+// violation unless it is the new diagonal tile read by a strip (which the
+// kernel does only after the diagonal task's flag).
+size_t potrf_step_sync_words(int64_t m)
+{
+    const int64_t np = (m + 63) / 64;
+    return (size_t)(2 * (np > 1 ? np - 1 : 1));
+}
+
+cudaError_t potrf_step(cudaStream_t, View<double> V, int64_t m, int64_t k0, int32_t *info,
+                       int64_t base, int32_t *sync)
+{
+    const int64_t T = 64, k1 = std::min(k0 + T, m);
+    if (k1 >= m) return cudaSuccess;
+    const int64_t k2 = std::min(k1 + T, m), w = k1 - k0, wn = k2 - k1;
+    const int64_t rest = (m - k2 + T - 1) / T, nstrip = rest, nbulk = rest * (rest + 1) / 2;
+    Launch L;
+    L.ordered = true;
+    if (L.rd(info) != 0) return L.commit();
+    std::unordered_map<uintptr_t, int64_t> owner;
+    int64_t task = 0;
+    auto in_diag = [&](const double *p) {
+        for (int64_t i = 0; i < wn; ++i)
+            for (int64_t j = 0; j <= i; ++j)
+                if (p == &V(k1 + i, k1 + j)) return true;
+        return false;
+    };
+    auto rd = [&](const double *p) {
+        auto it = owner.find((uintptr_t)p);
+        if (it != owner.end() && it->second != task && !(it->second == 0 && task <= nstrip && in_diag(p)))
+            violation("potrf_step: element written by one task and read by another", p);
+        return L.rd(p);
+    };
+    auto wr = [&](double *p, double v) {
+        auto it = owner.find((uintptr_t)p);
+        if (it != owner.end() && it->second != task) violation("potrf_step: two tasks write one element", p);
+        owner[(uintptr_t)p] = task;
+        L.wr(p, v);
+    };
+    // P_rows P_cols^T over the panel columns [k0, k1)
+    auto prod = [&](int64_t r, int64_t c) {
+        double sum = 0.0;
+        for (int64_t k = 0; k < w; ++k) sum += rd(&V(r, k0 + k)) * rd(&V(c, k0 + k));
+        return sum;
+    };
+    int32_t flag = 0;
+    L.wr(sync, 1);                                   // ticket counter
+    {   // diagonal tile
+        task = 0;
+        std::vector<double> D(wn * wn, 0.0);
+        for (int64_t i = 0; i < wn; ++i)
+            for (int64_t j = 0; j <= i; ++j) D[i * wn + j] = rd(&V(k1 + i, k1 + j)) - prod(k1 + i, k1 + j);
+        int64_t fail = -1;
+        std::vector<double> sq(wn);
+        for (int64_t j = 0; j < wn && fail < 0; ++j) {
+            const double d = D[j * wn + j];
+            if (!(d > 0.0)) { fail = j; break; }
+            sq[j] = std::sqrt(d);
+            const double ri = 1.0 / sq[j];
+            for (int64_t i = j + 1; i < wn; ++i) D[i * wn + j] *= ri;
+            for (int64_t i = j + 1; i < wn; ++i)
+                for (int64_t k = j + 1; k <= i; ++k) D[i * wn + k] -= D[i * wn + j] * D[k * wn + j];
+        }
+        if (fail >= 0) {
+            if (L.rd(info) == 0) L.wr(info, (int32_t)(base + k1 + fail + 1));
+            flag = 2;
+        } else {
+            for (int64_t i = 0; i < wn; ++i)
+                for (int64_t j = 0; j <= i; ++j) wr(&V(k1 + i, k1 + j), i == j ? sq[j] : D[i * wn + j]);
+            flag = 1;
+        }
+        L.wr(sync + 1, flag);
+    }
+    for (int64_t s = 0; s < nstrip; ++s) {   // strips of panel k+1
+        task = 1 + s;
+        L.wr(sync, (int32_t)(task + 1));
+        const int64_t r0 = k2 + s * T, nr = std::min(T, m - r0);
+        std::vector<double> X(nr * wn);
+        for (int64_t i = 0; i < nr; ++i)
+            for (int64_t j = 0; j < wn; ++j) X[i * wn + j] = rd(&V(r0 + i, k1 + j)) - prod(r0 + i, k1 + j);
+        if (flag != 1) continue;
+        for (int64_t i = 0; i < nr; ++i) {
+            for (int64_t j = 0; j < wn; ++j) {
+                X[i * wn + j] *= 1.0 / rd(&V(k1 + j, k1 + j));
+                for (int64_t c = j + 1; c < wn; ++c) X[i * wn + c] -= X[i * wn + j] * rd(&V(k1 + c, k1 + j));
+            }
+            for (int64_t j = 0; j < wn; ++j) wr(&V(r0 + i, k1 + j), X[i * wn + j]);
+        }
+    }
+    for (int64_t b = 0; b < nbulk; ++b) {    // lower tiles of A(k2:m, k2:m)
+        task = 1 + nstrip + b;
+        L.wr(sync, (int32_t)(task + 1));
+        int64_t ti = 0;
+        while ((ti + 1) * (ti + 2) / 2 <= b) ++ti;
+        const int64_t tj = b - ti * (ti + 1) / 2;
+        const int64_t r0 = k2 + ti * T, c0 = k2 + tj * T;
+        const int64_t nr = std::min(T, m - r0), nc = std::min(T, m - c0);
+        for (int64_t i = 0; i < nr; ++i)
+            for (int64_t j = 0; j < nc; ++j) {
+                if (ti == tj && j > i) continue;
+                wr(&V(r0 + i, c0 + j), rd(&V(r0 + i, c0 + j)) - prod(r0 + i, c0 + j));
+            }
+    }
+    return L.commit();
+}
+
 // The emulated scratch: heap memory registered as a device buffer for the
 // duration of the call.
 cudaError_t solve_scratch_acquire(cudaStream_t, size_t words, int32_t **out)

@@ -71,7 +71,7 @@ def _full_from_factor(transr, uplo, n, arf):
     return np.tril(F) if uplo == "L" else np.triu(F).T
 
 
-SIZES = [1, 2, 3, 5, 63, 64, 65, 127, 128, 129, 200, 257]
+SIZES = [1, 2, 3, 5, 63, 64, 65, 127, 128, 129, 200, 257, 400]
 
 
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
@@ -141,7 +141,8 @@ def test_emulated_single_precision(emu, transr, uplo, n):
 
 
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
-@pytest.mark.parametrize("n,k", [(70, 3), (70, 40), (130, 64), (130, 100)])
+@pytest.mark.parametrize("n,k", [(70, 3), (70, 40), (130, 64), (130, 100), (300, 100), (300, 140),
+                                 (300, 260), (300, 200)])
 def test_emulated_info_on_failure(emu, transr, uplo, n, k):
     A, L0 = gen.spd_integer_factor(n, seed=5)
     A = A.copy()
