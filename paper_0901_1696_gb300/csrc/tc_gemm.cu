@@ -17,7 +17,10 @@
 //     and to hand each finished accumulator to the epilogue,
 //   * warps 0-3 read an accumulator with tcgen05.ld (one TMEM lane per
 //     thread = one C row), hand it back, and apply the masked epilogue to C;
-//     meanwhile the MMAs of the next tile fill the other accumulator.
+//     meanwhile the MMAs of the next tile fill the other accumulator.  When
+//     the C view allows it, the C tile is staged in shared memory by TMA
+//     (four 128 x 32 FP32 boxes), the next tile's as soon as the current one
+//     has been read, so the epilogue does not wait on scattered C loads.
 // Every mbarrier wait is bounded by time; on expiry the kernel records an
 // error code in *err and every role stops issuing work; the producer then
 // waits (bounded) for its copies in flight, the MMA issuer for its MMAs, and
@@ -39,7 +42,9 @@ constexpr int kRowBytes = 128;                    // one K slice per row (swizzl
 constexpr int kTileBytes = kBM * kRowBytes;       // 16 KB per operand per stage
 constexpr int kThreads = 192;                     // 4 epilogue warps + TMA warp + MMA warp
 constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s bound on any single wait
-constexpr int kSmemBytes = 1024 /*align*/ + 2 * kStages * kTileBytes + 256;   // + barriers, TMEM slot
+constexpr int kCBox = 32;                         // C columns per TMA box (128 rows x 32 FP32 = 16 KB)
+constexpr int kCBytes = kBM * kBN * 4;            // one C tile staged in shared memory (64 KB)
+constexpr int kSmemBytes = 1024 /*align*/ + 2 * kStages * kTileBytes + kCBytes + 256;   // + barriers, TMEM slot
 
 struct Args {
     float *C;
@@ -51,6 +56,7 @@ struct Args {
     int tiles_n;            // column tiles
     int lower_tiles;        // 1: the tile list is the lower-triangular tile set
     int64_t num_tiles;      // tiles in the list
+    int c_tma;              // 1: C tiles are staged in shared memory by TMA (tmC)
     int *err;
 };
 
@@ -118,6 +124,22 @@ __device__ __forceinline__ bool mbar_wait_quiet(uint64_t *bar, uint32_t parity)
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255) == 255 && globaltimer() - t0 > kWaitNs) return false;
     }
+}
+
+// AND of `p` over the 128 threads of the four epilogue warps (named
+// barrier 1); every one of them must reach it.
+__device__ __forceinline__ bool epilogue_all(bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.and.pred po, 1, 128, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -231,19 +253,21 @@ __device__ __forceinline__ void tile_coords(const Args &a, int64_t t, int64_t &t
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   Args a)
+                   const __grid_constant__ CUtensorMap tmC, Args a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~uintptr_t(1023));
     uint8_t *sA = base;
     uint8_t *sB = base + kStages * kTileBytes;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kStages * kTileBytes);
+    float *sC = reinterpret_cast<float *>(sB + kStages * kTileBytes);   // [kBN][kBM], rows fastest
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sC) + kCBytes);
     uint64_t *empty = full + kStages;
     uint64_t *accf = empty + kStages;     // [2] accumulator ready (MMA commit)
     uint64_t *acce = accf + 2;            // [2] accumulator drained (4 epilogue warps)
     uint64_t *drain = acce + 2;           // every MMA of this CTA completed
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *cfull = drain + 1;          // the staged C tile has landed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cfull + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int bk = kRowBytes / (KIND == 0 ? 2 : 4);                 // K elements per stage
@@ -266,6 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&acce[b], 4);
         }
         mbar_init(drain, 1);
+        mbar_init(cfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before();
@@ -322,22 +347,42 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_commit(drain);
         mbar_wait_quiet(drain, 0);
     } else if (warp < 4) {
-        // ---- epilogue: lane = row of the tile
-        int64_t lt = 0;
+        // ---- epilogue: lane = row of the tile.  With c_tma, thread 0 stages
+        // the C tile of the CTA's next tile in shared memory by TMA as soon
+        // as the current one has been read, so its load overlaps the wait for
+        // the accumulator.
+        const int etid = threadIdx.x;   // 0 .. 127
+        int64_t lt = 0, c_issued = 0;
+        auto issue_c = [&](int64_t t) {
+            int64_t tm, tn;
+            tile_coords(a, t, tm, tn);
+            mbar_expect_tx(cfull, kCBytes);
+#pragma unroll
+            for (int b = 0; b < kBN / kCBox; ++b)
+                tma_load_2d(sC + b * kCBox * kBM, &tmC, cfull, (int)(tm * kBM), (int)(tn * kBN) + b * kCBox);
+        };
+        if (a.c_tma && etid == 0 && blockIdx.x < ntiles) {
+            issue_c(blockIdx.x);
+            c_issued = 1;
+        }
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
             const int buf = (int)(lt & 1);
             const int64_t u = lt >> 1;
             int64_t tm, tn;
             tile_coords(a, t, tm, tn);
             const int64_t m0 = tm * kBM, n0 = tn * kBN;
-            // warp-uniform decision: tcgen05.ld is a .sync.aligned warp instruction
-            const bool have = __all_sync(0xffffffffu, nk > 0 &&
-                                                          mbar_wait(&accf[buf], (uint32_t)(u & 1), a.err, 3));
-            if (nk > 0 && !have) break;
+            // Both waits are bounded; whether to go on is then decided for all
+            // four epilogue warps at once (a barrier reduction they all reach),
+            // so that none is left at the named barrier below.
+            const bool acc_ok = nk == 0 || mbar_wait(&accf[buf], (uint32_t)(u & 1), a.err, 3);
+            const bool c_ok = !a.c_tma || mbar_wait(cfull, (uint32_t)(lt & 1), a.err, 3);
+            if (!epilogue_all(acc_ok && c_ok)) break;
+            const bool have = nk > 0;   // uniform: tcgen05.ld is a .sync.aligned warp instruction
             fence_after();
             const int64_t i = m0 + warp * 32 + lane;
             const bool row_ok = i < a.M;
             const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kBN);
+            const float *crow = sC + warp * 32 + lane;   // sC[j][row]
 #pragma unroll 1
             for (int c0 = 0; c0 < kBN; c0 += 32) {
                 float v[32];
@@ -347,15 +392,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int q = 0; q < 32; ++q) v[q] = 0.f;
                 }
                 if (!row_ok) continue;
-                // All loads of the chunk are issued before any store (the stores
-                // could alias the loads as far as the compiler knows).
                 float cv[32];
                 float *prow = a.C + i * a.crs + (n0 + c0) * a.ccs;
                 const int64_t jmax = (a.cmode == MASK_LOWER && i < a.N - 1) ? i : a.N - 1;
                 const int cnt = (int)(jmax - (n0 + c0) + 1 < 32 ? jmax - (n0 + c0) + 1 : 32);
                 if (a.beta != 0.f) {
+                    if (a.c_tma) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
+                        for (int q = 0; q < 32; ++q) cv[q] = crow[(c0 + q) * kBM];
+                    } else {
+                        // All loads of the chunk are issued before any store (the
+                        // stores could alias the loads as far as the compiler knows).
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
@@ -369,7 +419,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[buf]);
+            if (a.c_tma) {
+                // every epilogue thread is done with the staged C tile
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (etid == 0 && t + gridDim.x < ntiles) {
+                    issue_c(t + gridDim.x);
+                    ++c_issued;
+                }
+            }
         }
+        // a staged C load still in flight (a wait above gave up) lands before teardown
+        if (a.c_tma && etid == 0 && c_issued > lt) mbar_wait_quiet(cfull, (uint32_t)((c_issued - 1) & 1));
     }
     fence_before();
     __syncthreads();
@@ -418,6 +478,26 @@ cudaError_t make_map(CUtensorMap *map, const void *ptr, int kind, int64_t rows, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 2-D tensor map over the FP32 C view (rows contiguous): M x N, columns
+// `ld_elems` apart, box = 128 rows x kCBox columns, no swizzle, zero fill.
+// Returns false (and the caller keeps C in registers) when the view does not
+// meet TMA's rules: unit row stride, 16-byte aligned base and column stride.
+bool make_c_map(CUtensorMap *map, const float *C, int64_t rs, int64_t ld_elems, int64_t M, int64_t N)
+{
+    auto fn = encode_fn();
+    if (!fn || rs != 1 || (reinterpret_cast<uintptr_t>(C) % 16) || ((ld_elems * 4) % 16) || M <= 0 ||
+        N <= 0 || ld_elems < M)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld_elems * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)kBM, (cuuint32_t)kCBox};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(C), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 }  // namespace tc
 
 cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows, int64_t a_pitch_elems,
@@ -442,6 +522,8 @@ cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows,
     args.tiles_n = (int)tiles_n;
     args.lower_tiles = (cmode == MASK_LOWER && M == N) ? 1 : 0;
     args.err = err;
+    CUtensorMap mc = ma;   // unused unless C is staged by TMA
+    args.c_tma = (beta != 0.f && make_c_map(&mc, C.p, C.rs, C.cs, M, N)) ? 1 : 0;
     args.num_tiles = args.lower_tiles ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
     // one CTA per SM (shared memory and TMEM fit one), never more than tiles
     const int64_t sms = device_sm_count();
@@ -449,11 +531,11 @@ cudaError_t tc_gemm_nt(cudaStream_t st, int kind, const void *A, int64_t a_rows,
     if (kind == 0) {
         e = cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
-        tc_gemm_kernel<0><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(ma, mb, args);
+        tc_gemm_kernel<0><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(ma, mb, mc, args);
     } else {
         e = cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
-        tc_gemm_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(ma, mb, args);
+        tc_gemm_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(ma, mb, mc, args);
     }
     note_launch();
     return cudaGetLastError();
