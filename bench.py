@@ -859,7 +859,13 @@ def serve_leg(lib, dev, sat_requests, load_requests, pool_size, loads, resident_
         span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
         ok = [c["status"] == 0 for c in done]
         fp64 = modes[:count] == 0
+        # device concurrency from the per-request device stamps: the mean
+        # number of requests in progress on the GPU over the span of GPU work
+        iv = sorted((c["gpu_start_ms"], c["gpu_end_ms"]) for c in done if c["gpu_end_ms"] > 0)
+        gspan = (max(e for _, e in iv) - iv[0][0]) if iv else 0.0
+        conc = sum(e - b for b, e in iv) / gspan if gspan > 0 else 0.0
         return {"requests": count, "requests_per_s": count / span,
+                "mean_requests_in_progress_on_gpu": conc,
                 "solves_per_s": float(nrhs[:count].sum()) / span,
                 "span_s": span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),

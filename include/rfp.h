@@ -246,7 +246,8 @@ int rfp_dpfsv_mixed_noalloc(char transr, char uplo, int64_t n, int64_t nrhs, con
  *   n       order, 0 <= n <= 512
  *   arf     element offset of its RFP array (n(n+1)/2 elements) in arf
  *   b       element offset of its right-hand sides (column-major, ldb) in B
- *   nrhs    0 (factor only) to 8; ldb >= max(1, n) when nrhs > 0
+ *   nrhs    0 (factor only) to 32 (solved 8 columns per pass); ldb >= max(1, n)
+ *           when nrhs > 0
  *   transr, uplo   its layout ('N'/'T', 'L'/'U')
  *   nb      panel width 16, 24 or 32 (0 = 32), e.g. from the package's
  *           autotuner; a launch reserves shared memory for the plan's widest
@@ -358,13 +359,16 @@ int rfp_slansf(char norm, char transr, char uplo, int64_t n, const float *arf, f
  * GPU with continuous batching.  One scheduler thread admits requests, oldest
  * first, as soon as a stream slot and device memory are free, so requests
  * that arrive while others run overlap with them on the device:
- *   - FP64 factor+solve requests with n <= small_n and nrhs <= 8 whose factor
- *     is not resident go into one launch of the batched kernel
+ *   - factor+solve requests with n <= small_n and nrhs <= 32 whose factor is
+ *     not resident go into one launch of the batched kernel
  *     (rfp_dpfsv_batched) whenever one of its two streams is idle (every such
  *     request that arrived meanwhile joins that launch, up to batch_max);
  *   - every other request runs on its own stream (one of `streams`): FP64
  *     PFTRF + PFTRS, the mixed-precision solve (rfp_dpfsv_mixed with
  *     RFP_PREC_TF32X3), or PFTRI on a copy of a resident array.
+ * A mixed-mode request of order n <= small_n is served in FP64 (its array is
+ * held as an FP64 factor): the FP64 result meets the mixed mode's accuracy,
+ * and at these orders FP64 is at least as fast.
  * All device memory is one arena of arena_bytes allocated at creation.  The
  * RFP array of a request with key >= 0 stays resident after it completes
  * (FP64 mode: the factor; mixed mode: the FP64 matrix) and is reused by later
@@ -395,6 +399,11 @@ int rfp_slansf(char norm, char transr, char uplo, int64_t n, const float *arf, f
  * (mixed refinement did not converge), ECUDA.  Times are seconds on the host
  * clock since creation: submitted, started (enqueued on the GPU), done
  * (observed complete by a host callback after the result copies).
+ * gpu_start_ms / gpu_end_ms: device clock (CUDA events, ms since creation)
+ * at the start of the request's first GPU operation and the end of its last
+ * (for a batched request, its batch's); both 0 if it never reached the GPU.
+ * Two requests whose [gpu_start_ms, gpu_end_ms] intervals intersect were in
+ * progress on the device at the same time.
  * rfp_serve_destroy: finishes every submitted request, then frees everything.
  */
 #define RFP_SERVE_OP_FACTOR_SOLVE 0
@@ -425,6 +434,7 @@ typedef struct rfp_serve_completion {
     int64_t id;
     int32_t status, iterations, cache_hit, batched;
     double t_submit, t_start, t_done, backward_error;
+    double gpu_start_ms, gpu_end_ms;
 } rfp_serve_completion_t;
 typedef struct rfp_serve_stats {
     int64_t submitted, completed, batches, batched_requests, cache_hits, evictions, cache_entries;

@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchMaxN = 512;
+constexpr int kBatchMaxRhs = 32;   // right-hand sides per matrix (solved 8 per pass)
 
 struct PlanEntry {           // device table row (sorted by n descending)
     int64_t n, arf, b;
@@ -314,7 +315,12 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(PlanHeader *hdr,
         else fail = factor_one<T, MAXNB>(A, e.n, P, s_rinv, &s_fail);
         if (threadIdx.x == 0) info[e.index] = fail;
         __syncthreads();
-        if (fail == 0 && e.nrhs > 0) solve_one<T>(A, e.n, B + e.b, e.ldb, e.nrhs, D, Y, rdiag);
+        // up to kMaxRhs right-hand sides per pass; the factor (n <= 512) stays in L2
+        for (int g = 0; fail == 0 && g < e.nrhs; g += kMaxRhs) {
+            solve_one<T>(A, e.n, B + e.b + (int64_t)g * e.ldb, e.ldb,
+                         e.nrhs - g < kMaxRhs ? e.nrhs - g : kMaxRhs, D, Y, rdiag);
+            __syncthreads();
+        }
         __syncthreads();
     }
 }
@@ -390,7 +396,7 @@ int batch_plan(int64_t batch, const rfp_batch_entry_t *h, int64_t arf_len, int64
         bool ok = tr_ok && up_ok && e.n >= 0 && e.n <= kBatchMaxN && e.arf >= 0 &&
                   e.arf + nt <= arf_len && (e.nb == 0 || e.nb == 16 || e.nb == 24 || e.nb == 32) &&
                   e.nrhs >= 0 &&
-                  e.nrhs <= 8;
+                  e.nrhs <= kBatchMaxRhs;
         if (ok && e.nrhs > 0)   // an order-0 matrix reads no right-hand side
             ok = e.ldb >= std::max<int64_t>(1, e.n) &&
                  (e.n == 0 || (e.b >= 0 && e.b + (int64_t)(e.nrhs - 1) * e.ldb + e.n <= b_len));

@@ -4,9 +4,12 @@
 // GPU as soon as a stream slot and arena memory are free, so work that
 // arrives while other requests run overlaps with it on the device
 // (continuous batching):
-//   * small FP64 factor+solve requests (n <= small_n, nrhs <= 8) are
-//     gathered into one launch of the batched kernel whenever a batch stream
-//     is idle: everything that arrived meanwhile goes into the next batch;
+//   * small factor+solve requests (n <= small_n, nrhs <= 32) are gathered
+//     into one launch of the batched kernel whenever a batch stream is idle:
+//     everything that arrived meanwhile goes into the next batch.  A
+//     mixed-mode request of order <= small_n is served in FP64 like the
+//     others: the FP64 result meets the mixed mode's accuracy, and at these
+//     orders FP64 is at least as fast;
 //   * every other request runs on its own stream: FP64 PFTRF + PFTRS
 //     (Sections 3-4), the mixed-precision solve, or PFTRI on a copy of a
 //     resident factor.
@@ -14,7 +17,8 @@
 // stay resident under the caller's key (least recently used evicted first,
 // never while in use), i.e. the cache is admitted by RFP bytes n(n+1)/2 * 8.
 // Completion times are taken by host callbacks enqueued behind each
-// request's result copies.
+// request's result copies; CUDA events around each request's (or batch's)
+// GPU work give its device-clock start and end.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -39,6 +43,7 @@ using rfp::serve::Held;
 constexpr int kMaxStreams = 64;
 constexpr int kBatchStreams = 2;
 constexpr int kSlots = 1 << 15;   // pinned result slots (in-flight jobs)
+constexpr int kBatchRhs = 32;     // right-hand sides a batched request may have
 
 struct ResultSlot {               // pinned host memory, written by D2H copies
     int32_t info;
@@ -56,6 +61,8 @@ struct Job {
     int slot = -1;                // ResultSlot index
     int stream = -1;              // stream slot (-1: batched)
     int32_t status = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around its GPU work (stream jobs)
+    double gpu_start_ms = 0, gpu_end_ms = 0;
 };
 
 struct Batch {
@@ -63,6 +70,7 @@ struct Batch {
     int64_t plan_off = -1, info_off = -1;
     int stream = -1;
     double t_done = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the batch's GPU work
 };
 
 double now_s(std::chrono::steady_clock::time_point t0)
@@ -91,6 +99,10 @@ public:
             if (cudaStreamCreateWithFlags(&streams_[i], cudaStreamNonBlocking) != cudaSuccess)
                 return RFP_ERR_CUDA;
         for (int i = 0; i < cfg_.streams; ++i) free_streams_.push_back(i);
+        // reference point of the device-clock stamps
+        if (cudaEventCreate(&ref_) != cudaSuccess || cudaEventRecord(ref_, streams_[0]) != cudaSuccess ||
+            cudaEventSynchronize(ref_) != cudaSuccess)
+            return RFP_ERR_CUDA;
         for (int i = 0; i < kBatchStreams; ++i) free_batch_streams_.push_back(cfg_.streams + i);
         worker_ = std::thread([this] { run(); });
         return RFP_OK;
@@ -105,6 +117,8 @@ public:
         cv_.notify_all();
         if (worker_.joinable()) worker_.join();
         for (auto s : streams_) if (s) cudaStreamDestroy(s);
+        for (auto ev : free_events_) cudaEventDestroy(ev);
+        if (ref_) cudaEventDestroy(ref_);
         if (slots_) cudaFreeHost(slots_);
         if (base_) cudaFree(base_);
     }
@@ -186,7 +200,9 @@ private:
         c.t_submit = j->t_submit;
         c.t_start = j->t_start;
         c.t_done = j->t_done;
-        if (j->slot >= 0 && j->req.mode == RFP_SERVE_MODE_MIXED && j->req.op != RFP_SERVE_OP_INVERT) {
+        c.gpu_start_ms = j->gpu_start_ms;
+        c.gpu_end_ms = j->gpu_end_ms;
+        if (j->slot >= 0 && !fp64_path(j->req) && j->req.op != RFP_SERVE_OP_INVERT) {
             c.iterations = slots_[j->slot].st.iterations;
             c.backward_error = slots_[j->slot].st.backward_error;
         }
@@ -216,7 +232,7 @@ private:
         int32_t status = 0;
         if (j->slot >= 0) {
             const ResultSlot &s = slots_[j->slot];
-            if (j->req.mode == RFP_SERVE_MODE_MIXED && j->req.op != RFP_SERVE_OP_INVERT) {
+            if (!fp64_path(j->req) && j->req.op != RFP_SERVE_OP_INVERT) {
                 if (s.st.info) status = s.st.info;
                 else if (s.st.tc_error) status = RFP_SERVE_ECUDA;
                 else if (!s.st.converged) status = RFP_SERVE_ENOCONV;
@@ -243,15 +259,50 @@ private:
         j->arf_off = -1;
         if (j->slot >= 0) free_slots_.push_back(j->slot);
         if (j->stream >= 0) free_streams_.push_back(j->stream);
+        if (j->ev0 && j->ev1) {   // its GPU work is complete (the callback came after ev1)
+            j->gpu_start_ms = event_ms(j->ev0);
+            j->gpu_end_ms = event_ms(j->ev1);
+        }
+        put_event(j->ev0);
+        put_event(j->ev1);
+        j->ev0 = j->ev1 = nullptr;
         complete(j);
         jobs_.erase(j);
+    }
+
+    // FP64 requests, and mixed-mode requests of order <= small_n, run the
+    // FP64 path (their array is held as an FP64 factor).
+    bool fp64_path(const rfp_serve_request_t &r) const
+    {
+        return r.mode == RFP_SERVE_MODE_FP64 || (cfg_.small_n > 0 && r.n <= cfg_.small_n);
     }
 
     bool is_small(const Job *j) const
     {
         const auto &r = j->req;
-        return r.op == RFP_SERVE_OP_FACTOR_SOLVE && r.mode == RFP_SERVE_MODE_FP64 &&
-               r.n <= cfg_.small_n && r.nrhs <= 8;
+        return r.op == RFP_SERVE_OP_FACTOR_SOLVE && fp64_path(r) && r.n <= cfg_.small_n &&
+               r.nrhs <= kBatchRhs;
+    }
+
+    // Event pool for the device-clock stamps.
+    cudaEvent_t get_event()
+    {
+        if (!free_events_.empty()) {
+            cudaEvent_t e = free_events_.back();
+            free_events_.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+    }
+    void put_event(cudaEvent_t e)
+    {
+        if (e) free_events_.push_back(e);
+    }
+    double event_ms(cudaEvent_t e)
+    {
+        float ms = 0.f;
+        return cudaEventElapsedTime(&ms, ref_, e) == cudaSuccess ? (double)ms : 0.0;
     }
 
     int64_t alloc(size_t bytes) { return cache_.alloc_evicting(bytes); }
@@ -310,7 +361,7 @@ private:
         const auto &r = j->req;
         const size_t bx = (size_t)r.n * (size_t)r.nrhs * sizeof(double);
         if (r.op == RFP_SERVE_OP_INVERT) return rfp_bytes(r.n) + 256;
-        if (r.mode == RFP_SERVE_MODE_MIXED)
+        if (!fp64_path(r))
             return 2 * bx + rfp_dpfsv_mixed_workspace(r.n, r.nrhs, RFP_PREC_TF32X3) + 3 * 256;
         return bx + 256;
     }
@@ -320,7 +371,7 @@ private:
     {
         const auto &r = j->req;
         const size_t bx = (size_t)r.n * (size_t)r.nrhs * sizeof(double);
-        const bool mixed = r.mode == RFP_SERVE_MODE_MIXED;
+        const bool mixed = !fp64_path(r);
         if (r.op == RFP_SERVE_OP_FACTOR_SOLVE) {
             if (!place_arf(j, mixed ? Held::Matrix64 : Held::Factor64)) return false;
         } else {   // SOLVE / INVERT need a resident array under the key
@@ -353,12 +404,15 @@ private:
         const auto &r = j->req;
         cudaStream_t st = streams_[j->stream];
         const size_t bx = (size_t)r.n * (size_t)r.nrhs * sizeof(double);
-        const bool mixed = r.mode == RFP_SERVE_MODE_MIXED;
+        const bool mixed = !fp64_path(r);
         ResultSlot *hs = &slots_[j->slot];
         int32_t *d_info = reinterpret_cast<int32_t *>(dptr(j->stat_off));
         int rc = 0;
         cudaError_t e = cudaSuccess;
         j->t_start = now_s(t0_);
+        j->ev0 = get_event();
+        j->ev1 = get_event();
+        if (j->ev0) cudaEventRecord(j->ev0, st);
         if (r.op == RFP_SERVE_OP_INVERT) {
             e = cudaMemcpyAsync(dptr(j->tmp_off), dptr(j->arf_off), rfp_bytes(r.n), cudaMemcpyDeviceToDevice, st);
             CacheEntry *ce = cache_.find(r.key);
@@ -386,6 +440,7 @@ private:
             }
         }
         if (e != cudaSuccess || rc != 0) j->status = RFP_SERVE_ECUDA;
+        if (j->ev1) cudaEventRecord(j->ev1, st);
         // the completion callback runs after everything enqueued above
         e = cudaLaunchHostFunc(st, on_done, new Done{this, j, nullptr});
         if (e != cudaSuccess) {   // no callback will come: finish now (after the stream drains)
@@ -459,6 +514,9 @@ private:
         int64_t bad = -1;
         const double t = now_s(t0_);
         int rc = rfp_batch_plan(count, ent.data(), len, len, dptr(b->plan_off), plan_bytes, &bad, st);
+        b->ev0 = get_event();
+        b->ev1 = get_event();
+        if (b->ev0) cudaEventRecord(b->ev0, st);
         cudaError_t e = cudaSuccess;
         for (int64_t k = 0; k < count && !rc && !e; ++k) {
             Job *j = b->jobs[k];
@@ -479,6 +537,7 @@ private:
         }
         if (rc || e)
             for (Job *j : b->jobs) j->status = RFP_SERVE_ECUDA;
+        if (b->ev1) cudaEventRecord(b->ev1, st);
         {
             std::lock_guard<std::mutex> lk(smu_);
             ++stats_.batches;
@@ -496,7 +555,13 @@ private:
 
     void retire_batch(Batch *b)
     {
+        const double g0 = (b->ev0 && b->ev1) ? event_ms(b->ev0) : 0.0;
+        const double g1 = (b->ev0 && b->ev1) ? event_ms(b->ev1) : 0.0;
+        put_event(b->ev0);
+        put_event(b->ev1);
         for (Job *j : b->jobs) {
+            j->gpu_start_ms = g0;
+            j->gpu_end_ms = g1;
             j->t_done = b->t_done;
             retire(j);
         }
@@ -628,6 +693,8 @@ private:
     void *base_ = nullptr;
     ResultSlot *slots_ = nullptr;
     std::vector<cudaStream_t> streams_;
+    cudaEvent_t ref_ = nullptr;                // device-clock origin of the stamps
+    std::vector<cudaEvent_t> free_events_;     // scheduler thread only
     std::vector<int> free_streams_, free_batch_streams_, free_slots_;
     std::thread worker_;
 

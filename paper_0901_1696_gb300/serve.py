@@ -35,7 +35,8 @@ class ServeCompletion(ctypes.Structure):
                 ("iterations", ctypes.c_int32), ("cache_hit", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("t_submit", ctypes.c_double),
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
-                ("backward_error", ctypes.c_double)]
+                ("backward_error", ctypes.c_double), ("gpu_start_ms", ctypes.c_double),
+                ("gpu_end_ms", ctypes.c_double)]
 
 
 class ServeStats(ctypes.Structure):

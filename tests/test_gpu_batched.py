@@ -33,7 +33,7 @@ def make_batch(count, seed, n_max=512, fail_every=0):
     for k, n in enumerate(ns):
         n = int(n)
         transr, uplo = LAYOUTS8[rng.integers(0, 4)]
-        nrhs = int(rng.integers(0, 9))
+        nrhs = int(rng.integers(0, 33))   # up to 32: solved in passes of 8 columns
         A, r2 = gen.spd_bbt(n, seed=1000 + seed * 10000 + k, return_rng=True)
         fail = 0
         if fail_every and k % fail_every == fail_every - 1 and n > 2:
@@ -157,3 +157,13 @@ def test_autotune_small_writes_cache(tmp_path):
     assert bt.TuningCache(str(tmp_path / "tune.json")).get(gpu, "f64") == table
     e, _, _ = bt.make_entries([40, 400], ["N", "T"], ["L", "U"], [1, 2])
     assert cache.fill_nb(e, gpu, "f64") and set(e["nb"]) <= {16, 24, 32}
+
+
+def test_plan_rejects_more_than_32_right_hand_sides():
+    entries = np.zeros(2, dtype=rfp.batch_entry_dtype())
+    for k, r in enumerate((32, 33)):
+        entries[k] = (10, 55 * k, 10 * 32 * k, r, 10, b"N", b"L", 16, 0)
+    plan = torch.empty(rfp.rfp_batch_plan_bytes(2), dtype=torch.uint8, device="cuda")
+    with pytest.raises(rfp.RfpError) as e:
+        rfp.rfp_batch_plan(2, entries, 110, 10 * 32 + 10 * 33, plan, plan.numel())
+    assert e.value.status == -2 and "entry 1" in str(e.value)

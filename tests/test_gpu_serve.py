@@ -162,3 +162,38 @@ def test_serve_rejects_bad_requests():
             s.submit(0, 7, 0, "N", "L", 4, 1, arf=B, B=B, X=B)
     with pytest.raises(rfp.RfpError):
         srv_mod.Server(arena_bytes=1024, streams=1)
+
+
+def test_serve_two_long_requests_overlap_on_the_device():
+    """Two long factor+solve requests submitted together run on two streams
+    at once: their device intervals (CUDA events around each request's GPU
+    work) intersect, and each result is the oracle's."""
+    reqs = make_requests([(4000, 8, 0, 0), (4001, 8, 0, 3)], seed=6)
+    with srv_mod.Server(arena_bytes=1 << 30, streams=4, small_n=0) as s:
+        for r in reqs:
+            submit(s, r)
+        done = {c["id"]: c for c in s.wait(2)}
+    a, b = done[0], done[1]
+    for c in (a, b):
+        assert c["status"] == 0 and c["batched"] == 0
+        assert 0.0 < c["gpu_start_ms"] < c["gpu_end_ms"]
+    assert max(a["gpu_start_ms"], b["gpu_start_ms"]) < min(a["gpu_end_ms"], b["gpu_end_ms"])
+    for r in reqs:
+        check_solution(r)
+
+
+def test_serve_small_requests_with_many_rhs_and_mixed_mode_are_batched():
+    """Factor+solve requests of order <= small_n with up to 32 right-hand
+    sides, FP64 or mixed mode, go into batched launches; every result meets
+    its mode's bar."""
+    specs = [(100, 32, 0, 0), (257, 17, 1, 1), (512, 9, 1, 2), (64, 1, 0, 3), (300, 32, 1, 0)]
+    reqs = make_requests(specs, seed=7)
+    with srv_mod.Server(arena_bytes=1 << 30, streams=2, batch_max=64) as s:
+        for r in reqs:
+            submit(s, r)
+        done = {c["id"]: c for c in s.wait(len(reqs))}
+    for r in reqs:
+        c = done[r["id"]]
+        assert c["status"] == 0 and c["batched"] == 1, c
+        assert c["gpu_start_ms"] <= c["gpu_end_ms"]
+        check_solution(r)
