@@ -151,6 +151,16 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
                 while (ti * (ti + 1) / 2 > t) --ti;
                 const int tj = t - ti * (ti + 1) / 2;
                 const T *pa = P + kb + 4 * ti, *pb = P + kb + 4 * tj;   // zero beyond `rows`
+                // the tile's current values first: their load latency overlaps
+                // the multiply-adds below (nothing in the loop writes them)
+                T cin[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int i = 4 * ti + u, j = 4 * tj + v;
+                        cin[u][v] = (i < m && j <= i) ? *A.at(k0 + kb + i, k0 + kb + j) : T(0);
+                    }
                 T acc[4][4] = {};
                 for (int c = 0; c < kb; ++c) {
                     T a[4], b[4];
@@ -161,14 +171,6 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
 #pragma unroll
                         for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
                 }
-                T cin[4][4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int i = 4 * ti + u, j = 4 * tj + v;
-                        cin[u][v] = (i < m && j <= i) ? *A.at(k0 + kb + i, k0 + kb + j) : T(0);
-                    }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
