@@ -61,7 +61,8 @@ def parse():
                         "reference step)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["fp64", "mixed", "batched", "serve", "surface"], default="fp64",
+    p.add_argument("--mode", choices=["fp64", "mixed", "batched", "serve", "surface", "c1"],
+                   default="fp64",
                    help="fp64: the FP64 hot path (default line); mixed: the mixed-precision "
                         "solve at n = 32768 against the FP64 path (its own line)")
     p.add_argument("--mixed-n", type=int, default=32768)
@@ -1041,8 +1042,25 @@ def run_surface(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c1(args):
+    """The n = 1001 latency case alone (its own line): `--steps` timed calls
+    of each routine after 5 warm-up rounds, without the oracle."""
+    import torch
+
+    from paper_0901_1696_gb300 import binding as rfp
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    out = c1_leg(rfp.library(), dev, torch.cuda.current_stream(dev), reps=max(args.steps, 1),
+                 oracle_too=False)
+    print(json.dumps({"mode": "c1", "metric": "PFTRF / PFTRS / PFTRI latency at n = 1001",
+                      "unit": "us", "higher_is_better": False, **out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "c1":
+        run_c1(args)
+        return
     if args.mode == "mixed":
         run_mixed(args)
         return

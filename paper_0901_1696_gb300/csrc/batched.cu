@@ -116,7 +116,14 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
                 if (!(d > T(0))) {
                     *s_fail = c;
                 } else {
-                    const T sq = sqrt(d), ri = T(1) / sq;
+                    T sq, ri;
+                    if constexpr (sizeof(T) == 8) {   // see rsqrt_newton
+                        ri = rsqrt_newton(d);
+                        sq = d * ri;
+                    } else {
+                        sq = sqrt(d);
+                        ri = T(1) / sq;
+                    }
                     P[c * LDC + c] = sq;
                     *s_rinv = ri;
                     for (int q = c + 1; q < kb; ++q) P[c * LDC + q] *= ri;

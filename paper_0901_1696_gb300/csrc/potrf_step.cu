@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
             if (tid == 0) {
                 const double d = sm.T[j][j];
                 sm.flag = (d > 0.0) ? -1 : j;            // pivot <= 0 or NaN fails
-                const double r = sqrt(d);
-                sm.sq[j] = r;
-                sm.rinv[j] = 1.0 / r;
+                const double y = rsqrt_newton(d);        // 1 / sqrt(d), a few ulp
+                sm.sq[j] = d * y;
+                sm.rinv[j] = y;
             }
             __syncthreads();
             if (sm.flag >= 0) { fail = sm.flag; break; }

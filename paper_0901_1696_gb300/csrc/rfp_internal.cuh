@@ -59,6 +59,32 @@ __host__ __device__ inline bool mask_keeps(int mask, int64_t r, int64_t c)
     }
 }
 
+#ifdef __CUDACC__
+// 1 / sqrt(d) for a normal, finite d > 0 by Newton-Raphson iteration for the
+// reciprocal square root, y <- y (3/2 - (d/2) y^2): d = m 4^k with m in
+// [1, 4) (exponent split), a single-precision seed for m (about 23 correct
+// bits), two double-precision steps (each doubles the correct bits; the
+// last one's rounding leaves an error of a few ulp), and the scale 2^-k.
+// Other d (zero, negative, subnormal, infinite, NaN) take 1 / sqrt(d).  On
+// GB300's narrow FP64 pipe this is a few dependent multiply-adds where a
+// square root followed by a division is two long instruction sequences; the
+// Cholesky pivots use it for both l_jj = d y and the column scale y.
+__device__ __forceinline__ double rsqrt_newton(double d)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    if (!(d > 0.0) || e <= -1023 || e >= 1024) return 1.0 / sqrt(d);
+    const int k = e >> 1;                                           // floor(e / 2)
+    const double m = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) |
+                                                      ((unsigned long long)(e - 2 * k + 1023) << 52)));
+    double y = (double)rsqrtf((float)m);
+    const double h = 0.5 * m;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) y = fma(y, fma(-h * y, y, 0.5), y);
+    return y * __longlong_as_double((long long)((unsigned long long)(1023 - k) << 52));
+}
+#endif
+
 // Records e as the calling thread's last CUDA error (rfp_last_cuda_error) and
 // returns the library's CUDA-failure status (1); cudaSuccess returns 0.
 int finish_cuda(cudaError_t e);

@@ -514,9 +514,10 @@ __device__ __forceinline__ void store_lower_tile(View<T> A, const T *S, int w)
 // Unblocked right-looking Cholesky of one tile, l_ij = a_ij * (1 / sqrt(pivot))
 // (LAPACK's unblocked Cholesky also scales a column by the reciprocal of its
 // diagonal).
-// FP64: at step j one thread forms the pivot's square root and reciprocal
-// (on GB300's narrow FP64 pipe a square root and a division in every thread
-// would cost more than the step's multiply-adds), the column is scaled in
+// FP64: at step j one thread forms the pivot's reciprocal square root y
+// (Newton-Raphson, rsqrt_newton) and l_jj = d y (on GB300's narrow FP64
+// pipe a square root and a division per step, let alone per thread, would
+// cost more than the step's multiply-adds), the column is scaled in
 // place, and the trailing triangle is updated by a 16 x 16 grid of threads
 // (one DFMA per element); three barriers per column.
 // FP32: one barrier per column; each thread forms the pivot's reciprocal and
@@ -538,9 +539,9 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(View<T> A, int w, int32
             if (threadIdx.x == 0) {
                 const T d = S[j * kTileLd + j];
                 s_fail = (d > T(0)) ? -1 : j;              // pivot <= 0 or NaN fails
-                const T r = sqrt(d);
-                sq[j] = r;
-                rinv[j] = T(1) / r;
+                const T y = rsqrt_newton(d);
+                sq[j] = d * y;
+                rinv[j] = y;
             }
             __syncthreads();
             if (s_fail >= 0) { fail = s_fail; break; }

@@ -238,3 +238,26 @@ def test_runs_on_the_given_stream():
     s.synchronize()
     ref, _ = oracle.pftrf("N", "L", n, oracle.pack("N", "L", A))
     assert np.max(np.abs(arf.cpu().numpy() - ref)) <= factor_tolerance(n) * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("transr,uplo", [("N", "L"), ("T", "U"), ("N", "U"), ("T", "L")])
+def test_pftrf_diagonal_pivots_within_ulps(transr, uplo):
+    """The FP64 pivots' square roots come from a Newton-Raphson reciprocal
+    square root (about a few ulp); for a diagonal A, L = diag(sqrt(a_ii)) must
+    be within 4 ulp of the correctly rounded square root (numpy's, IEEE) over
+    the whole normal exponent range, subnormal entries included (they take
+    the exact path), with every off-diagonal entry exactly zero.  n = 300
+    spans the first panel (tile POTRF) and the lookahead steps."""
+    n = 300
+    rng = np.random.default_rng(5)
+    d = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-1020, 1020, n))
+    d[:12] = [1.0, 2.0, 4.0, 0.25, 3.0, 1e-300, 1e300, 1.7e308, 2.3e-308, 1e-310, 5e-324, 0.5]
+    A = np.diag(d)
+    arf = _arf(oracle.pack(transr, uplo, A))
+    info = _info()
+    rfp.rfp_dpftrf(transr, uplo, n, arf, info)
+    assert int(info.item()) == 0
+    L = _lower(transr, uplo, n, arf.cpu().numpy())
+    ref = np.sqrt(d)
+    assert np.all(np.abs(np.diag(L) - ref) <= 4 * np.spacing(ref))
+    assert np.count_nonzero(L - np.diag(np.diag(L))) == 0

@@ -9,6 +9,8 @@ contents: the second result must be just as right.  This file is collected
 last so that a failure here leaves every other test already run; it passes
 alone in a fresh process as well.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -66,14 +68,15 @@ def test_no_alloc_call_allocates_nothing():
     _no_alloc(transr, uplo, n, nrhs, arf, dB, prec)          # set-up call
     X = torch.full((nrhs, n), np.nan, dtype=torch.float64, device="cuda")
     st = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    gc.collect()              # temporaries of the set-up call are released now, not mid-test
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
     alloc0 = torch.cuda.memory_allocated()
     rfp.rfp_dpfsv_mixed_noalloc(transr, uplo, n, nrhs, arf, dB, n, X, n, prec, 30, 1e-15, st)
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
-    assert torch.cuda.memory_allocated() == alloc0
-    assert free1 == free0
+    assert torch.cuda.memory_allocated() <= alloc0
+    assert free1 >= free0
     assert rfp.mixed_status(st.cpu().numpy().tobytes())["converged"] == 1
     assert oracle.solve_backward_error(A, X.cpu().numpy().T, B) <= 1e-14
 
