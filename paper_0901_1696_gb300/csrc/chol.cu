@@ -26,6 +26,29 @@ constexpr int64_t kNb = 64;   // diagonal tile width
         if (e_ != cudaSuccess) return e_;        \
     } while (0)
 
+// op(V) Y = alpha X in place (V the m x m lower triangle, X an m x nrhs view,
+// op = transpose when `trans`) as one launch of the block substitution
+// (rfp_solve.cu) in FP64.  Returns false when it did not run (FP32, or no
+// scratch, e.g. under stream capture): the caller then runs its multi-launch
+// form.  *err receives the launch's result when it ran.
+template <typename T>
+bool solve_one_launch(cudaStream_t st, View<T> V, int64_t m, View<T> X, int64_t nrhs, bool trans,
+                      T alpha, const int32_t *abort, cudaError_t *err)
+{
+    if constexpr (sizeof(T) == 8) {
+        int32_t *sync = nullptr;
+        if (solve_scratch_acquire(st, rfp_solve_sync_words(nrhs), &sync) != cudaSuccess) {
+            (void)cudaGetLastError();   // the failed scratch request is not the caller's error
+            return false;
+        }
+        const cudaError_t e = rfp_solve(st, V, V, V, m, 0, X, nrhs, trans, sync, abort, alpha);
+        const cudaError_t e2 = solve_scratch_release(st, sync);
+        *err = e != cudaSuccess ? e : e2;
+        return true;
+    }
+    return false;
+}
+
 // ---- triangle-level building blocks ----------------------------------------
 
 // Right-looking blocked Cholesky of the m x m lower triangle V in place
@@ -172,6 +195,21 @@ cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *
     return cudaSuccess;
 }
 
+// S <- -L22^{-1} S L11^{-1} (Sec. 5, W21 = -W22 L21 W11, reading R9): first
+// S <- -S L11^{-1}, i.e. L11^T S^T = -S^T, then S <- L22^{-1} S.  In FP64
+// each is one launch of the block substitution.
+template <typename T>
+cudaError_t w21_solves(cudaStream_t st, View<T> t1, View<T> s, View<T> t2, int64_t n1, int64_t n2,
+                       const int32_t *info)
+{
+    cudaError_t e = cudaSuccess;
+    if (solve_one_launch(st, t1, n1, s.t(), n2, true, T(-1), info, &e)) RFP_TRY(e);
+    else RFP_TRY(trsm_right_lower_notrans(st, s, n2, t1, n1, T(-1), info));
+    if (solve_one_launch(st, t2, n2, s, n1, false, T(1), info, &e)) RFP_TRY(e);
+    else RFP_TRY(trsm_left_lower_notrans(st, s, n1, t2, n2, info));
+    return cudaSuccess;
+}
+
 // ---- the three routines --------------------------------------------------------
 
 template <typename T>
@@ -187,20 +225,9 @@ cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
         // step 2: L21 L11^T = A21, i.e. L11 L21^T = A21^T: in FP64 one launch
         // of the block substitution with T1 and the n2 columns of S^T
         // (rfp_solve.cu); the multi-launch form when no scratch can be had.
-        bool done = false;
-        if constexpr (sizeof(T) == 8) {
-            int32_t *sync = nullptr;
-            if (solve_scratch_acquire(st, rfp_solve_sync_words(L.n2), &sync) == cudaSuccess) {
-                const cudaError_t e = rfp_solve(st, t1, s, t2, L.n1, 0, s.t(), L.n2, false, sync, info);
-                const cudaError_t e2 = solve_scratch_release(st, sync);
-                RFP_TRY(e);
-                RFP_TRY(e2);
-                done = true;
-            } else {
-                (void)cudaGetLastError();   // the failed scratch request is not the caller's error
-            }
-        }
-        if (!done) RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
+        cudaError_t e = cudaSuccess;
+        if (solve_one_launch(st, t1, L.n1, s.t(), L.n2, false, T(1), info, &e)) RFP_TRY(e);
+        else RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
         stage_mark(st, "pftrf.trsm_s");
         // step 3: A22 <- A22 - L21 L21^T (lower triangle of T2)
         RFP_TRY(gemm_nt(st, t2, s, s, L.n2, L.n2, L.n1, T(-1), T(1), MASK_LOWER, MASK_NONE,
@@ -260,8 +287,7 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     RFP_TRY(check_diag(st, t1, L.n1, t2, L.n2, info));
     if (L.n1 > 0 && L.n2 > 0) {
         // W21 = -L22^{-1} L21 L11^{-1}: two in-place solves with the factor
-        RFP_TRY(trsm_right_lower_notrans(st, s, L.n2, t1, L.n1, T(-1), info));
-        RFP_TRY(trsm_left_lower_notrans(st, s, L.n1, t2, L.n2, info));
+        RFP_TRY(w21_solves(st, t1, s, t2, L.n1, L.n2, info));
     }
     stage_mark(st, "pftri.w21");
     // T1 <- W11^T W11 + W21^T W21
@@ -274,7 +300,9 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
                         MASK_NONE, MASK_NONE, info));
         stage_mark(st, "pftri.syrk_t1");
         // S <- W22^T W21 = L22^{-T} W21 (T2 still holds L22)
-        RFP_TRY(trsm_left_lower_trans(st, s, L.n1, t2, L.n2, info));
+        cudaError_t e = cudaSuccess;
+        if (solve_one_launch(st, t2, L.n2, s, L.n1, true, T(1), info, &e)) RFP_TRY(e);
+        else RFP_TRY(trsm_left_lower_trans(st, s, L.n1, t2, L.n2, info));
         stage_mark(st, "pftri.trmm_s");
     }
     // T2 <- W22^T W22
@@ -294,10 +322,7 @@ cudaError_t tftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
 {
     View<T> t1 = block_view(arf, L, L.t1), s = block_view(arf, L, L.s), t2 = block_view(arf, L, L.t2);
     RFP_TRY(check_diag(st, t1, L.n1, t2, L.n2, info));
-    if (L.n1 > 0 && L.n2 > 0) {
-        RFP_TRY(trsm_right_lower_notrans(st, s, L.n2, t1, L.n1, T(-1), info));
-        RFP_TRY(trsm_left_lower_notrans(st, s, L.n1, t2, L.n2, info));
-    }
+    if (L.n1 > 0 && L.n2 > 0) RFP_TRY(w21_solves(st, t1, s, t2, L.n1, L.n2, info));
     RFP_TRY(trtri_blocked(st, t1, L.n1, info));
     return trtri_blocked(st, t2, L.n2, info);
 }

@@ -253,12 +253,12 @@ cudaError_t trsm_wavefront(cudaStream_t st, View<float> Lv, int64_t n, const flo
 // its RFP block views (n2 = 0: L is T1 alone).  sync: device scratch of
 // rfp_solve_sync_words(nrhs) int32 (cleared by the call, stream-ordered).
 // abort: if non-null and non-zero when the launch starts, nothing is done.
-// If a wait between tasks expires (2 s), the blocks of X not computed are
-// set to NaN.
+// alpha scales the right-hand side (op(L) Y = alpha X).  If a wait between
+// tasks expires (2 s), the blocks of X not computed are set to NaN.
 size_t rfp_solve_sync_words(int64_t nrhs);
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
-                      const int32_t *abort = nullptr);
+                      const int32_t *abort = nullptr, double alpha = 1.0);
 // One panel step of the FP64 lookahead Cholesky of an m x m lower triangle V
 // (potrf_step.cu), panel k = [k0, k0 + 64) already factored: the trailing
 // update with it, and the factorization of panel k + 1 (its diagonal tile

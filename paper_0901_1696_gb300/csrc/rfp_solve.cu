@@ -55,6 +55,7 @@ struct SolveArgs {
     int ng;
     int32_t *counter, *prog, *err;
     const int32_t *abort;           // if set (non-zero) at launch, nothing is done
+    double alpha;                   // the right-hand side is alpha X
 };
 
 __device__ __forceinline__ uint64_t rs_globaltimer()
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int r = ty * 4 + m, cc = tx * 2 + c;
-            acc[m][c] = (r < rows && cc < cols) ? __ldcg(&Xb(r, cc)) : 0.0;
+            acc[m][c] = (r < rows && cc < cols) ? a.alpha * __ldcg(&Xb(r, cc)) : 0.0;
         }
 
     bool ok = true;
@@ -361,7 +362,7 @@ size_t rfp_solve_sync_words(int64_t nrhs)
 
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
-                      const int32_t *abort)
+                      const int32_t *abort, double alpha)
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
@@ -373,7 +374,7 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
     cudaError_t e = cudaMemsetAsync(sync, 0, rfp_solve_sync_words(nrhs) * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, nrhs, (int)ng,
-                sync, sync + 2, sync + 1, abort};
+                sync, sync + 2, sync + 1, abort, alpha};
     if (trans) rfp_solve_kernel<true><<<(unsigned)tasks, kThreads, 0, st>>>(a);
     else rfp_solve_kernel<false><<<(unsigned)tasks, kThreads, 0, st>>>(a);
     note_launch();

@@ -389,7 +389,7 @@ size_t rfp_solve_sync_words(int64_t nrhs) { return (size_t)(2 + (nrhs + 15) / 16
 
 cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> Xv, int64_t nrhs, bool trans, int32_t *sync,
-                      const int32_t *abort)
+                      const int32_t *abort, double alpha)
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
@@ -421,7 +421,7 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
         const int64_t c0 = g * 16, cols = std::min<int64_t>(16, nrhs - c0);
         std::vector<double> acc(rows * cols);
         for (int64_t c = 0; c < cols; ++c)
-            for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = L.rd(xat(r0 + r, c0 + c));
+            for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = alpha * L.rd(xat(r0 + r, c0 + c));
         for (int64_t q = 0; q < p; ++q) {
             const int64_t j = trans ? nb - 1 - q : q;
             if (L.rd(prog + g) < q + 1) violation("X block read before its group's progress", prog + g);
