@@ -18,9 +18,10 @@
 //   * warps 0-3 read an accumulator with tcgen05.ld (one TMEM lane per
 //     thread = one C row), hand it back, and apply the masked epilogue to C;
 //     meanwhile the MMAs of the next tile fill the other accumulator.  When
-//     the C view allows it, the C tile is staged in shared memory by TMA
-//     (four 128 x 32 FP32 boxes), the next tile's as soon as the current one
-//     has been read, so the epilogue does not wait on scattered C loads.
+//     the C view allows it, the C tile is staged in shared memory by TMA in
+//     two halves of 64 columns (two 128 x 32 FP32 boxes each); half h of the
+//     next tile is loaded as soon as half h of the current one has been read,
+//     so the epilogue does not wait on scattered C loads.
 // Every mbarrier wait is bounded by time; on expiry the kernel records an
 // error code in *err and every role stops issuing work; the producer then
 // waits (bounded) for its copies in flight, the MMA issuer for its MMAs, and
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *accf = empty + kStages;     // [2] accumulator ready (MMA commit)
     uint64_t *acce = accf + 2;            // [2] accumulator drained (4 epilogue warps)
     uint64_t *drain = acce + 2;           // every MMA of this CTA completed
-    uint64_t *cfull = drain + 1;          // the staged C tile has landed
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cfull + 1);
+    uint64_t *cfull = drain + 1;          // [2] a staged half of the C tile has landed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cfull + 2);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int bk = kRowBytes / (KIND == 0 ? 2 : 4);                 // K elements per stage
@@ -290,7 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&acce[b], 4);
         }
         mbar_init(drain, 1);
-        mbar_init(cfull, 1);
+        mbar_init(&cfull[0], 1);
+        mbar_init(&cfull[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before();
@@ -347,89 +349,100 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_commit(drain);
         mbar_wait_quiet(drain, 0);
     } else if (warp < 4) {
-        // ---- epilogue: lane = row of the tile.  With c_tma, thread 0 stages
-        // the C tile of the CTA's next tile in shared memory by TMA as soon
-        // as the current one has been read, so its load overlaps the wait for
-        // the accumulator.
+        // ---- epilogue: lane = row of the tile.  With c_tma, the C tile is
+        // staged in shared memory in two halves of 64 columns; thread 0 loads
+        // half h of the CTA's next tile by TMA as soon as every epilogue
+        // thread has read half h of the current one, so each load overlaps
+        // the processing of the other half.
         const int etid = threadIdx.x;   // 0 .. 127
-        int64_t lt = 0, c_issued = 0;
-        auto issue_c = [&](int64_t t) {
+        int64_t lt = 0, issued0 = 0, issued1 = 0;   // C-half loads issued (thread 0)
+        auto issue_half = [&](int64_t t, int h) {
             int64_t tm, tn;
             tile_coords(a, t, tm, tn);
-            mbar_expect_tx(cfull, kCBytes);
+            mbar_expect_tx(&cfull[h], kCBytes / 2);
 #pragma unroll
-            for (int b = 0; b < kBN / kCBox; ++b)
-                tma_load_2d(sC + b * kCBox * kBM, &tmC, cfull, (int)(tm * kBM), (int)(tn * kBN) + b * kCBox);
+            for (int b = 2 * h; b < 2 * h + 2; ++b)
+                tma_load_2d(sC + b * kCBox * kBM, &tmC, &cfull[h], (int)(tm * kBM), (int)(tn * kBN) + b * kCBox);
+            if (h) ++issued1;
+            else ++issued0;
         };
         if (a.c_tma && etid == 0 && blockIdx.x < ntiles) {
-            issue_c(blockIdx.x);
-            c_issued = 1;
+            issue_half(blockIdx.x, 0);
+            issue_half(blockIdx.x, 1);
         }
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+        bool stop = false;
+        for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++lt) {
             const int buf = (int)(lt & 1);
             const int64_t u = lt >> 1;
             int64_t tm, tn;
             tile_coords(a, t, tm, tn);
             const int64_t m0 = tm * kBM, n0 = tn * kBN;
-            // Both waits are bounded; whether to go on is then decided for all
-            // four epilogue warps at once (a barrier reduction they all reach),
-            // so that none is left at the named barrier below.
             const bool acc_ok = nk == 0 || mbar_wait(&accf[buf], (uint32_t)(u & 1), a.err, 3);
-            const bool c_ok = !a.c_tma || mbar_wait(cfull, (uint32_t)(lt & 1), a.err, 3);
-            if (!epilogue_all(acc_ok && c_ok)) break;
             const bool have = nk > 0;   // uniform: tcgen05.ld is a .sync.aligned warp instruction
-            fence_after();
             const int64_t i = m0 + warp * 32 + lane;
             const bool row_ok = i < a.M;
             const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kBN);
             const float *crow = sC + warp * 32 + lane;   // sC[j][row]
-#pragma unroll 1
-            for (int c0 = 0; c0 < kBN; c0 += 32) {
-                float v[32];
-                if (have) tmem_ld32(acc + (uint32_t)c0, v);
-                else {
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                // Both waits are bounded; whether to go on is then decided for
+                // all four epilogue warps at once (a barrier reduction they all
+                // reach), so that none is left at the named barrier below.
+                const bool c_ok = !a.c_tma || mbar_wait(&cfull[h], (uint32_t)(lt & 1), a.err, 3);
+                if (!epilogue_all(acc_ok && c_ok)) {
+                    stop = true;
+                    break;
                 }
-                if (!row_ok) continue;
-                float cv[32];
-                float *prow = a.C + i * a.crs + (n0 + c0) * a.ccs;
-                const int64_t jmax = (a.cmode == MASK_LOWER && i < a.N - 1) ? i : a.N - 1;
-                const int cnt = (int)(jmax - (n0 + c0) + 1 < 32 ? jmax - (n0 + c0) + 1 : 32);
-                if (a.beta != 0.f) {
-                    if (a.c_tma) {
+                fence_after();
+#pragma unroll 1
+                for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 32) {
+                    float v[32];
+                    if (have) tmem_ld32(acc + (uint32_t)c0, v);
+                    else {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) cv[q] = crow[(c0 + q) * kBM];
-                    } else {
-                        // All loads of the chunk are issued before any store (the
-                        // stores could alias the loads as far as the compiler knows).
+                        for (int q = 0; q < 32; ++q) v[q] = 0.f;
+                    }
+                    if (!row_ok) continue;
+                    float cv[32];
+                    float *prow = a.C + i * a.crs + (n0 + c0) * a.ccs;
+                    const int64_t jmax = (a.cmode == MASK_LOWER && i < a.N - 1) ? i : a.N - 1;
+                    const int cnt = (int)(jmax - (n0 + c0) + 1 < 32 ? jmax - (n0 + c0) + 1 : 32);
+                    if (a.beta != 0.f) {
+                        if (a.c_tma) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
+                            for (int q = 0; q < 32; ++q) cv[q] = crow[(c0 + q) * kBM];
+                        } else {
+                            // All loads of the chunk are issued before any store (the
+                            // stores could alias the loads as far as the compiler knows).
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) cv[q] = q < cnt ? prow[q * a.ccs] : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (q >= cnt) continue;
+                        float out = a.alpha * v[q];
+                        if (a.beta != 0.f) out = fmaf(a.beta, cv[q], out);
+                        prow[q * a.ccs] = out;
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    if (q >= cnt) continue;
-                    float out = a.alpha * v[q];
-                    if (a.beta != 0.f) out = fmaf(a.beta, cv[q], out);
-                    prow[q * a.ccs] = out;
+                if (a.c_tma) {
+                    // every epilogue thread is done with half h of the staged tile
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (etid == 0 && t + gridDim.x < ntiles) issue_half(t + gridDim.x, h);
                 }
             }
+            if (stop) break;
             // this warp's lanes of the accumulator are read: hand it back
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[buf]);
-            if (a.c_tma) {
-                // every epilogue thread is done with the staged C tile
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (etid == 0 && t + gridDim.x < ntiles) {
-                    issue_c(t + gridDim.x);
-                    ++c_issued;
-                }
-            }
         }
-        // a staged C load still in flight (a wait above gave up) lands before teardown
-        if (a.c_tma && etid == 0 && c_issued > lt) mbar_wait_quiet(cfull, (uint32_t)((c_issued - 1) & 1));
+        // the last load of each half lands before teardown (a wait above may
+        // have given up with it still in flight; a completed one returns at once)
+        if (a.c_tma && etid == 0) {
+            if (issued0 > 0) mbar_wait_quiet(&cfull[0], (uint32_t)((issued0 - 1) & 1));
+            if (issued1 > 0) mbar_wait_quiet(&cfull[1], (uint32_t)((issued1 - 1) & 1));
+        }
     }
     fence_before();
     __syncthreads();
