@@ -8,7 +8,7 @@
 // rows below solved against that tile (TRSM).  Launch k does all of this:
 //   ticket 0             the diagonal tile of panel k+1: its update, then
 //                        POTRF in shared memory; writes L and raises a flag;
-//   tickets 1 .. P       64-row strips of panel k+1 below the diagonal: the
+//   tickets 1 .. P       32-row strips of panel k+1 below the diagonal: the
 //                        update, then (once the flag is up) the solve
 //                        X L_D^T = strip with the new diagonal tile;
 //   the other tickets    64 x 64 lower tiles of A(k2:m, k2:m): the update.
@@ -25,6 +25,7 @@ namespace rfp {
 namespace {
 
 constexpr int kT = 64;              // tile / panel width
+constexpr int kStrip = 32;          // rows of a panel strip task
 constexpr int kTh = 256;            // threads per CTA
 constexpr int kBk = 16;             // K step of the tile update
 constexpr int kSLd = kT + 2;        // staging rows (doubles; 16-byte aligned)
@@ -34,7 +35,7 @@ constexpr uint64_t kStepWaitNs = 2000000000ull;
 struct StepArgs {
     View<double> V;                 // the m x m lower triangle
     int64_t m, k0, k1, k2;          // panel k = [k0, k1), panel k+1 = [k1, k2)
-    int nstrip;                     // 64-row strips of panel k+1 in rows [k2, m)
+    int nstrip;                     // 32-row strips of panel k+1 in rows [k2, m)
     int64_t nbulk;                  // lower 64 x 64 tiles of A(k2:m, k2:m)
     int32_t *info;                  // failure index (1-based, global); also the abort word
     int64_t base;                   // global index of V's first row
@@ -57,38 +58,80 @@ __device__ __forceinline__ uint64_t step_globaltimer()
     return t;
 }
 
-// acc(64 x 64, 4 x 4 per thread) = P_rows(64 x w) P_cols(64 x w)^T with
+// The block of the C tile a thread owns: TM rows x 4 columns at row block
+// ry, column block cx.  The usual map is cx = tid % 16, ry = tid / 16; for
+// the diagonal tile (`lower`, TM = 4) threads 0 .. 135 take the 136 blocks
+// with ry >= cx in order and the others own none, so warps 5 .. 7 issue no
+// multiply-adds on the factorization's critical path.
+template <int TM>
+struct Owner {
+    int ry, cx;
+    bool active;
+    __device__ __forceinline__ Owner(bool lower)
+    {
+        const int tid = threadIdx.x;
+        if (!lower) {
+            cx = tid % 16;
+            ry = tid / 16;
+            active = true;
+        } else {
+            int r = (int)((sqrtf(8.f * (float)tid + 1.f) - 1.f) * 0.5f);
+            while ((r + 1) * (r + 2) / 2 <= tid) ++r;
+            while (r * (r + 1) / 2 > tid) --r;
+            ry = r;
+            cx = tid - r * (r + 1) / 2;
+            active = tid < 136;
+        }
+    }
+};
+
+// acc(16 TM x 64: TM x 4 per thread) = P_rows(16 TM x w) P_cols(64 x w)^T with
 // P_rows(i, k) = V(r0 + i, k0 + k) for i < nr (zero beyond), likewise
 // P_cols with c0 / nc.  w <= 64.  Register-staged, double-buffered K steps
 // of 16 read along V's unit stride.
+template <int TM>
 __device__ __forceinline__ void panel_product(const StepArgs &a, Smem &sm, int64_t r0, int nr,
-                                              int64_t c0, int nc, int w, double (&acc)[4][4])
+                                              int64_t c0, int nc, int w, const Owner<TM> &o,
+                                              double (&acc)[TM][4])
 {
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    constexpr int ROWS = 16 * TM;
+    const int tid = threadIdx.x;
     const bool rowfast = a.V.rs == 1;
     const View<double> Pr = a.V.sub(r0, a.k0), Pc = a.V.sub(c0, a.k0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    double ra[4], rb[4];
+    double ra[TM], rb[4];
     auto load = [&](int kb) {
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+            int i, k;
+            if (rowfast) { i = tid % ROWS; k = kb + tid / ROWS + (kTh / ROWS) * q; }
+            else { k = kb + tid % kBk; i = tid / kBk + 16 * q; }
+            ra[q] = (i < nr && k < w) ? Pr(i, k) : 0.0;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int i, k;
             if (rowfast) { i = tid % kT; k = kb + tid / kT + 4 * q; }
             else { k = kb + tid % kBk; i = tid / kBk + 16 * q; }
-            ra[q] = (i < nr && k < w) ? Pr(i, k) : 0.0;
             rb[q] = (i < nc && k < w) ? Pc(i, k) : 0.0;
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
+        for (int q = 0; q < TM; ++q) {
+            int i, k;
+            if (rowfast) { i = tid % ROWS; k = tid / ROWS + (kTh / ROWS) * q; }
+            else { k = tid % kBk; i = tid / kBk + 16 * q; }
+            sm.As[buf][k][i] = ra[q];
+        }
+#pragma unroll
         for (int q = 0; q < 4; ++q) {
             int i, k;
             if (rowfast) { i = tid % kT; k = tid / kT + 4 * q; }
             else { k = tid % kBk; i = tid / kBk + 16 * q; }
-            sm.As[buf][k][i] = ra[q];
             sm.Bs[buf][k][i] = rb[q];
         }
     };
@@ -99,34 +142,42 @@ __device__ __forceinline__ void panel_product(const StepArgs &a, Smem &sm, int64
         store(buf);
         __syncthreads();
         if (s + 1 < nsteps) load((s + 1) * kBk);
+        if (o.active) {
 #pragma unroll
-        for (int kk = 0; kk < kBk; ++kk) {
-            const double2 a01 = *reinterpret_cast<const double2 *>(&sm.As[buf][kk][ty * 4]);
-            const double2 a23 = *reinterpret_cast<const double2 *>(&sm.As[buf][kk][ty * 4 + 2]);
-            const double2 b01 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][tx * 4]);
-            const double2 b23 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][tx * 4 + 2]);
-            const double av[4] = {a01.x, a01.y, a23.x, a23.y}, bv[4] = {b01.x, b01.y, b23.x, b23.y};
+            for (int kk = 0; kk < kBk; ++kk) {
+                double av[TM];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < TM; i += 2) {
+                    const double2 t2 = *reinterpret_cast<const double2 *>(&sm.As[buf][kk][o.ry * TM + i]);
+                    av[i] = t2.x;
+                    av[i + 1] = t2.y;
+                }
+                const double2 b01 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][o.cx * 4]);
+                const double2 b23 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][o.cx * 4 + 2]);
+                const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            }
         }
     }
     __syncthreads();   // staging buffers free for the next product
 }
 
-// T = V(r0.., c0..) - acc for the nr x nc tile (lower part only when `lower`),
-// into shared memory; entries outside are zero.
+// T = V(r0.., c0..) - acc for the owned blocks of the nr x nc tile (lower
+// part only when `lower`), into shared memory; entries outside are zero.
+template <int TM>
 __device__ __forceinline__ void updated_tile_to_smem(const StepArgs &a, Smem &sm, int64_t r0, int nr,
                                                      int64_t c0, int nc, bool lower,
-                                                     const double (&acc)[4][4])
+                                                     const Owner<TM> &o, const double (&acc)[TM][4])
 {
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    if (!o.active) return;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int r = ty * 4 + i, c = tx * 4 + j;
+            const int r = o.ry * TM + i, c = o.cx * 4 + j;
             const bool in = r < nr && c < nc && (!lower || c <= r);
             sm.T[r][c] = in ? a.V(r0 + r, c0 + c) - acc[i][j] : 0.0;
         }
@@ -143,13 +194,15 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
     const int64_t t = sm.ticket;
     const int w = (int)(a.k1 - a.k0);            // panel k width
     const int wn = (int)(a.k2 - a.k1);           // panel k+1 width
-    double acc[4][4];
     int32_t *flag = a.sync + 1;
 
     if (t == 0) {
-        // ---- diagonal tile of panel k+1: update, then unblocked Cholesky
-        panel_product(a, sm, a.k1, wn, a.k1, wn, w, acc);
-        updated_tile_to_smem(a, sm, a.k1, wn, a.k1, wn, true, acc);
+        // ---- diagonal tile of panel k+1: update (its lower blocks only), then
+        // unblocked Cholesky
+        const Owner<4> o(true);
+        double acc[4][4];
+        panel_product<4>(a, sm, a.k1, wn, a.k1, wn, w, o, acc);
+        updated_tile_to_smem<4>(a, sm, a.k1, wn, a.k1, wn, true, o, acc);
         __syncthreads();
         const int tx = tid % 16, ty = tid / 16;
         int fail = -1;
@@ -192,11 +245,13 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
     }
 
     if (t <= a.nstrip) {
-        // ---- a 64-row strip of panel k+1: update, wait for the diagonal tile, solve
-        const int64_t r0 = a.k2 + (t - 1) * kT;
-        const int nr = (int)(a.m - r0 < kT ? a.m - r0 : kT);
-        panel_product(a, sm, r0, nr, a.k1, wn, w, acc);
-        updated_tile_to_smem(a, sm, r0, nr, a.k1, wn, false, acc);
+        // ---- a 32-row strip of panel k+1: update, wait for the diagonal tile, solve
+        const int64_t r0 = a.k2 + (t - 1) * kStrip;
+        const int nr = (int)(a.m - r0 < kStrip ? a.m - r0 : kStrip);
+        const Owner<2> o(false);
+        double acc[2][4];
+        panel_product<2>(a, sm, r0, nr, a.k1, wn, w, o, acc);
+        updated_tile_to_smem<2>(a, sm, r0, nr, a.k1, wn, false, o, acc);
         if (tid == 0) {
             const uint64_t t0 = step_globaltimer();
             int f = 0;
@@ -231,13 +286,14 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
         if (tid < wn) sm.rinv[tid] = 1.0 / sm.Ld[tid][tid];
         __syncthreads();
         // X L_D^T = T, columns in increasing order; rows are independent
-        const int row = tid % kT, grp = tid / kT;
+        constexpr int kGroups = kTh / kStrip;
+        const int row = tid % kStrip, grp = tid / kStrip;
         double *xr = sm.T[row];
         for (int j = 0; j < wn; ++j) {
             if (grp == 0) xr[j] *= sm.rinv[j];
             __syncthreads();
             const double xj = xr[j];
-            for (int c = j + 1 + grp; c < wn; c += 4) xr[c] -= xj * sm.Ld[c][j];
+            for (int c = j + 1 + grp; c < wn; c += kGroups) xr[c] -= xj * sm.Ld[c][j];
             __syncthreads();
         }
         for (int e = tid; e < kT * kT; e += kTh) {
@@ -256,7 +312,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
     const int64_t tj = b - ti * (ti + 1) / 2;
     const int64_t r0 = a.k2 + ti * kT, c0 = a.k2 + tj * kT;
     const int nr = (int)(a.m - r0 < kT ? a.m - r0 : kT), nc = (int)(a.m - c0 < kT ? a.m - c0 : kT);
-    panel_product(a, sm, r0, nr, c0, nc, w, acc);
+    const Owner<4> o(false);
+    double acc[4][4];
+    panel_product<4>(a, sm, r0, nr, c0, nc, w, o, acc);
     const int tx = tid % 16, ty = tid / 16;
     double cin[4][4];
 #pragma unroll
@@ -291,7 +349,8 @@ cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, i
     if (k1 >= m) return cudaSuccess;                  // no next panel
     const int64_t k2 = k1 + kT < m ? k1 + kT : m;
     const int64_t rest = (m - k2 + kT - 1) / kT;      // row tiles of A(k2:m, k2:m)
-    StepArgs a{V, m, k0, k1, k2, (int)rest, rest * (rest + 1) / 2, info, base, sync};
+    const int64_t strips = (m - k2 + kStrip - 1) / kStrip;
+    StepArgs a{V, m, k0, k1, k2, (int)strips, rest * (rest + 1) / 2, info, base, sync};
     const int64_t grid = 1 + a.nstrip + a.nbulk;
     if (grid > INT32_MAX) return cudaErrorInvalidValue;
     const int smem = (int)sizeof(Smem);
