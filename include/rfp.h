@@ -98,6 +98,13 @@ int rfp_sunpack(char transr, char uplo, int64_t n, const float *arf, float *A,
  * triangular solve of S, symmetric rank-n1 update of T2, Cholesky of T2.
  * *info (device) is set to 0, or to j > 0 when the leading minor of order j
  * is not positive definite (a pivot <= 0 or NaN); arf is then unspecified.
+ * FP64 scratch: the triangle factorizations run one launch per 64-column
+ * panel step (trailing update and the next panel's factorization together)
+ * and step 2 runs as one launch; together they take 8 bytes per panel step
+ * plus 8 bytes per 16 columns of S of stream-ordered scratch from a
+ * library-private memory pool, returned on `stream` when the call's work is
+ * done.  While `stream` is being captured into a CUDA graph, the routine
+ * runs its multi-launch form instead, which takes none.
  * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
  */
 int rfp_dpftrf(char transr, char uplo, int64_t n, double *arf, int32_t *info,
@@ -111,6 +118,10 @@ int rfp_spftrf(char transr, char uplo, int64_t n, float *arf, int32_t *info,
  * max(1,n)) and is overwritten by X.  Forward: L11 Y1 = B1, B2 -= L21 Y1,
  * L22 Y2 = B2; backward: L22^T X2 = Y2, Y1 -= L21^T X2, L11^T X1 = Y1, where
  * B1 is rows [0, n1) of B.
+ * FP64: each direction is one launch over the whole factor; it takes
+ * 8 + 4 ceil(nrhs / 16) bytes of stream-ordered scratch from the same pool
+ * as rfp_dpftrf (the multi-launch form under graph capture).  The FP32
+ * variant uses the multi-launch form always.
  * Arguments: 1 transr, 2 uplo, 3 n, 4 nrhs, 5 arf, 6 B, 7 ldb, 8 stream.
  */
 int rfp_dpftrs(char transr, char uplo, int64_t n, int64_t nrhs, const double *arf,
@@ -123,6 +134,8 @@ int rfp_spftrs(char transr, char uplo, int64_t n, int64_t nrhs, const float *arf
  * arf with the UPLO triangle of A^{-1} = W^T W (W = L^{-1}), same layout.
  * *info (device) is set to 0, or to j > 0 when the j-th diagonal entry of the
  * factor is exactly zero; arf is then unspecified.
+ * FP64: the three solves with the factor (W21 and S <- L22^-T W21) run as
+ * one launch each, with scratch as for rfp_dpftrs.
  * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
  */
 int rfp_dpftri(char transr, char uplo, int64_t n, double *arf, int32_t *info,
