@@ -100,10 +100,9 @@ int rfp_sunpack(char transr, char uplo, int64_t n, const float *arf, float *A,
  * is not positive definite (a pivot <= 0 or NaN); arf is then unspecified.
  * FP64 scratch: the triangle factorizations run one launch per 64-column
  * panel step (trailing update and the next panel's factorization together)
- * and step 2 runs as one launch; together they take 8 bytes per panel step
- * plus 8 bytes per 16 columns of S of stream-ordered scratch from a
- * library-private memory pool, returned on `stream` when the call's work is
- * done.  While `stream` is being captured into a CUDA graph, the routine
+ * and step 2 runs as one launch; they take stream-ordered scratch from a
+ * library-private memory pool (8 bytes per panel step, and 8 + 4 ceil(n2 /
+ * 16) bytes for step 2), returned on `stream` when the call's work is done.  While `stream` is being captured into a CUDA graph, the routine
  * runs its multi-launch form instead, which takes none.
  * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
  */
