@@ -34,7 +34,8 @@ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ?
 // Row/column of the t-th tile of a lower-triangular tile grid (row-major).
 __device__ __forceinline__ void tri_tile(int64_t t, int64_t &ti, int64_t &tj)
 {
-    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    // single-precision guess (the FP64 pipe is narrow), corrected below
+    int64_t r = (int64_t)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
     while ((r + 1) * (r + 2) / 2 <= t) ++r;
     while (r * (r + 1) / 2 > t) --r;
     ti = r;

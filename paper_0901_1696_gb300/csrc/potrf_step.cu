@@ -8,7 +8,7 @@
 // rows below solved against that tile (TRSM).  Launch k does all of this:
 //   ticket 0             the diagonal tile of panel k+1: its update, then
 //                        POTRF in shared memory; writes L and raises a flag;
-//   tickets 1 .. P       32-row strips of panel k+1 below the diagonal: the
+//   tickets 1 .. P       32- or 64-row strips of panel k+1 below the diagonal: the
 //                        update, then (once the flag is up) the solve
 //                        X L_D^T = strip with the new diagonal tile;
 //   the other tickets    64 x 64 lower tiles of A(k2:m, k2:m): the update.
@@ -25,7 +25,10 @@ namespace rfp {
 namespace {
 
 constexpr int kT = 64;              // tile / panel width
-constexpr int kStrip = 32;          // rows of a panel strip task
+// Rows of a panel strip task: 32 for triangles up to kSmallStrips (their
+// factorization is bound by the diagonal chain, which shorter strips
+// shorten), 64 beyond (fewer, more efficient tasks beside the bulk update).
+constexpr int64_t kSmallStrips = 2048;
 constexpr int kTh = 256;            // threads per CTA
 constexpr int kBk = 16;             // K step of the tile update
 constexpr int kSLd = kT + 2;        // staging rows (doubles; 16-byte aligned)
@@ -35,7 +38,7 @@ constexpr uint64_t kStepWaitNs = 2000000000ull;
 struct StepArgs {
     View<double> V;                 // the m x m lower triangle
     int64_t m, k0, k1, k2;          // panel k = [k0, k1), panel k+1 = [k1, k2)
-    int nstrip;                     // 32-row strips of panel k+1 in rows [k2, m)
+    int nstrip;                     // strips of panel k+1 in rows [k2, m)
     int64_t nbulk;                  // lower 64 x 64 tiles of A(k2:m, k2:m)
     int32_t *info;                  // failure index (1-based, global); also the abort word
     int64_t base;                   // global index of V's first row
@@ -183,8 +186,10 @@ __device__ __forceinline__ void updated_tile_to_smem(const StepArgs &a, Smem &sm
         }
 }
 
+template <int STRIP>
 __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
 {
+    constexpr int STM = STRIP / 16;   // rows per thread in a strip's update
     extern __shared__ __align__(16) unsigned char step_smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(step_smem_raw);
     if (*a.info != 0) return;   // an earlier panel failed (written before this launch)
@@ -245,13 +250,13 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
     }
 
     if (t <= a.nstrip) {
-        // ---- a 32-row strip of panel k+1: update, wait for the diagonal tile, solve
-        const int64_t r0 = a.k2 + (t - 1) * kStrip;
-        const int nr = (int)(a.m - r0 < kStrip ? a.m - r0 : kStrip);
-        const Owner<2> o(false);
-        double acc[2][4];
-        panel_product<2>(a, sm, r0, nr, a.k1, wn, w, o, acc);
-        updated_tile_to_smem<2>(a, sm, r0, nr, a.k1, wn, false, o, acc);
+        // ---- a STRIP-row strip of panel k+1: update, wait for the diagonal tile, solve
+        const int64_t r0 = a.k2 + (t - 1) * STRIP;
+        const int nr = (int)(a.m - r0 < STRIP ? a.m - r0 : STRIP);
+        const Owner<STM> o(false);
+        double acc[STM][4];
+        panel_product<STM>(a, sm, r0, nr, a.k1, wn, w, o, acc);
+        updated_tile_to_smem<STM>(a, sm, r0, nr, a.k1, wn, false, o, acc);
         if (tid == 0) {
             const uint64_t t0 = step_globaltimer();
             int f = 0;
@@ -286,8 +291,8 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
         if (tid < wn) sm.rinv[tid] = 1.0 / sm.Ld[tid][tid];
         __syncthreads();
         // X L_D^T = T, columns in increasing order; rows are independent
-        constexpr int kGroups = kTh / kStrip;
-        const int row = tid % kStrip, grp = tid / kStrip;
+        constexpr int kGroups = kTh / STRIP;
+        const int row = tid % STRIP, grp = tid / STRIP;
         double *xr = sm.T[row];
         for (int j = 0; j < wn; ++j) {
             if (grp == 0) xr[j] *= sm.rinv[j];
@@ -306,7 +311,8 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
 
     // ---- a lower 64 x 64 tile of A(k2:m, k2:m): the update only
     const int64_t b = t - 1 - a.nstrip;
-    int64_t ti = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    // single-precision guess (the FP64 pipe is narrow), corrected below
+    int64_t ti = (int64_t)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
     while ((ti + 1) * (ti + 2) / 2 <= b) ++ti;
     while (ti * (ti + 1) / 2 > b) --ti;
     const int64_t tj = b - ti * (ti + 1) / 2;
@@ -349,15 +355,23 @@ cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, i
     if (k1 >= m) return cudaSuccess;                  // no next panel
     const int64_t k2 = k1 + kT < m ? k1 + kT : m;
     const int64_t rest = (m - k2 + kT - 1) / kT;      // row tiles of A(k2:m, k2:m)
-    const int64_t strips = (m - k2 + kStrip - 1) / kStrip;
+    const int64_t strip = m <= kSmallStrips ? 32 : 64;
+    const int64_t strips = (m - k2 + strip - 1) / strip;
     StepArgs a{V, m, k0, k1, k2, (int)strips, rest * (rest + 1) / 2, info, base, sync};
     const int64_t grid = 1 + a.nstrip + a.nbulk;
     if (grid > INT32_MAX) return cudaErrorInvalidValue;
     const int smem = (int)sizeof(Smem);
-    cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem);
-    if (e != cudaSuccess) return e;
-    potrf_step_kernel<<<(unsigned)grid, kTh, smem, st>>>(a);
+    if (strip == 32) {
+        cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel<32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        potrf_step_kernel<32><<<(unsigned)grid, kTh, smem, st>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel<64>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        potrf_step_kernel<64><<<(unsigned)grid, kTh, smem, st>>>(a);
+    }
     note_launch();
     return cudaGetLastError();
 }

@@ -236,7 +236,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 __device__ __forceinline__ void tile_coords(const Args &a, int64_t t, int64_t &tm, int64_t &tn)
 {
     if (a.lower_tiles) {   // row-major lower-triangular tile list
-        int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        // single-precision guess (the FP64 pipe is narrow), corrected below
+        int64_t r = (int64_t)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
         while ((r + 1) * (r + 2) / 2 <= t) ++r;
         while (r * (r + 1) / 2 > t) --r;
         tm = r;

@@ -458,7 +458,7 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
 }
 
 // potrf_step: one ordered launch (ticket order: the diagonal tile of panel
-// k+1, its 32-row strips, then the lower tiles of A(k2:m, k2:m)) with the
+// k+1, its 32-row (m <= 2048) or 64-row strips, then the lower tiles of A(k2:m, k2:m)) with the
 // kernel's own tile decomposition.  Besides the bounds checks, every element
 // one task writes is recorded, and a read of it by another task is a
 // violation unless it is the new diagonal tile read by a strip (which the
@@ -475,7 +475,7 @@ cudaError_t potrf_step(cudaStream_t, View<double> V, int64_t m, int64_t k0, int3
     const int64_t T = 64, k1 = std::min(k0 + T, m);
     if (k1 >= m) return cudaSuccess;
     const int64_t k2 = std::min(k1 + T, m), w = k1 - k0, wn = k2 - k1;
-    const int64_t S = 32;                            // rows per strip task
+    const int64_t S = m <= 2048 ? 32 : 64;           // rows per strip task
     const int64_t rest = (m - k2 + T - 1) / T, nstrip = (m - k2 + S - 1) / S, nbulk = rest * (rest + 1) / 2;
     Launch L;
     L.ordered = true;
