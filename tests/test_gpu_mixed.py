@@ -64,10 +64,8 @@ def test_mixed_conditioning(prec, kappa):
     X, st = solve_mixed("N", "L", A, B, PRECS[prec], max_iter=40)
     assert st["tc_error"] == 0
     bwd = oracle.solve_backward_error(A, X, B) if st["info"] == 0 else np.inf
-    # bf16x8 keeps every product of the three-part split above 2^-32: its
-    # update error is the split's own 2^-24 remainder, as for FP32
-    u_f = {"fp32": 2.0 ** -24, "tf32x3": 2.0 ** -22, "bf16x6": 2.0 ** -22, "bf16x8": 2.0 ** -24,
-           "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
+    u_f = {"fp32": 2.0 ** -24, "tf32x3": 2.0 ** -22, "bf16x6": 2.0 ** -22, "tf32": 2.0 ** -11,
+           "bf16": 2.0 ** -8}[prec]
     if st["converged"]:
         assert st["backward_error"] <= 1e-15 and bwd <= 1e-14, (st, bwd)
     if kappa * u_f * 100 < 1:         # well inside the convergence condition
