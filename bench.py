@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--mixed-n", type=int, default=32768)
     p.add_argument("--mixed-nrhs", type=int, default=64)
     p.add_argument("--kappas", default="1e2,1e4,1e6")
-    p.add_argument("--precs", default="fp32,tf32x3,bf16x6,bf16x8,tf32,bf16")
+    p.add_argument("--precs", default="fp32,tf32x3,bf16x6,tf32,bf16")
     p.add_argument("--max-iter", type=int, default=30, help="refinement steps (mixed mode)")
     p.add_argument("--batch", type=int, default=4096, help="batched mode: matrices per batch")
     p.add_argument("--serve-requests", type=int, default=1000,
@@ -378,7 +378,7 @@ def other_legs(args, lib, dev, stream):
     """The other configurations of the metric, each after the main timed
     region (its own clocks and timing; nothing here enters `value`):
       c1: n = 1001 latencies of PFTRF / PFTRS / PFTRI;
-      mixed: n = 32768, nrhs = 64, kappa = 1e6, split-BF16 (8 and 6 products) and split-TF32
+      mixed: n = 32768, nrhs = 64, kappa = 1e6, split-BF16 and split-TF32
              mixed-precision solves against FP64 PFTRF + PFTRS on the same
              matrix;
       batched: 4096 uneven matrices (n ~ U{32..512}), FP64 and FP32;
@@ -395,8 +395,8 @@ def other_legs(args, lib, dev, stream):
             elif leg == "mixed":
                 sampler = ClockSampler(0)
                 sampler.start()
-                fp64, res = mixed_leg(lib, dev, stream, 32768, 64, [1e6],
-                                      ["bf16x8", "bf16x6", "tf32x3"], 30, True)
+                fp64, res = mixed_leg(lib, dev, stream, 32768, 64, [1e6], ["bf16x6", "tf32x3"],
+                                      30, True)
                 out["mixed"] = {"workload": "n=32768, nrhs=64, kappa=1e6, A = Q diag(lam) Q^T "
                                             "(random butterfly Q, lam log-uniform on [1, 1e6])",
                                 "fp64": fp64, "results": res, "clocks": sampler.stop()}
@@ -572,8 +572,7 @@ def mixed_leg(lib, dev, stream, n, nrhs, kappas, precs_wanted, max_iter, fp64_re
     from paper_0901_1696_gb300 import binding as rfp
     from paper_0901_1696_gb300.flops import pftrf_flops, pftrs_flops
     precs = {"fp32": rfp.RFP_PREC_FP32, "tf32": rfp.RFP_PREC_TF32, "bf16": rfp.RFP_PREC_BF16,
-             "tf32x3": rfp.RFP_PREC_TF32X3, "bf16x6": rfp.RFP_PREC_BF16X6,
-             "bf16x8": rfp.RFP_PREC_BF16X8}
+             "tf32x3": rfp.RFP_PREC_TF32X3, "bf16x6": rfp.RFP_PREC_BF16X6}
     results, fp64 = [], []
     Bh = gen.rhs(n, nrhs, seed=3)
     dB = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev)

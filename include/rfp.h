@@ -182,11 +182,7 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
  *        each panel value is split into three BF16 parts (hi + mid + lo,
  *        Henry, Tang and Heinecke's bfloat16 splitting) and the update sums
  *        the six products hi hi, hi mid, mid hi, mid mid, hi lo, lo hi (panel
- *        buffer twelve times a BF16 panel);
- *   prec RFP_PREC_BF16X8: as RFP_PREC_BF16X6 with the two products mid lo
- *        and lo mid added (eight in all): every product above 2^-32 of the
- *        split, so the update's error is that of the split itself (panel
- *        buffer sixteen times a BF16 panel).
+ *        buffer twelve times a BF16 panel).
  * Refinement: X = 0, R = B, then up to max_iter times D = (L L^T)^{-1} R in
  * FP32, X += D in FP64, R = B - A X in FP64 from arf; it stops as soon as
  * max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol, decided on
@@ -205,7 +201,6 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
 #define RFP_PREC_FP32 2
 #define RFP_PREC_TF32X3 3
 #define RFP_PREC_BF16X6 4
-#define RFP_PREC_BF16X8 5
 typedef struct rfp_mixed_status {
     int32_t info, iterations, converged, tc_error;
     double backward_error;

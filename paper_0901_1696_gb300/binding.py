@@ -58,7 +58,6 @@ for _x, _f in (("d", ctypes.c_double), ("s", ctypes.c_float)):
         f"rfp_{_x}lansf": [_c, _c, _c, _i64, _p, _p, _p, _p],
     })
 RFP_PREC_BF16, RFP_PREC_TF32, RFP_PREC_FP32, RFP_PREC_TF32X3, RFP_PREC_BF16X6 = 0, 1, 2, 3, 4
-RFP_PREC_BF16X8 = 5
 
 
 class RfpMixedStatus(ctypes.Structure):

@@ -115,7 +115,7 @@ int mixed_check_args(char transr, char uplo, int64_t n, int64_t nrhs, const doub
     if (!valid_uplo(uplo)) return -2;
     if (n < 0 || n > kMaxN || n > (int64_t(1) << 31) - 1) return -3;
     if (nrhs < 0 || nrhs > (int64_t(1) << 31) - 1) return -4;
-    if (prec < RFP_PREC_BF16 || prec > RFP_PREC_BF16X8) return -10;
+    if (prec < RFP_PREC_BF16 || prec > RFP_PREC_BF16X6) return -10;
     if (max_iter < 0) return -11;
     if (!(tol >= 0.0)) return -12;
     if (!status || !aligned(status)) return -15;
@@ -413,7 +413,7 @@ int rfp_ssyrk_tc(char uplo, int64_t n, int64_t k, float alpha, const void *A, in
 size_t rfp_dpfsv_mixed_workspace(int64_t n, int64_t nrhs, int prec)
 {
     if (n <= 0 || nrhs <= 0 || n > kMaxN) return 0;
-    if (prec < RFP_PREC_BF16 || prec > RFP_PREC_BF16X8) return 0;
+    if (prec < RFP_PREC_BF16 || prec > RFP_PREC_BF16X6) return 0;
     return rfp::mixed_workspace_bytes(n, nrhs, prec);
 }
 

@@ -12,8 +12,7 @@
 //        RFP_PREC_TF32X3: the same kernel on a split panel P = hi + lo (both
 //        TF32), C -= hi hi^T + lo hi^T + hi lo^T (three products, one launch);
 //        RFP_PREC_BF16X6: P = hi + mid + lo (all BF16), the six products
-//        above 2^-24 in one kind::f16 launch; RFP_PREC_BF16X8: also mid lo
-//        and lo mid (every product above 2^-32);
+//        above 2^-24 in one kind::f16 launch;
 //      the diagonal blocks and the panel solves stay in FP32.
 //   3. X = 0, R = B; repeat: D = (L L^T)^{-1} fl32(R) (FP32 block solves of
 //      Section 4, one launch each, the 128-wide diagonal blocks applied as
@@ -30,10 +29,7 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 int64_t ldw_for(int64_t n) { return (n + 31) / 32 * 32; }
-size_t panel_elem(int prec)
-{
-    return (prec == RFP_PREC_BF16 || prec == RFP_PREC_BF16X6 || prec == RFP_PREC_BF16X8) ? 2 : 4;
-}
+size_t panel_elem(int prec) { return (prec == RFP_PREC_BF16 || prec == RFP_PREC_BF16X6) ? 2 : 4; }
 size_t inv_elems(int64_t n) { return (size_t)((n + kInvBlock - 1) / kInvBlock) * kInvBlock * kInvBlock; }
 }  // namespace
 
@@ -140,16 +136,14 @@ static cudaError_t factor_panels(cudaStream_t st, View<float> W, int64_t n, int 
         } else if (prec == RFP_PREC_TF32X3) {
             RFP_TRY(split_tf32(st, X, static_cast<float *>(w.P), m, nb, kMixedPanel, info));
         } else {
-            const int np = prec == RFP_PREC_BF16X8 ? 8 : 6;
-            __nv_bfloat16 *QA = static_cast<__nv_bfloat16 *>(w.P), *QB = QA + (size_t)m * np * kMixedPanel;
-            RFP_TRY(split_bf16x3(st, X, QA, QB, m, nb, kMixedPanel, np, info));
+            __nv_bfloat16 *QA = static_cast<__nv_bfloat16 *>(w.P), *QB = QA + (size_t)m * 6 * kMixedPanel;
+            RFP_TRY(split_bf16x3(st, X, QA, QB, m, nb, kMixedPanel, info));
         }
-        if (prec == RFP_PREC_BF16X6 || prec == RFP_PREC_BF16X8) {
-            const int64_t np = prec == RFP_PREC_BF16X8 ? 8 : 6;
+        if (prec == RFP_PREC_BF16X6) {
             const __nv_bfloat16 *QA = static_cast<const __nv_bfloat16 *>(w.P),
-                                *QB = QA + (size_t)m * np * kMixedPanel;
-            RFP_TRY(tc_gemm_nt(st, RFP_PREC_BF16, QA, m, np * kMixedPanel, 0, QB, m, np * kMixedPanel,
-                               0, W.sub(j1, j1), m, m, np * kMixedPanel, -1.0f, 1.0f, MASK_LOWER,
+                                *QB = QA + (size_t)m * 6 * kMixedPanel;
+            RFP_TRY(tc_gemm_nt(st, RFP_PREC_BF16, QA, m, 6 * kMixedPanel, 0, QB, m, 6 * kMixedPanel, 0,
+                               W.sub(j1, j1), m, m, 6 * kMixedPanel, -1.0f, 1.0f, MASK_LOWER,
                                w.tc_err));
         } else if (prec == RFP_PREC_TF32X3) {
             // A = segments 1..3 = [hi | lo | hi], B = segments 0..2 = [hi | hi | lo]

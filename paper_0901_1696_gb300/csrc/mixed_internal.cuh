@@ -24,12 +24,10 @@ cudaError_t convert(cudaStream_t st, View<Ts> src, View<Td> dst, int64_t rows, i
 // FP32 block src, hi = x truncated to TF32, lo = x - hi.
 cudaError_t split_tf32(cudaStream_t st, View<float> src, float *Q, int64_t rows, int64_t cols,
                        int64_t seg, const int32_t *stop);
-// QA / QB rows of `products` (6 or 8) K-segments (width seg) of the three-way
-// BF16 split of the rows x cols FP32 block src: QA [hi|hi|mid|mid|hi|lo],
-// QB [hi|mid|hi|mid|lo|hi], then (8) QA [..|mid|lo], QB [..|lo|mid].
+// QA / QB rows of six K-segments (width seg) of the three-way BF16 split of
+// the rows x cols FP32 block src: QA [hi|hi|mid|mid|hi|lo], QB [hi|mid|hi|mid|lo|hi].
 cudaError_t split_bf16x3(cudaStream_t st, View<float> src, __nv_bfloat16 *QA, __nv_bfloat16 *QB,
-                         int64_t rows, int64_t cols, int64_t seg, int products,
-                         const int32_t *stop);
+                         int64_t rows, int64_t cols, int64_t seg, const int32_t *stop);
 cudaError_t add_correction(cudaStream_t st, View<double> X, View<float> D, int64_t n, int64_t nrhs,
                            const int32_t *stop);
 cudaError_t fill(cudaStream_t st, View<double> X, int64_t n, int64_t nrhs, double v);
@@ -72,8 +70,7 @@ constexpr int64_t kMixedPanel = 512;   // panel width of the tensor-core factori
 inline int64_t panel_cols(int prec)
 {
     return prec == RFP_PREC_TF32X3 ? 4 * kMixedPanel
-                                   : (prec == RFP_PREC_BF16X6 ? 12 * kMixedPanel
-                                      : (prec == RFP_PREC_BF16X8 ? 16 * kMixedPanel : kMixedPanel));
+                                   : (prec == RFP_PREC_BF16X6 ? 12 * kMixedPanel : kMixedPanel);
 }
 
 size_t mixed_workspace_bytes(int64_t n, int64_t nrhs, int prec);

@@ -132,7 +132,7 @@ cudaError_t split_tf32(cudaStream_t st, View<float> src, float *Q, int64_t rows,
 // mid mid^T, hi lo^T, lo hi^T; the dropped ones are below 2^-24 |x y|.
 __global__ void __launch_bounds__(256) split_bf16x3_kernel(View<float> src, __nv_bfloat16 *QA,
                                                            __nv_bfloat16 *QB, int64_t rows,
-                                                           int64_t cols, int64_t seg, int products,
+                                                           int64_t cols, int64_t seg,
                                                            const int32_t *stop)
 {
     __shared__ float tile[kCvtTile][kCvtTile + 1];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) split_bf16x3_kernel(View<float> src, __nv
         if (r0 + ti < rows && c0 + tj < cols) tile[ti][tj] = src(r0 + ti, c0 + tj);
     }
     __syncthreads();
-    const int64_t pitch = products * seg;
+    const int64_t pitch = 6 * seg;
 #pragma unroll
     for (int q = 0; q < kCvtTile / 8; ++q) {
         const int ti = slow0 + 8 * q, tj = fast;
@@ -165,20 +165,16 @@ __global__ void __launch_bounds__(256) split_bf16x3_kernel(View<float> src, __nv
             a[3 * seg] = mid; b[3 * seg] = mid;
             a[4 * seg] = hi;  b[4 * seg] = lo;
             a[5 * seg] = lo;  b[5 * seg] = hi;
-            if (products == 8) {
-                a[6 * seg] = mid; b[6 * seg] = lo;
-                a[7 * seg] = lo;  b[7 * seg] = mid;
-            }
         }
     }
 }
 
 cudaError_t split_bf16x3(cudaStream_t st, View<float> src, __nv_bfloat16 *QA, __nv_bfloat16 *QB,
-                         int64_t rows, int64_t cols, int64_t seg, int products, const int32_t *stop)
+                         int64_t rows, int64_t cols, int64_t seg, const int32_t *stop)
 {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     dim3 grid((unsigned)((cols + kCvtTile - 1) / kCvtTile), (unsigned)((rows + kCvtTile - 1) / kCvtTile));
-    split_bf16x3_kernel<<<grid, 256, 0, st>>>(src, QA, QB, rows, cols, seg, products, stop);
+    split_bf16x3_kernel<<<grid, 256, 0, st>>>(src, QA, QB, rows, cols, seg, stop);
     note_launch();
     return cudaGetLastError();
 }

@@ -957,7 +957,7 @@ cudaError_t split_tf32(cudaStream_t, View<float> src, float *Q, int64_t rows, in
 }
 
 cudaError_t split_bf16x3(cudaStream_t, View<float> src, __nv_bfloat16 *QA, __nv_bfloat16 *QB,
-                         int64_t rows, int64_t cols, int64_t seg, int products, const int32_t *stop)
+                         int64_t rows, int64_t cols, int64_t seg, const int32_t *stop)
 {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     Launch L;
@@ -974,11 +974,9 @@ cudaError_t split_bf16x3(cudaStream_t, View<float> src, __nv_bfloat16 *QA, __nv_
                     const float r1 = x - hi;
                     const float mid = bf16_round(r1, &bm);
                     bf16_round(r1 - mid, &bl);
-                    const uint16_t a[8] = {bh, bh, bm, bm, bh, bl, bm, bl},
-                                   b[8] = {bh, bm, bh, bm, bl, bh, bl, bm};
-                    for (int q = 0; q < products; ++q) {
-                        __nv_bfloat16 *pa = QA + r * products * seg + q * seg + k,
-                                      *pb = QB + r * products * seg + q * seg + k;
+                    const uint16_t a[6] = {bh, bh, bm, bm, bh, bl}, b[6] = {bh, bm, bh, bm, bl, bh};
+                    for (int q = 0; q < 6; ++q) {
+                        __nv_bfloat16 *pa = QA + r * 6 * seg + q * seg + k, *pb = QB + r * 6 * seg + q * seg + k;
                         L.wr_any(pa, 2);
                         L.pend_b.push_back({pa, a[q]});
                         L.wr_any(pb, 2);

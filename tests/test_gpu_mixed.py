@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 rfp = pytest.importorskip("paper_0901_1696_gb300.binding")
 
-PRECS = {"fp32": 2, "tf32": 1, "bf16": 0, "tf32x3": 3, "bf16x6": 4, "bf16x8": 5}
+PRECS = {"fp32": 2, "tf32": 1, "bf16": 0, "tf32x3": 3, "bf16x6": 4}
 
 
 def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
@@ -40,7 +40,7 @@ def solve_mixed(transr, uplo, A, B, prec, max_iter=30, tol=1e-15):
     return X, st
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6", "bf16x8", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6", "tf32", "bf16"])
 @pytest.mark.parametrize("transr,uplo,n", [("N", "L", 100), ("T", "U", 513), ("N", "U", 1300),
                                            ("T", "L", 2100)])
 def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
@@ -56,7 +56,7 @@ def test_mixed_converges_well_conditioned(prec, transr, uplo, n):
 
 
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6", "bf16x8", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6", "tf32", "bf16"])
 def test_mixed_conditioning(prec, kappa):
     n = 1200
     A = gen.spd_spectrum(n, seed=7, kappa=kappa)

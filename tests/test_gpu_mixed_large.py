@@ -22,8 +22,8 @@ torch = pytest.importorskip("torch")
 rfp = pytest.importorskip("paper_0901_1696_gb300.binding")
 
 N, NRHS, MAX_ITER = 16384, 32, 30
-PRECS = {"fp32": 2, "tf32x3": 3, "bf16x6": 4, "bf16x8": 5, "tf32": 1, "bf16": 0}
-MUST_CONVERGE = {"fp32", "tf32x3", "bf16x6", "bf16x8"}
+PRECS = {"fp32": 2, "tf32x3": 3, "bf16x6": 4, "tf32": 1, "bf16": 0}
+MUST_CONVERGE = {"fp32", "tf32x3", "bf16x6"}
 SAMPLE = [0, NRHS // 2, NRHS - 1]
 
 

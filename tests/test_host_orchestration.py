@@ -224,8 +224,7 @@ def _aligned_bytes(nbytes, align=256):
     return raw[off:off + nbytes]
 
 
-@pytest.mark.parametrize("prec", [2, 3, 4, 5, 1, 0],
-                         ids=["fp32", "tf32x3", "bf16x6", "bf16x8", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", [2, 3, 4, 1, 0], ids=["fp32", "tf32x3", "bf16x6", "tf32", "bf16"])
 @pytest.mark.parametrize("transr,uplo,n", [("N", "L", 5), ("T", "U", 70), ("N", "U", 600),
                                            ("T", "L", 600)])
 def test_emulated_mixed_precision_solve(emu_lib, prec, transr, uplo, n):
