@@ -779,7 +779,7 @@ def run_serve(args):
     out = serve_leg(lib, dev, R, R, P, loads, resident_requests=min(R, 1000))
     line = {"mode": "serve", "metric": "served solves/s, p50/p99 at <=1e-12 bwd err",
             "value": out["runs"]["saturation"]["solves_per_s"], "unit": "solves/s (right-hand sides)",
-            "higher_is_better": True, "dtype": "f64 in/out (FP64 or split-TF32 + FP64 refinement)",
+            "higher_is_better": True, "dtype": "f64 in/out (FP64 or split-BF16 + FP64 refinement)",
             "data": "synthetic: A = Q diag(lam) Q^T, Q = 8 Householder reflectors, lam log-uniform "
                     "on [1, kappa]",
             "config": {"workload": out["workload"], "requests": R, "pool": P},

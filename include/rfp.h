@@ -377,7 +377,7 @@ int rfp_slansf(char norm, char transr, char uplo, int64_t n, const float *arf, f
  *     request that arrived meanwhile joins that launch, up to batch_max);
  *   - every other request runs on its own stream (one of `streams`): FP64
  *     PFTRF + PFTRS, the mixed-precision solve (rfp_dpfsv_mixed with
- *     RFP_PREC_TF32X3), or PFTRI on a copy of a resident array.
+ *     RFP_PREC_BF16X6), or PFTRI on a copy of a resident array.
  * A mixed-mode request of order n <= small_n is served in FP64 (its array is
  * held as an FP64 factor): the FP64 result meets the mixed mode's accuracy,
  * and at these orders FP64 is at least as fast.

@@ -44,6 +44,9 @@ constexpr int kMaxStreams = 64;
 constexpr int kBatchStreams = 2;
 constexpr int kSlots = 1 << 15;   // pinned result slots (in-flight jobs)
 constexpr int kBatchRhs = 32;     // right-hand sides a batched request may have
+// Precision of the mixed-mode solves: the split-BF16 factor, as fast as the
+// split-TF32 one at kappa <= 1e4 and faster at 1e6 (fewer refinement steps).
+constexpr int kServeMixedPrec = RFP_PREC_BF16X6;
 
 struct ResultSlot {               // pinned host memory, written by D2H copies
     int32_t info;
@@ -362,7 +365,7 @@ private:
         const size_t bx = (size_t)r.n * (size_t)r.nrhs * sizeof(double);
         if (r.op == RFP_SERVE_OP_INVERT) return rfp_bytes(r.n) + 256;
         if (!fp64_path(r))
-            return 2 * bx + rfp_dpfsv_mixed_workspace(r.n, r.nrhs, RFP_PREC_TF32X3) + 3 * 256;
+            return 2 * bx + rfp_dpfsv_mixed_workspace(r.n, r.nrhs, kServeMixedPrec) + 3 * 256;
         return bx + 256;
     }
 
@@ -390,7 +393,7 @@ private:
         } else {
             ok = (j->b_off = alloc(bx)) >= 0 && (j->stat_off = alloc(256)) >= 0;
             if (ok && mixed) {
-                const size_t wb = rfp_dpfsv_mixed_workspace(r.n, r.nrhs, RFP_PREC_TF32X3);
+                const size_t wb = rfp_dpfsv_mixed_workspace(r.n, r.nrhs, kServeMixedPrec);
                 ok = (j->x_off = alloc(bx)) >= 0 && (j->work_off = alloc(wb)) >= 0;
             }
         }
@@ -431,9 +434,9 @@ private:
                 if (!e && !rc) e = cudaMemcpyAsync(&hs->info, d_info, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
             } else if (!e) {
                 auto *d_st = reinterpret_cast<rfp_mixed_status_t *>(d_info);
-                const size_t wb = rfp_dpfsv_mixed_workspace(r.n, r.nrhs, RFP_PREC_TF32X3);
+                const size_t wb = rfp_dpfsv_mixed_workspace(r.n, r.nrhs, kServeMixedPrec);
                 rc = rfp_dpfsv_mixed(r.transr, r.uplo, r.n, r.nrhs, dptr(j->arf_off), dptr(j->b_off), r.n,
-                                     dptr(j->x_off), r.n, RFP_PREC_TF32X3, cfg_.max_iter, cfg_.tol,
+                                     dptr(j->x_off), r.n, kServeMixedPrec, cfg_.max_iter, cfg_.tol,
                                      dptr(j->work_off), wb, d_st, st);
                 if (!rc) e = cudaMemcpyAsync(r.X, dptr(j->x_off), bx, cudaMemcpyDeviceToHost, st);
                 if (!e && !rc) e = cudaMemcpyAsync(&hs->st, d_st, sizeof(rfp_mixed_status_t), cudaMemcpyDeviceToHost, st);
