@@ -111,3 +111,52 @@ def test_two_streams_at_once_equal_alone():
             X = host_colmajor(d, n, nrhs)
             assert np.array_equal(X, ref)
             assert oracle.solve_backward_error(A, X, B) <= 1e-13
+
+
+@pytest.mark.parametrize("transr,uplo,n", [("N", "L", 700), ("T", "U", 385), ("N", "U", 1001)])
+def test_captured_factor_solve_inverse_match_direct(transr, uplo, n):
+    """Under CUDA graph capture PFTRF, PFTRS and PFTRI run their
+    multi-launch forms (no scratch is taken while capturing); replayed, they
+    must agree with the direct calls (lookahead steps and one-launch solves)
+    within rounding, and with the oracle."""
+    nrhs = 20
+    A, rng = gen.spd_bbt(n, seed=n + 3, return_rng=True)
+    B = gen.rhs(n, nrhs, rng)
+    arf0 = torch.from_numpy(oracle.pack(transr, uplo, A)).cuda()
+    B0 = dev_colmajor(torch, B)
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+
+    def run(arf, dB, stream=None):
+        rfp.rfp_dpftrf(transr, uplo, n, arf, info[0:1], stream=stream)
+        rfp.rfp_dpftrs(transr, uplo, n, nrhs, arf, dB, n, stream=stream)
+        fac = arf.clone()
+        rfp.rfp_dpftri(transr, uplo, n, arf, info[1:2], stream=stream)
+        return fac
+
+    a1, b1 = arf0.clone(), B0.clone()
+    f1 = run(a1, b1)
+    torch.cuda.synchronize()
+    assert int(info.abs().sum().item()) == 0
+    a2, b2 = arf0.clone(), B0.clone()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        f2 = run(a2, b2, stream=s)
+    a2.copy_(arf0)
+    b2.copy_(B0)
+    info.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(info.abs().sum().item()) == 0
+    ref_f, _ = oracle.pftrf(transr, uplo, n, oracle.pack(transr, uplo, A))
+    ref_x = oracle.pftrs(transr, uplo, n, ref_f, B)
+    ref_i, _ = oracle.pftri(transr, uplo, n, ref_f)
+    tol = factor_tolerance(n)
+    for got, ref in ((f1, ref_f), (f2, ref_f), (a1, ref_i), (a2, ref_i)):
+        got = got.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    for dB in (b1, b2):
+        X = host_colmajor(dB, n, nrhs)
+        assert np.max(np.abs(X - ref_x)) <= tol * np.max(np.abs(ref_x))
+        assert oracle.solve_backward_error(A, X, B) <= 1e-13
