@@ -281,9 +281,11 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
                 }
             return;
         }
-        // the new diagonal factor tile, from L2 (another SM wrote it in this launch)
-        for (int e = tid; e < kT * kT; e += kTh) {
-            const int u = e % kT, v = e / kT;
+        // the new diagonal factor tile, from L2 (another SM wrote it in this
+        // launch); unrolled so that each thread's loads are in flight together
+#pragma unroll
+        for (int q = 0; q < kT * kT / kTh; ++q) {
+            const int e = tid + q * kTh, u = e % kT, v = e / kT;
             const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
             if (i < wn && j <= i) sm.Ld[i][j] = __ldcg(&a.V(a.k1 + i, a.k1 + j));
         }

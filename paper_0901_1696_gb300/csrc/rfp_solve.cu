@@ -273,8 +273,11 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     {
         const View<double> D = lblock(a, b, b);
         const bool rowfast = D.rs == 1;
-        for (int e = tid; e < kR * kR; e += kThreads) {
-            const int u = e % kR, v = e / kR;
+        // unrolled by 8: eight loads per thread in flight at a time (this
+        // load is on the critical path of the block substitution)
+#pragma unroll 8
+        for (int q = 0; q < kR * kR / kThreads; ++q) {
+            const int e = tid + q * kThreads, u = e % kR, v = e / kR;
             const int i = rowfast ? u : v, jj = rowfast ? v : u;
             if (i < rows && jj <= i) sm.d.Ld[i][jj] = D(i, jj);
         }
