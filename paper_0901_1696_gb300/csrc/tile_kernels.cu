@@ -593,22 +593,39 @@ cudaError_t potrf_tile(cudaStream_t st, View<T> A, int w, int32_t *info, int64_t
     return cudaGetLastError();
 }
 
+// Inverse of one lower-triangular tile: column c of W = L^{-1} by forward
+// substitution, W(c, c) = 1 / L(c, c) and, for i > c,
+//   W(i, c) = -(sum_{p = c}^{i-1} L(i, p) W(p, c)) / L(i, i).
+// Four lanes of one warp share a column: each sums every fourth term, the
+// partial sums are combined by shuffles inside the group of four, and the
+// group's first lane writes W(i, c).  The diagonal's reciprocals are formed
+// once, in parallel (a division per element would dominate on GB300's narrow
+// FP64 pipe).
 template <typename T>
 __global__ void __launch_bounds__(256) trtri_tile_kernel(View<T> A, int w, const int32_t *abort)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Ls = reinterpret_cast<T *>(smem_raw);
     T *Ws = Ls + kTileMax * kTileLd;
+    T *rinv = Ws + kTileMax * kTileLd;
     if (abort && *abort) return;
     load_lower_tile(Ls, A, w);
     __syncthreads();
-    const int c = threadIdx.x;      // one column of W = L^{-1} per thread
+    if ((int)threadIdx.x < w) rinv[threadIdx.x] = T(1) / Ls[threadIdx.x * kTileLd + threadIdx.x];
+    __syncthreads();
+    const int c = threadIdx.x / 4, part = threadIdx.x % 4;
+    const int lane = threadIdx.x % 32;
+    const unsigned group = 0xFu << (lane & ~3);   // this column's four lanes
     if (c < w) {
-        Ws[c * kTileLd + c] = T(1) / Ls[c * kTileLd + c];
+        if (part == 0) Ws[c * kTileLd + c] = rinv[c];
+        __syncwarp(group);
         for (int i = c + 1; i < w; ++i) {
             T s = T(0);
-            for (int p = c; p < i; ++p) s += Ls[i * kTileLd + p] * Ws[p * kTileLd + c];
-            Ws[i * kTileLd + c] = -s / Ls[i * kTileLd + i];
+            for (int p = c + part; p < i; p += 4) s += Ls[i * kTileLd + p] * Ws[p * kTileLd + c];
+            s += __shfl_xor_sync(group, s, 1);
+            s += __shfl_xor_sync(group, s, 2);
+            if (part == 0) Ws[i * kTileLd + c] = -s * rinv[i];
+            __syncwarp(group);   // W(i, c) visible to the group's next sums
         }
     }
     __syncthreads();
@@ -619,7 +636,7 @@ template <typename T>
 cudaError_t trtri_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort)
 {
     if (w <= 0) return cudaSuccess;
-    const int smem = 2 * kTileMax * kTileLd * (int)sizeof(T);
+    const int smem = (2 * kTileMax * kTileLd + kTileMax) * (int)sizeof(T);
     cudaError_t e = set_smem_once<T>((const void *)trtri_tile_kernel<T>, smem);
     if (e != cudaSuccess) return e;
     trtri_tile_kernel<T><<<1, 256, smem, st>>>(A, w, abort);
