@@ -36,15 +36,17 @@ namespace rfp {
 
 namespace {
 
-constexpr int kR = 64;              // rows per block
 constexpr int kG = 16;              // right-hand sides per task
 constexpr int kKc = 16;             // K chunk staged in shared memory
 constexpr int kThreads = 128;
-constexpr int kAsLd = kR + 2;       // doubles
 constexpr int kXsLd = kG + 2;
-constexpr int kLdLd = kR + 1;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kErrWait = 4;
+// Block rows: 64 for large orders (fewer, larger tasks), 32 up to
+// kSmallSolve rows, where the diagonal chain bounds the solve: on GB300 a
+// 64-row block's update and substitution keep one SM's FP64 pipe busy about
+// four times longer than a 32-row block's.
+constexpr int64_t kSmallSolve = 4096;
 
 struct SolveArgs {
     View<double> t1, s, t2;
@@ -65,24 +67,26 @@ __device__ __forceinline__ uint64_t rs_globaltimer()
     return t;
 }
 
-// First row (global) and row count of block b.
+// First row (global) and row count of block b (R-row blocks).
+template <int R>
 __device__ __forceinline__ void block_rows(const SolveArgs &a, int b, int64_t &r0, int &rows)
 {
     if (b < a.nb1) {
-        r0 = (int64_t)b * kR;
-        rows = (int)(int)(a.n1 - r0 < kR ? a.n1 - r0 : kR);
+        r0 = (int64_t)b * R;
+        rows = (int)(a.n1 - r0 < R ? a.n1 - r0 : R);
     } else {
-        const int64_t lr = (int64_t)(b - a.nb1) * kR;
+        const int64_t lr = (int64_t)(b - a.nb1) * R;
         r0 = a.n1 + lr;
-        rows = (int)(int)(a.n2 - lr < kR ? a.n2 - lr : kR);
+        rows = (int)(a.n2 - lr < R ? a.n2 - lr : R);
     }
 }
 
 // View of block (bi, bj) of L, bi >= bj, at the block's first element.
+template <int R>
 __device__ __forceinline__ View<double> lblock(const SolveArgs &a, int bi, int bj)
 {
-    const int64_t ri = bi < a.nb1 ? (int64_t)bi * kR : (int64_t)(bi - a.nb1) * kR;
-    const int64_t cj = bj < a.nb1 ? (int64_t)bj * kR : (int64_t)(bj - a.nb1) * kR;
+    const int64_t ri = bi < a.nb1 ? (int64_t)bi * R : (int64_t)(bi - a.nb1) * R;
+    const int64_t cj = bj < a.nb1 ? (int64_t)bj * R : (int64_t)(bj - a.nb1) * R;
     if (bi < a.nb1) return a.t1.sub(ri, cj);
     if (bj < a.nb1) return a.s.sub(ri, cj);
     return a.t2.sub(ri, cj);
@@ -103,13 +107,15 @@ __device__ __forceinline__ bool wait_progress(const int32_t *prog, int need, int
     }
 }
 
-// Staging of one 64 x 16 chunk of op(L_jb) (rows r < rv of the task's block,
+// Staging of one R x 16 chunk of op(L_jb) (rows r < rv of the task's block,
 // k in [k0, k0 + 16) < kv) and of the matching 16 x 16 chunk of X_j.
 // A(r, k) = V(r, k) for a view V; both loaders read along their view's unit
 // stride (X's rows for a right-hand-side block, its columns for a
 // transposed RFP block).
+template <int R>
 struct ChunkRegs {
-    double a[kR * kKc / kThreads];   // 8
+    static constexpr int AQ = R * kKc / kThreads, ALd = R + 2;
+    double a[AQ];
     double x[kKc * kG / kThreads];   // 2
 
     __device__ __forceinline__ void load(View<double> V, int rv, int k0, int kv, View<double> Xj,
@@ -118,13 +124,13 @@ struct ChunkRegs {
         const int tid = threadIdx.x;
         if (V.rs == 1) {      // rows contiguous
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int r = tid % kR, k = k0 + tid / kR + 2 * q;
+            for (int q = 0; q < AQ; ++q) {
+                const int r = tid % R, k = k0 + tid / R + (kThreads / R) * q;
                 a[q] = (r < rv && k < kv) ? __ldg(&V.p[r + (int64_t)k * V.cs]) : 0.0;
             }
         } else {              // k contiguous
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < AQ; ++q) {
                 const int k = k0 + tid % kKc, r = tid / kKc + 8 * q;
                 a[q] = (r < rv && k < kv) ? __ldg(&V.p[(int64_t)r * V.rs + k * V.cs]) : 0.0;
             }
@@ -143,16 +149,16 @@ struct ChunkRegs {
             }
         }
     }
-    __device__ __forceinline__ void store(const View<double> &V, bool xrowfast,
-                                          double (*As)[kAsLd], double (*Xs)[kXsLd]) const
+    __device__ __forceinline__ void store(const View<double> &V, bool xrowfast, double (*As)[ALd],
+                                          double (*Xs)[kXsLd]) const
     {
         const int tid = threadIdx.x;
         if (V.rs == 1) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) As[tid / kR + 2 * q][tid % kR] = a[q];
+            for (int q = 0; q < AQ; ++q) As[tid / R + (kThreads / R) * q][tid % R] = a[q];
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) As[tid % kKc][tid / kKc + 8 * q] = a[q];
+            for (int q = 0; q < AQ; ++q) As[tid % kKc][tid / kKc + 8 * q] = a[q];
         }
         if (xrowfast) {
 #pragma unroll
@@ -164,24 +170,29 @@ struct ChunkRegs {
     }
 };
 
+template <int R>
 struct UpdateSmem {
-    double As[2][kKc][kAsLd];
+    double As[2][kKc][R + 2];
     double Xs[2][kKc][kXsLd];
 };
+template <int R>
 struct DiagSmem {
-    double Ld[kR][kLdLd];       // lower triangle of L_bb
-    double Bs[kR][kG + 1];      // the block's right-hand side, redistributed
-    double rinv[kR];            // 1 / L_bb(j, j)
+    double Ld[R][R + 1];        // lower triangle of L_bb
+    double Bs[R][kG + 1];       // the block's right-hand side, redistributed
+    double rinv[R];             // 1 / L_bb(j, j)
 };
+template <int R>
 union SolveSmem {
-    UpdateSmem u;
-    DiagSmem d;
+    UpdateSmem<R> u;
+    DiagSmem<R> d;
 };
 
-template <bool TRANS>
+template <bool TRANS, int R>
 __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 {
-    __shared__ __align__(16) SolveSmem sm;
+    constexpr int RM = R / 16;       // rows per thread in the update (16 row groups)
+    constexpr int H = R / 32;        // rows per lane in the substitution
+    __shared__ __align__(16) SolveSmem<R> sm;
     __shared__ int s_ticket, s_ok;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -195,19 +206,19 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     const int b = TRANS ? a.nb - 1 - p : p;
     int64_t r0;
     int rows;
-    block_rows(a, b, r0, rows);
+    block_rows<R>(a, b, r0, rows);
     const int64_t c0 = (int64_t)g * kG;
     const int cols = (int)(a.nrhs - c0 < kG ? a.nrhs - c0 : kG);
     const View<double> Xb = a.X.sub(r0, c0);
     int32_t *prog = a.prog + g;
 
-    const int tx = tid % 8, ty = tid / 8;                    // 2 columns x 4 rows each
-    double acc[4][2];
+    const int tx = tid % 8, ty = tid / 8;                    // 2 columns x RM rows each
+    double acc[RM][2];
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+    for (int m = 0; m < RM; ++m)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int r = ty * 4 + m, cc = tx * 2 + c;
+            const int r = ty * RM + m, cc = tx * 2 + c;
             acc[m][c] = (r < rows && cc < cols) ? a.alpha * __ldcg(&Xb(r, cc)) : 0.0;
         }
 
@@ -227,13 +238,13 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
         }
         int64_t j0;
         int kv;
-        block_rows(a, j, j0, kv);
+        block_rows<R>(a, j, j0, kv);
         // op(L) for this task: forward A = L_bj (rows b, k over j);
         // backward A = L_jb^T (rows b, k over j).
-        const View<double> V = TRANS ? lblock(a, j, b).t() : lblock(a, b, j);
+        const View<double> V = TRANS ? lblock<R>(a, j, b).t() : lblock<R>(a, b, j);
         const View<double> Xj = a.X.sub(j0, c0);
         const int nch = (kv + kKc - 1) / kKc;
-        ChunkRegs st;
+        ChunkRegs<R> st;
         st.load(V, rows, 0, kv, Xj, cols);
         for (int ch = 0; ch < nch; ++ch) {
             const int buf = ch & 1;
@@ -242,12 +253,16 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
             if (ch + 1 < nch) st.load(V, rows, (ch + 1) * kKc, kv, Xj, cols);
 #pragma unroll
             for (int kk = 0; kk < kKc; ++kk) {
-                const double2 a01 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * 4]);
-                const double2 a23 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * 4 + 2]);
-                const double2 x = *reinterpret_cast<const double2 *>(&sm.u.Xs[buf][kk][tx * 2]);
-                const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+                double av[RM];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
+                for (int m = 0; m < RM; m += 2) {
+                    const double2 t2 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * RM + m]);
+                    av[m] = t2.x;
+                    av[m + 1] = t2.y;
+                }
+                const double2 x = *reinterpret_cast<const double2 *>(&sm.u.Xs[buf][kk][tx * 2]);
+#pragma unroll
+                for (int m = 0; m < RM; ++m) {
                     acc[m][0] = fma(-av[m], x.x, acc[m][0]);
                     acc[m][1] = fma(-av[m], x.y, acc[m][1]);
                 }
@@ -259,10 +274,10 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 
     if (!ok) {             // a wait gave up: mark this block of X as not computed
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < RM; ++m)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const int r = ty * 4 + m, cc = tx * 2 + c;
+                const int r = ty * RM + m, cc = tx * 2 + c;
                 if (r < rows && cc < cols) Xb(r, cc) = __longlong_as_double(0x7ff8000000000000ll);
             }
         return;
@@ -271,13 +286,13 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     // Diagonal block: the lower triangle of L_bb into shared memory, the
     // right-hand side from the accumulators, then substitution.
     {
-        const View<double> D = lblock(a, b, b);
+        const View<double> D = lblock<R>(a, b, b);
         const bool rowfast = D.rs == 1;
         // unrolled by 8: eight loads per thread in flight at a time (this
         // load is on the critical path of the block substitution)
 #pragma unroll 8
-        for (int q = 0; q < kR * kR / kThreads; ++q) {
-            const int e = tid + q * kThreads, u = e % kR, v = e / kR;
+        for (int q = 0; q < R * R / kThreads; ++q) {
+            const int e = tid + q * kThreads, u = e % R, v = e / R;
             const int i = rowfast ? u : v, jj = rowfast ? v : u;
             if (i < rows && jj <= i) sm.d.Ld[i][jj] = D(i, jj);
         }
@@ -287,15 +302,15 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
         if (tid < rows) sm.d.rinv[tid] = 1.0 / D(tid, tid);
     }
     // The right-hand side is redistributed through shared memory: lane l of
-    // warp w takes rows l and l + 32 of columns 4w .. 4w + 3.
+    // warp w takes rows l (and l + 32 when R = 64) of columns 4w .. 4w + 3.
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+    for (int m = 0; m < RM; ++m)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) sm.d.Bs[ty * 4 + m][tx * 2 + c] = acc[m][c];
+        for (int c = 0; c < 2; ++c) sm.d.Bs[ty * RM + m][tx * 2 + c] = acc[m][c];
     __syncthreads();
-    double v[2][4];
+    double v[H][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < H; ++h)
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[h][c] = sm.d.Bs[lane + 32 * h][warp * 4 + c];
 
@@ -306,16 +321,16 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     for (int q = 0; q < rows; ++q) {
         const int j = TRANS ? rows - 1 - q : q;
         const int owner = j & 31;
-        const bool hi = j >= 32;
+        const bool hi = H > 1 && j >= 32;
         const double ri = sm.d.rinv[j];
         double xj[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const double own = hi ? v[1][c] : v[0][c];
+            const double own = hi ? v[H - 1][c] : v[0][c];
             xj[c] = __shfl_sync(0xffffffffu, own, owner) * ri;
         }
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
+        for (int hh = 0; hh < H; ++hh) {
             const int r = lane + 32 * hh;
             if (r == j) {
 #pragma unroll
@@ -333,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
             const int cc = warp * 4 + c;
             if (cc >= cols) continue;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < H; ++h) {
                 const int r = lane + 32 * h;
                 if (r < rows) Xb(r, cc) = v[h][c];
             }
@@ -343,10 +358,10 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) sm.d.Bs[lane + 32 * h][warp * 4 + c] = v[h][c];
+            for (int h = 0; h < H; ++h) sm.d.Bs[lane + 32 * h][warp * 4 + c] = v[h][c];
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kR * kG / kThreads; ++q) {
+        for (int q = 0; q < R * kG / kThreads; ++q) {
             const int cc = tid % kG, r = tid / kG + (kThreads / kG) * q;
             if (r < rows && cc < cols) Xb(r, cc) = sm.d.Bs[r][cc];
         }
@@ -369,7 +384,8 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
-    const int64_t nb1 = (n1 + kR - 1) / kR, nb2 = (n2 + kR - 1) / kR, ng = (nrhs + kG - 1) / kG;
+    const int64_t R = n <= kSmallSolve ? 32 : 64;
+    const int64_t nb1 = (n1 + R - 1) / R, nb2 = (n2 + R - 1) / R, ng = (nrhs + kG - 1) / kG;
     const int64_t tasks = (nb1 + nb2) * ng;
     if (tasks > INT32_MAX) return cudaErrorInvalidValue;
     // sync: [0] ticket counter, [1] error word, [2 .. 2 + ng) progress per
@@ -378,8 +394,13 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
     if (e != cudaSuccess) return e;
     SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, nrhs, (int)ng,
                 sync, sync + 2, sync + 1, abort, alpha};
-    if (trans) rfp_solve_kernel<true><<<(unsigned)tasks, kThreads, 0, st>>>(a);
-    else rfp_solve_kernel<false><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+    if (R == 32) {
+        if (trans) rfp_solve_kernel<true, 32><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+        else rfp_solve_kernel<false, 32><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+    } else {
+        if (trans) rfp_solve_kernel<true, 64><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+        else rfp_solve_kernel<false, 64><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+    }
     note_launch();
     return cudaGetLastError();
 }

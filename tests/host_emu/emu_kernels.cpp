@@ -393,7 +393,8 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
-    const int64_t R = 64, nb1 = (n1 + R - 1) / R, nb = nb1 + (n2 + R - 1) / R, ng = (nrhs + 15) / 16;
+    const int64_t R = n <= 4096 ? 32 : 64;             // block rows, as the kernel picks them
+    const int64_t nb1 = (n1 + R - 1) / R, nb = nb1 + (n2 + R - 1) / R, ng = (nrhs + 15) / 16;
     Launch L;
     L.ordered = true;
     for (size_t w = 0; w < rfp_solve_sync_words(nrhs); ++w) L.wr(sync + w, 0);   // the memset
