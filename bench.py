@@ -501,6 +501,21 @@ def c1_leg(lib, dev, stream, reps: int = 30, oracle_too: bool = True):
     torch.cuda.synchronize(dev)
     assert int(info.abs().sum().item()) == 0
     Xh = X.cpu().numpy().T
+    # per-step split (events between the steps; three extra rounds, not in
+    # the medians above)
+    lib.rfp_stage_timing(True)
+    for _ in range(3):
+        arf.copy_(arf0)
+        flush.fill_(1)
+        lib.rfp_dpftrf("N", "L", n, arf, info[0:1], stream)
+        X.copy_(B0)
+        lib.rfp_dpftrs("N", "L", n, nrhs, arf, X, n, stream)
+        lib.rfp_dpftri("N", "L", n, arf, info[1:2], stream)
+    torch.cuda.synchronize(dev)
+    steps = {}
+    for name, ms in lib.rfp_stage_times():
+        steps[name] = steps.get(name, 0.0) + ms * 1e3 / 3
+    lib.rfp_stage_timing(False)
     from paper_0901_1696_gb300.flops import pftrf_flops, pftri_flops, pftrs_flops
     med = {k: float(np.median(v)) for k, v in times.items()}
     out = {"workload": "n=1001 N/L, A = B B^T/n + I (seed 0), nrhs=16; L2 flushed before each call",
@@ -509,7 +524,8 @@ def c1_leg(lib, dev, stream, reps: int = 30, oracle_too: bool = True):
            "pftrf_gflops": pftrf_flops(n) / (med["pftrf"] * 1e-6) / 1e9,
            "pftrs_gflops": pftrs_flops(n, nrhs) / (med["pftrs"] * 1e-6) / 1e9,
            "pftri_gflops": pftri_flops(n) / (med["pftri"] * 1e-6) / 1e9,
-           "bwd_err": sampled_backward_error(A, Xh, Bh), "reps": reps}
+           "bwd_err": sampled_backward_error(A, Xh, Bh), "reps": reps,
+           "steps_us": {k: round(v, 1) for k, v in steps.items()}}
     if oracle_too:
         import oracle
         packed = oracle.pack("N", "L", A)

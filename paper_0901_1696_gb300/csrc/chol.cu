@@ -59,15 +59,17 @@ cudaError_t potrf_blocked(cudaStream_t st, View<T> V, int64_t m, int32_t *info,
 {
     if constexpr (sizeof(T) == 8) {
         // FP64: panel 0 as below, then one lookahead launch per panel step
-        // (potrf_step.cu); the multi-launch form when no scratch can be had.
+        // (potrf_step.cu, panels potrf_step_width(m) wide); the multi-launch
+        // form when no scratch can be had.
         int32_t *sync = nullptr;
         if (m > kNb && solve_scratch_acquire(st, potrf_step_sync_words(m), &sync) == cudaSuccess) {
+            const int64_t pw = potrf_step_width(m);
             cudaError_t e = cudaMemsetAsync(sync, 0, potrf_step_sync_words(m) * sizeof(int32_t), st);
-            if (e == cudaSuccess) e = potrf_tile(st, V, (int)kNb, info, base);
+            if (e == cudaSuccess) e = potrf_tile(st, V, (int)pw, info, base);
             if (e == cudaSuccess)
-                e = trsm_strip(st, V.sub(kNb, 0), V, m - kNb, (int)kNb, 1, T(1), info);
-            for (int64_t k0 = 0; e == cudaSuccess && k0 + kNb < m; k0 += kNb)
-                e = potrf_step(st, V, m, k0, info, base, sync + 2 * (k0 / kNb));
+                e = trsm_strip(st, V.sub(pw, 0), V, m - pw, (int)pw, 1, T(1), info);
+            for (int64_t k0 = 0; e == cudaSuccess && k0 + pw < m; k0 += pw)
+                e = potrf_step(st, V, m, k0, info, base, sync + 2 * (k0 / pw));
             const cudaError_t e2 = solve_scratch_release(st, sync);
             return e != cudaSuccess ? e : e2;
         }
@@ -164,13 +166,13 @@ cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *
         RFP_TRY(trtri_tile(st, V.sub(k0, k0), (int)w, abort));
         if (k0 > 0)
             RFP_TRY(gemm_nt(st, V.sub(k0, 0), V.sub(k0, k0), V.sub(k0, 0).t(), w, k0, w, T(1),
-                            T(0), MASK_NONE, MASK_LOWER, MASK_NONE, abort, true));
+                            T(0), MASK_NONE, MASK_LOWER, MASK_NONE, abort, GEMM_INPLACE_COLS));
         if (k1 < m) {
             if (k0 > 0)
                 RFP_TRY(gemm_nt(st, V.sub(k1, 0), V.sub(k1, k0), V.sub(k0, 0).t(), m - k1, k0, w,
                                 T(-1), T(1), MASK_NONE, MASK_NONE, MASK_NONE, abort));
             RFP_TRY(gemm_nt(st, V.sub(k1, k0), V.sub(k1, k0), V.sub(k0, k0).t(), m - k1, w, w,
-                            T(-1), T(0), MASK_NONE, MASK_NONE, MASK_UPPER, abort, true));
+                            T(-1), T(0), MASK_NONE, MASK_NONE, MASK_UPPER, abort, GEMM_INPLACE_ROWS));
         }
     }
     return cudaSuccess;
@@ -188,7 +190,7 @@ cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *
             RFP_TRY(gemm_nt(st, V, V.sub(k0, 0).t(), V.sub(k0, 0).t(), k0, k0, w, T(1), T(1),
                             MASK_LOWER, MASK_NONE, MASK_NONE, abort));
             RFP_TRY(gemm_nt(st, V.sub(k0, 0), V.sub(k0, k0).t(), V.sub(k0, 0).t(), w, k0, w,
-                            T(1), T(0), MASK_NONE, MASK_UPPER, MASK_NONE, abort, true));
+                            T(1), T(0), MASK_NONE, MASK_UPPER, MASK_NONE, abort, GEMM_INPLACE_COLS));
         }
         RFP_TRY(lauum_tile(st, V.sub(k0, k0), (int)w, abort));
     }

@@ -119,7 +119,7 @@ static cudaError_t factor_panels(cudaStream_t st, View<float> W, int64_t n, int 
             // X_c <- X_c W_c^T with W_c = L11(c0.., c0..)^{-1} (lower): in place
             View<float> Wc{inv0 + (c0 / kInvBlock) * kInvBlock * kInvBlock, 1, kInvBlock};
             RFP_TRY(gemm_nt(st, X.sub(0, c0), X.sub(0, c0), Wc, m, cw, cw, 1.0f, 0.0f, MASK_NONE,
-                            MASK_NONE, MASK_LOWER, info, true));
+                            MASK_NONE, MASK_LOWER, info, GEMM_INPLACE_ROWS));
         }
         if (prec == RFP_PREC_FP32) {
             RFP_TRY(gemm_nt(st, W.sub(j1, j1), X, X, m, m, nb, -1.0f, 1.0f, MASK_LOWER, MASK_NONE,

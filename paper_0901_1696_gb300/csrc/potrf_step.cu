@@ -1,11 +1,12 @@
 // FP64 Cholesky of one RFP triangle (PFTRF steps 1 and 4, Section 3) with a
 // one-panel lookahead, one launch per panel step.
 //
-// Right-looking blocked Cholesky of the m x m lower triangle V with 64-wide
-// panels: after panel k (columns [k0, k1)) is factored, the trailing matrix
-// A(k1:m, k1:m) receives -= L(:, k0:k1) L(:, k0:k1)^T, and panel k+1
-// (columns [k1, k2)) is then factored: POTRF of its diagonal tile, and the
-// rows below solved against that tile (TRSM).  Launch k does all of this:
+// Right-looking blocked Cholesky of the m x m lower triangle V with panels
+// of width PW (32 for small triangles, 64 beyond): after panel k (columns
+// [k0, k1)) is factored, the trailing matrix A(k1:m, k1:m) receives
+// -= L(:, k0:k1) L(:, k0:k1)^T, and panel k+1 (columns [k1, k2)) is then
+// factored: POTRF of its diagonal tile, and the rows below solved against
+// that tile (TRSM).  Launch k does all of this:
 //   ticket 0             the diagonal tile of panel k+1: its update, then
 //                        POTRF in shared memory; writes L and raises a flag;
 //   tickets 1 .. P       32- or 64-row strips of panel k+1 below the diagonal: the
@@ -18,13 +19,20 @@
 // beside the bulk of the trailing update instead of between launches.  No
 // element is written by one CTA and read by another except the diagonal
 // tile, which is read only after its flag.
+//
+// The chain's length is set by one SM's FP64 pipe: a PW x PW x PW update,
+// a PW-column POTRF and a PW-column solve, one after another.  Halving PW
+// cuts that chain about four-fold per step for twice the steps, which pays
+// while the chain, not the bulk update, bounds a step (small triangles).
 #include "rfp_internal.cuh"
 
 namespace rfp {
 
 namespace {
 
-constexpr int kT = 64;              // tile / panel width
+constexpr int kT = 64;              // bulk tile width; the widest panel
+// Panel width: 32 for triangles up to kNarrowPanels, 64 beyond.
+constexpr int64_t kNarrowPanels = 2048;
 // Rows of a panel strip task: 32 for triangles up to kSmallStrips (their
 // factorization is bound by the diagonal chain, which shorter strips
 // shorten), 64 beyond (fewer, more efficient tasks beside the bulk update).
@@ -61,12 +69,13 @@ __device__ __forceinline__ uint64_t step_globaltimer()
     return t;
 }
 
-// The block of the C tile a thread owns: TM rows x 4 columns at row block
-// ry, column block cx.  The usual map is cx = tid % 16, ry = tid / 16; for
-// the diagonal tile (`lower`, TM = 4) threads 0 .. 135 take the 136 blocks
-// with ry >= cx in order and the others own none, so warps 5 .. 7 issue no
-// multiply-adds on the factorization's critical path.
-template <int TM>
+// The block of the C tile a thread owns: TM rows x CW columns at row block
+// ry, column block cx.  The usual map is cx = tid % 16, ry = tid / 16 (a
+// 16 TM x 16 CW tile); for the 64-wide diagonal tile (`lower`, TM = CW = 4)
+// threads 0 .. 135 take the 136 blocks with ry >= cx in order and the others
+// own none, so warps 5 .. 7 issue no multiply-adds on the factorization's
+// critical path.
+template <int TM, int CW>
 struct Owner {
     int ry, cx;
     bool active;
@@ -88,53 +97,55 @@ struct Owner {
     }
 };
 
-// acc(16 TM x 64: TM x 4 per thread) = P_rows(16 TM x w) P_cols(64 x w)^T with
-// P_rows(i, k) = V(r0 + i, k0 + k) for i < nr (zero beyond), likewise
+// acc(16 TM x 16 CW: TM x CW per thread) = P_rows(16 TM x w) P_cols(16 CW x w)^T
+// with P_rows(i, k) = V(r0 + i, k0 + k) for i < nr (zero beyond), likewise
 // P_cols with c0 / nc.  w <= 64.  Register-staged, double-buffered K steps
 // of 16 read along V's unit stride.
-template <int TM>
+template <int TM, int CW>
 __device__ __forceinline__ void panel_product(const StepArgs &a, Smem &sm, int64_t r0, int nr,
-                                              int64_t c0, int nc, int w, const Owner<TM> &o,
-                                              double (&acc)[TM][4])
+                                              int64_t c0, int nc, int w, const Owner<TM, CW> &o,
+                                              double (&acc)[TM][CW])
 {
-    constexpr int ROWS = 16 * TM;
+    constexpr int ROWS = 16 * TM, COLS = 16 * CW;
     const int tid = threadIdx.x;
     const bool rowfast = a.V.rs == 1;
     const View<double> Pr = a.V.sub(r0, a.k0), Pc = a.V.sub(c0, a.k0);
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    double ra[TM], rb[4];
+        for (int j = 0; j < CW; ++j) acc[i][j] = 0.0;
+    double ra[TM], rb[CW];
+    // element q of this thread's share of a (R rows x 16 k) block: consecutive
+    // threads along V's unit stride
+    auto at = [&](int R, int q, int &i, int &k) {
+        if (rowfast) { i = tid % R; k = tid / R + (kTh / R) * q; }
+        else { k = tid % kBk; i = tid / kBk + 16 * q; }
+    };
     auto load = [&](int kb) {
 #pragma unroll
         for (int q = 0; q < TM; ++q) {
             int i, k;
-            if (rowfast) { i = tid % ROWS; k = kb + tid / ROWS + (kTh / ROWS) * q; }
-            else { k = kb + tid % kBk; i = tid / kBk + 16 * q; }
-            ra[q] = (i < nr && k < w) ? Pr(i, k) : 0.0;
+            at(ROWS, q, i, k);
+            ra[q] = (i < nr && kb + k < w) ? Pr(i, kb + k) : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < CW; ++q) {
             int i, k;
-            if (rowfast) { i = tid % kT; k = kb + tid / kT + 4 * q; }
-            else { k = kb + tid % kBk; i = tid / kBk + 16 * q; }
-            rb[q] = (i < nc && k < w) ? Pc(i, k) : 0.0;
+            at(COLS, q, i, k);
+            rb[q] = (i < nc && kb + k < w) ? Pc(i, kb + k) : 0.0;
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
         for (int q = 0; q < TM; ++q) {
             int i, k;
-            if (rowfast) { i = tid % ROWS; k = tid / ROWS + (kTh / ROWS) * q; }
-            else { k = tid % kBk; i = tid / kBk + 16 * q; }
+            at(ROWS, q, i, k);
             sm.As[buf][k][i] = ra[q];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < CW; ++q) {
             int i, k;
-            if (rowfast) { i = tid % kT; k = tid / kT + 4 * q; }
-            else { k = tid % kBk; i = tid / kBk + 16 * q; }
+            at(COLS, q, i, k);
             sm.Bs[buf][k][i] = rb[q];
         }
     };
@@ -148,20 +159,23 @@ __device__ __forceinline__ void panel_product(const StepArgs &a, Smem &sm, int64
         if (o.active) {
 #pragma unroll
             for (int kk = 0; kk < kBk; ++kk) {
-                double av[TM];
+                double av[TM], bv[CW];
 #pragma unroll
                 for (int i = 0; i < TM; i += 2) {
                     const double2 t2 = *reinterpret_cast<const double2 *>(&sm.As[buf][kk][o.ry * TM + i]);
                     av[i] = t2.x;
                     av[i + 1] = t2.y;
                 }
-                const double2 b01 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][o.cx * 4]);
-                const double2 b23 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][o.cx * 4 + 2]);
-                const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+                for (int j = 0; j < CW; j += 2) {
+                    const double2 t2 = *reinterpret_cast<const double2 *>(&sm.Bs[buf][kk][o.cx * CW + j]);
+                    bv[j] = t2.x;
+                    bv[j + 1] = t2.y;
+                }
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                    for (int j = 0; j < CW; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
             }
         }
     }
@@ -170,25 +184,36 @@ __device__ __forceinline__ void panel_product(const StepArgs &a, Smem &sm, int64
 
 // T = V(r0.., c0..) - acc for the owned blocks of the nr x nc tile (lower
 // part only when `lower`), into shared memory; entries outside are zero.
-template <int TM>
+template <int TM, int CW>
 __device__ __forceinline__ void updated_tile_to_smem(const StepArgs &a, Smem &sm, int64_t r0, int nr,
                                                      int64_t c0, int nc, bool lower,
-                                                     const Owner<TM> &o, const double (&acc)[TM][4])
+                                                     const Owner<TM, CW> &o,
+                                                     const double (&acc)[TM][CW])
 {
     if (!o.active) return;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = o.ry * TM + i, c = o.cx * 4 + j;
+        for (int j = 0; j < CW; ++j) {
+            const int r = o.ry * TM + i, c = o.cx * CW + j;
             const bool in = r < nr && c < nc && (!lower || c <= r);
             sm.T[r][c] = in ? a.V(r0 + r, c0 + c) - acc[i][j] : 0.0;
         }
 }
 
-template <int STRIP>
+// Element e of a rows x cols block written or read along V's unit stride.
+__device__ __forceinline__ void block_elem(const View<double> &V, int e, int rows, int cols, int &i,
+                                           int &j)
+{
+    if (V.rs == 1) { i = e % rows; j = e / rows; }
+    else { j = e % cols; i = e / cols; }
+}
+
+template <int PW, int STRIP>
 __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
 {
+    static_assert(PW == 32 || PW == 64, "panel width");
+    constexpr int CW = PW / 16;       // columns per thread in a panel tile's update
     constexpr int STM = STRIP / 16;   // rows per thread in a strip's update
     extern __shared__ __align__(16) unsigned char step_smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(step_smem_raw);
@@ -202,12 +227,14 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
     int32_t *flag = a.sync + 1;
 
     if (t == 0) {
-        // ---- diagonal tile of panel k+1: update (its lower blocks only), then
-        // unblocked Cholesky
-        const Owner<4> o(true);
-        double acc[4][4];
-        panel_product<4>(a, sm, a.k1, wn, a.k1, wn, w, o, acc);
-        updated_tile_to_smem<4>(a, sm, a.k1, wn, a.k1, wn, true, o, acc);
+        // ---- diagonal tile of panel k+1: update (its lower blocks only when
+        // 64 wide; a 32-wide tile spreads over all warps), then unblocked
+        // Cholesky
+        constexpr int DM = PW == 64 ? 4 : 2;
+        const Owner<DM, CW> o(PW == 64);
+        double acc[DM][CW];
+        panel_product<DM, CW>(a, sm, a.k1, wn, a.k1, wn, w, o, acc);
+        updated_tile_to_smem<DM, CW>(a, sm, a.k1, wn, a.k1, wn, true, o, acc);
         __syncthreads();
         const int tx = tid % 16, ty = tid / 16;
         int fail = -1;
@@ -238,9 +265,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
             }
             return;
         }
-        for (int e = tid; e < kT * kT; e += kTh) {
-            const int u = e % kT, v = e / kT;
-            const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;   // along the unit stride
+        for (int e = tid; e < PW * PW; e += kTh) {
+            int i, j;
+            block_elem(a.V, e, PW, PW, i, j);
             if (i < wn && j <= i) a.V(a.k1 + i, a.k1 + j) = (i == j) ? sm.sq[j] : sm.T[i][j];
         }
         __threadfence();
@@ -253,10 +280,10 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
         // ---- a STRIP-row strip of panel k+1: update, wait for the diagonal tile, solve
         const int64_t r0 = a.k2 + (t - 1) * STRIP;
         const int nr = (int)(a.m - r0 < STRIP ? a.m - r0 : STRIP);
-        const Owner<STM> o(false);
-        double acc[STM][4];
-        panel_product<STM>(a, sm, r0, nr, a.k1, wn, w, o, acc);
-        updated_tile_to_smem<STM>(a, sm, r0, nr, a.k1, wn, false, o, acc);
+        const Owner<STM, CW> o(false);
+        double acc[STM][CW];
+        panel_product<STM, CW>(a, sm, r0, nr, a.k1, wn, w, o, acc);
+        updated_tile_to_smem<STM, CW>(a, sm, r0, nr, a.k1, wn, false, o, acc);
         if (tid == 0) {
             const uint64_t t0 = step_globaltimer();
             int f = 0;
@@ -274,9 +301,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
             // The diagonal tile failed (info is set) or never came: the strip is
             // left as NaN so that the failure cannot pass unnoticed.
             if (sm.flag == 0)
-                for (int e = tid; e < kT * kT; e += kTh) {
-                    const int u = e % kT, v = e / kT;
-                    const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
+                for (int e = tid; e < STRIP * PW; e += kTh) {
+                    int i, j;
+                    block_elem(a.V, e, STRIP, PW, i, j);
                     if (i < nr && j < wn) a.V(r0 + i, a.k1 + j) = __longlong_as_double(0x7ff8000000000000ll);
                 }
             return;
@@ -284,9 +311,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
         // the new diagonal factor tile, from L2 (another SM wrote it in this
         // launch); unrolled so that each thread's loads are in flight together
 #pragma unroll
-        for (int q = 0; q < kT * kT / kTh; ++q) {
-            const int e = tid + q * kTh, u = e % kT, v = e / kT;
-            const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
+        for (int q = 0; q < PW * PW / kTh; ++q) {
+            int i, j;
+            block_elem(a.V, tid + q * kTh, PW, PW, i, j);
             if (i < wn && j <= i) sm.Ld[i][j] = __ldcg(&a.V(a.k1 + i, a.k1 + j));
         }
         __syncthreads();
@@ -303,9 +330,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
             for (int c = j + 1 + grp; c < wn; c += kGroups) xr[c] -= xj * sm.Ld[c][j];
             __syncthreads();
         }
-        for (int e = tid; e < kT * kT; e += kTh) {
-            const int u = e % kT, v = e / kT;
-            const int i = a.V.rs == 1 ? u : v, j = a.V.rs == 1 ? v : u;
+        for (int e = tid; e < STRIP * PW; e += kTh) {
+            int i, j;
+            block_elem(a.V, e, STRIP, PW, i, j);
             if (i < nr && j < wn) a.V(r0 + i, a.k1 + j) = sm.T[i][j];
         }
         return;
@@ -320,9 +347,9 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
     const int64_t tj = b - ti * (ti + 1) / 2;
     const int64_t r0 = a.k2 + ti * kT, c0 = a.k2 + tj * kT;
     const int nr = (int)(a.m - r0 < kT ? a.m - r0 : kT), nc = (int)(a.m - c0 < kT ? a.m - c0 : kT);
-    const Owner<4> o(false);
+    const Owner<4, 4> o(false);
     double acc[4][4];
-    panel_product<4>(a, sm, r0, nr, c0, nc, w, o, acc);
+    panel_product<4, 4>(a, sm, r0, nr, c0, nc, w, o, acc);
     const int tx = tid % 16, ty = tid / 16;
     double cin[4][4];
 #pragma unroll
@@ -344,38 +371,44 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
 
 }  // namespace
 
+int potrf_step_width(int64_t m)
+{
+    return m <= kNarrowPanels ? 32 : kT;
+}
+
 size_t potrf_step_sync_words(int64_t m)
 {
-    const int64_t np = (m + kT - 1) / kT;
+    const int64_t pw = potrf_step_width(m), np = (m + pw - 1) / pw;
     return (size_t)(2 * (np > 1 ? np - 1 : 1));
+}
+
+template <int PW, int STRIP>
+static cudaError_t launch_step(cudaStream_t st, const StepArgs &a, int64_t grid)
+{
+    const int smem = (int)sizeof(Smem);
+    cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel<PW, STRIP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    potrf_step_kernel<PW, STRIP><<<(unsigned)grid, kTh, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, int32_t *info,
                        int64_t base, int32_t *sync)
 {
-    const int64_t k1 = k0 + kT < m ? k0 + kT : m;
+    const int64_t pw = potrf_step_width(m);
+    const int64_t k1 = k0 + pw < m ? k0 + pw : m;
     if (k1 >= m) return cudaSuccess;                  // no next panel
-    const int64_t k2 = k1 + kT < m ? k1 + kT : m;
+    const int64_t k2 = k1 + pw < m ? k1 + pw : m;
     const int64_t rest = (m - k2 + kT - 1) / kT;      // row tiles of A(k2:m, k2:m)
     const int64_t strip = m <= kSmallStrips ? 32 : 64;
     const int64_t strips = (m - k2 + strip - 1) / strip;
     StepArgs a{V, m, k0, k1, k2, (int)strips, rest * (rest + 1) / 2, info, base, sync};
     const int64_t grid = 1 + a.nstrip + a.nbulk;
     if (grid > INT32_MAX) return cudaErrorInvalidValue;
-    const int smem = (int)sizeof(Smem);
-    if (strip == 32) {
-        cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel<32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        potrf_step_kernel<32><<<(unsigned)grid, kTh, smem, st>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(potrf_step_kernel<64>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        potrf_step_kernel<64><<<(unsigned)grid, kTh, smem, st>>>(a);
-    }
-    note_launch();
-    return cudaGetLastError();
+    if (pw == 32) return strip == 32 ? launch_step<32, 32>(st, a, grid) : launch_step<32, 64>(st, a, grid);
+    return strip == 32 ? launch_step<64, 32>(st, a, grid) : launch_step<64, 64>(st, a, grid);
 }
 
 }  // namespace rfp

@@ -96,21 +96,38 @@ void stage_mark(cudaStream_t st, const char *name);   // end of one of its steps
 
 // ---- launchers (all enqueue on `st`, return cudaSuccess or the launch error)
 
-// Tile shape of one gemm_nt launch: the large tile (64 x 64 FP64, 128 x 128
-// FP32) or the small one (32 x 32 FP64, 64 x 64 FP32), whichever has the
-// smaller estimated time: waves x (CTAs per SM) x (tile area), the CTAs of a
-// wave sharing their SM's pipes and each doing work proportional to its tile
-// area.  The small tile must win by 5%.  In-place calls (A or B aliasing C) always take
-// the large tile, whose width covers the 64-wide diagonal blocks the
-// in-place products work on.
+// In-place gemm_nt calls (A or B aliasing C): which elements of C a CTA
+// must own whole, so that it reads only what it writes itself.
+//   GEMM_INPLACE_COLS  C(:, j) is computed from C(:, j) (M <= 64): a CTA
+//                      holds all M rows of its columns;
+//   GEMM_INPLACE_ROWS  C(i, :) is computed from C(i, :) (N <= 64): a CTA
+//                      holds all N columns of its rows.
+enum { GEMM_INPLACE_NONE = 0, GEMM_INPLACE_COLS = 1, GEMM_INPLACE_ROWS = 2 };
+
+// Tile shape of one gemm_nt launch.  Out-of-place: the large tile (64 x 64
+// FP64, 128 x 128 FP32) or the small one (32 x 32 FP64, 64 x 64 FP32),
+// whichever has the smaller estimated time: waves x (CTAs per SM) x (tile
+// area), the CTAs of a wave sharing their SM's pipes and each doing work
+// proportional to its tile area.  The small tile must win by 5%.  In-place
+// FP64 calls take 64 x 16 column strips (GEMM_INPLACE_COLS) or 16 x 64 row
+// strips (GEMM_INPLACE_ROWS): four times the CTAs of the 64 x 64 tile, each
+// with a quarter of its serial work, since these products sit on the
+// latency-bound chain of the blocked triangle inverse and LAUUM.  In-place
+// FP32 calls take the large tile, which covers a 64-wide block either way.
+enum { GEMM_TILE_BIG = 0, GEMM_TILE_SMALL = 1, GEMM_TILE_COLSTRIP = 2, GEMM_TILE_ROWSTRIP = 3 };
 struct GemmTileChoice {
     int bm, bn;
-    bool small;
+    int kind;
 };
-inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, bool inplace,
+inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, int inplace,
                                        int elem_size, int num_sms, int occ_big, int occ_small)
 {
     const int big = elem_size == 8 ? 64 : 128, sml = elem_size == 8 ? 32 : 64;
+    if (inplace != GEMM_INPLACE_NONE) {
+        if (elem_size == 8 && inplace == GEMM_INPLACE_COLS && M <= 64) return {64, 16, GEMM_TILE_COLSTRIP};
+        if (elem_size == 8 && inplace == GEMM_INPLACE_ROWS && N <= 64) return {16, 64, GEMM_TILE_ROWSTRIP};
+        return {big, big, GEMM_TILE_BIG};
+    }
     auto ctas = [&](int64_t t) {
         const int64_t gm = (M + t - 1) / t, gn = (N + t - 1) / t;
         if (cmode != MASK_LOWER) return gm * gn;
@@ -126,9 +143,9 @@ inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, bool inp
         const int64_t slots = (int64_t)num_sms * occ;
         return (double)((c + slots - 1) / slots) * occ * (double)t * t;
     };
-    if (!inplace && est(ctas(sml), occ_small, sml) < 0.95 * est(ctas(big), occ_big, big))
-        return {sml, sml, true};
-    return {big, big, false};
+    if (est(ctas(sml), occ_small, sml) < 0.95 * est(ctas(big), occ_big, big))
+        return {sml, sml, GEMM_TILE_SMALL};
+    return {big, big, GEMM_TILE_BIG};
 }
 int device_sm_count();   // SMs of the current device (cached per device)
 // Resident CTAs per SM of the large / small gemm_nt configuration for
@@ -137,14 +154,14 @@ void gemm_occupancy(int elem_size, int *occ_big, int *occ_small);
 
 // C(M x N) = alpha * A(M x K) * B(N x K)^T + beta * C.  cmode MASK_LOWER
 // writes only i >= j.  amask / bmask treat an operand as triangular (entries
-// outside the triangle read as zero and are never loaded).  A may alias C
-// when every C tile's rows cover the whole K range of A (N <= tile width),
-// which the in-place triangular products rely on.  abort: if non-null and
-// *abort != 0 at kernel start, the kernel does nothing.
+// outside the triangle read as zero and are never loaded).  A or B may
+// alias C when `inplace` says which of C's dimensions is tied (the C
+// elements each CTA reads are then among those it writes).  abort: if
+// non-null and *abort != 0 at kernel start, the kernel does nothing.
 template <typename T>
 cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
                     int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
-                    const int32_t *abort, bool inplace = false);
+                    const int32_t *abort, int inplace = GEMM_INPLACE_NONE);
 
 // gemm_nt with K split into `splits` chunks (one launch, grid z = chunk), the
 // chunk products written to work (splits x M x N, dense) and summed into C in
@@ -260,12 +277,14 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
                       int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
                       const int32_t *abort = nullptr, double alpha = 1.0);
 // One panel step of the FP64 lookahead Cholesky of an m x m lower triangle V
-// (potrf_step.cu), panel k = [k0, k0 + 64) already factored: the trailing
-// update with it, and the factorization of panel k + 1 (its diagonal tile
-// and the rows below), in one launch.  sync: 2 int32 per step, zero before
-// the launch (potrf_step_sync_words(m) for all steps of one factorization).
-// info as for potrf_tile (global index base + column + 1; the launch does
-// nothing if *info is already non-zero).
+// (potrf_step.cu), panel k = [k0, k0 + pw) already factored, pw =
+// potrf_step_width(m) (32 or 64): the trailing update with it, and the
+// factorization of panel k + 1 (its diagonal tile and the rows below), in
+// one launch.  sync: 2 int32 per step, zero before the launch
+// (potrf_step_sync_words(m) for all steps of one factorization).  info as
+// for potrf_tile (global index base + column + 1; the launch does nothing if
+// *info is already non-zero).
+int potrf_step_width(int64_t m);
 size_t potrf_step_sync_words(int64_t m);
 cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, int32_t *info,
                        int64_t base, int32_t *sync);

@@ -28,10 +28,16 @@ struct GemmCfg {
     static constexpr int PAD = 16 / (int)sizeof(T);
     static_assert(NT % BM == 0 && NT % BN == 0 && NT % BK == 0, "loader mapping");
 };
+// FP64: 256 threads in every shape, so that a CTA alone on an SM keeps all
+// four of its schedulers issuing to the FP64 pipe (small grids are common
+// on the latency-bound chains); 2 x 2 per thread is enough reuse at FP64's
+// arithmetic rate.  The strips are the in-place shapes (gemm_tile_choice).
 template <typename T> struct GemmBig;
 template <typename T> struct GemmSmall;
 template <> struct GemmBig<double> { using C = GemmCfg<double, 64, 64, 4, 4>; };
-template <> struct GemmSmall<double> { using C = GemmCfg<double, 32, 32, 4, 4>; };
+template <> struct GemmSmall<double> { using C = GemmCfg<double, 32, 32, 2, 2>; };
+using GemmColStrip = GemmCfg<double, 64, 16, 2, 2>;
+using GemmRowStrip = GemmCfg<double, 16, 64, 2, 2>;
 template <> struct GemmBig<float> { using C = GemmCfg<float, 128, 128, 8, 8>; };
 template <> struct GemmSmall<float> { using C = GemmCfg<float, 64, 64, 4, 4>; };
 
@@ -250,7 +256,7 @@ cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int
 template <typename T>
 cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
                     int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
-                    const int32_t *abort, bool inplace)
+                    const int32_t *abort, int inplace)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 && beta == T(1)) return cudaSuccess;
@@ -259,8 +265,12 @@ cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M,
     gemm_occupancy((int)sizeof(T), &occ_big, &occ_small);
     const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, inplace, (int)sizeof(T),
                                                device_sm_count(), occ_big, occ_small);
-    if (tc.small) launch_gemm<T, typename GemmSmall<T>::C>(st, g);
-    else launch_gemm<T, typename GemmBig<T>::C>(st, g);
+    if (tc.kind == GEMM_TILE_SMALL) launch_gemm<T, typename GemmSmall<T>::C>(st, g);
+    else if constexpr (sizeof(T) == 8) {
+        if (tc.kind == GEMM_TILE_COLSTRIP) launch_gemm<T, GemmColStrip>(st, g);
+        else if (tc.kind == GEMM_TILE_ROWSTRIP) launch_gemm<T, GemmRowStrip>(st, g);
+        else launch_gemm<T, typename GemmBig<T>::C>(st, g);
+    } else launch_gemm<T, typename GemmBig<T>::C>(st, g);
     note_launch();
     return cudaGetLastError();
 }
@@ -753,7 +763,7 @@ cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int6
 
 #define RFP_INSTANTIATE(T)                                                                    \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
-                                    int64_t, T, T, int, int, int, const int32_t *, bool);     \
+                                    int64_t, T, T, int, int, int, const int32_t *, int);      \
     template cudaError_t gemm_nt_splitk<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t,   \
                                            int64_t, int64_t, T, T, int, int, int,             \
                                            const int32_t *, int, T *);                        \

@@ -138,7 +138,7 @@ int device_sm_count() { return g_emu_sms; }
 template <typename T>
 cudaError_t gemm_nt(cudaStream_t, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N, int64_t K,
                     T alpha, T beta, int cmode, int amask, int bmask, const int32_t *abort,
-                    bool inplace)
+                    int inplace)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0 && beta == T(1)) return cudaSuccess;
@@ -459,24 +459,40 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
 }
 
 // potrf_step: one ordered launch (ticket order: the diagonal tile of panel
-// k+1, its 32-row (m <= 2048) or 64-row strips, then the lower tiles of A(k2:m, k2:m)) with the
-// kernel's own tile decomposition.  Besides the bounds checks, every element
-// one task writes is recorded, and a read of it by another task is a
-// violation unless it is the new diagonal tile read by a strip (which the
-// kernel does only after the diagonal task's flag).
+// k+1, its 32-row (m <= 2048) or 64-row strips, then the lower 64 x 64 tiles
+// of A(k2:m, k2:m)) with the kernel's own tile decomposition; panels 32 wide
+// for m <= 2048, 64 beyond.  Besides the bounds checks, every element one
+// task writes is recorded, and a read of it by another task is a violation
+// unless it is the new diagonal tile read by a strip (which the kernel does
+// only after the diagonal task's flag).
+// The kernel's rules (panels 32 wide up to m = 2048, strips 32 rows up to
+// m = 2048); emu_set_step_rules lowers the bounds so that small orders also
+// take the 64-wide panels and 64-row strips.
+static int64_t g_narrow_panels = 2048, g_small_strips = 2048;
+extern "C" void emu_set_step_rules(long narrow_panels, long small_strips)
+{
+    g_narrow_panels = narrow_panels;
+    g_small_strips = small_strips;
+}
+
+int potrf_step_width(int64_t m)
+{
+    return m <= g_narrow_panels ? 32 : 64;
+}
+
 size_t potrf_step_sync_words(int64_t m)
 {
-    const int64_t np = (m + 63) / 64;
+    const int64_t pw = potrf_step_width(m), np = (m + pw - 1) / pw;
     return (size_t)(2 * (np > 1 ? np - 1 : 1));
 }
 
 cudaError_t potrf_step(cudaStream_t, View<double> V, int64_t m, int64_t k0, int32_t *info,
                        int64_t base, int32_t *sync)
 {
-    const int64_t T = 64, k1 = std::min(k0 + T, m);
+    const int64_t T = 64, P = potrf_step_width(m), k1 = std::min(k0 + P, m);
     if (k1 >= m) return cudaSuccess;
-    const int64_t k2 = std::min(k1 + T, m), w = k1 - k0, wn = k2 - k1;
-    const int64_t S = m <= 2048 ? 32 : 64;           // rows per strip task
+    const int64_t k2 = std::min(k1 + P, m), w = k1 - k0, wn = k2 - k1;
+    const int64_t S = m <= g_small_strips ? 32 : 64;  // rows per strip task
     const int64_t rest = (m - k2 + T - 1) / T, nstrip = (m - k2 + S - 1) / S, nbulk = rest * (rest + 1) / 2;
     Launch L;
     L.ordered = true;
@@ -1094,7 +1110,7 @@ template cudaError_t batched_run<float>(int64_t, const void *, float *, float *,
 
 #define EMU_INST(T)                                                                                  \
     template cudaError_t gemm_nt<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, int64_t, \
-                                    T, T, int, int, int, const int32_t *, bool);                     \
+                                    T, T, int, int, int, const int32_t *, int);                      \
     template cudaError_t gemm_nt_splitk<T>(cudaStream_t, View<T>, View<T>, View<T>, int64_t, int64_t, \
                                            int64_t, T, T, int, int, int, const int32_t *, int, T *); \
     template cudaError_t trsm_strip<T>(cudaStream_t, View<T>, View<T>, int64_t, int, int, T,         \

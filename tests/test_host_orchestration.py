@@ -42,6 +42,7 @@ def emu_lib(tmp_path_factory):
     raw.emu_message.restype = ctypes.c_char_p
     raw.emu_launches.restype = ctypes.c_long
     raw.emu_set_sms.argtypes = [ctypes.c_int]
+    raw.emu_set_step_rules.argtypes = [ctypes.c_long, ctypes.c_long]
     return lib
 
 
@@ -119,6 +120,32 @@ def test_emulated_path_matches_oracle(emu, transr, uplo, n):
     want = oracle.unpack(transr, uplo, n, arf, np.full((n, n), 7.0))
     np.testing.assert_array_equal(Aout[:n], want)
     assert np.all(Aout[n:] == 7.0)
+
+
+@pytest.mark.parametrize("transr,uplo", LAYOUTS)
+@pytest.mark.parametrize("n", [129, 258, 400])
+@pytest.mark.parametrize("rules", [(0, 0), (0, 4096), (4096, 0)],
+                         ids=["panel64_strip64", "panel64_strip32", "panel32_strip64"])
+def test_emulated_step_rules(emu_lib, transr, uplo, n, rules):
+    """The lookahead steps with 64-wide panels (the rule for triangles above
+    order 2048), and 32-wide panels with 64-row strips, at orders the emulator
+    covers: same bounds, ownership and ordering checks, same factor as the
+    oracle."""
+    raw = emu_lib.lib
+    raw.emu_set_sms(152)
+    raw.emu_set_step_rules(*rules)
+    try:
+        A = gen.spd_bbt(n, seed=n + 11)
+        arf = oracle.pack(transr, uplo, A)
+        info = np.zeros(1, dtype=np.int32)
+        _register(emu_lib, arf, info)
+        ref_f, ref_info = oracle.pftrf(transr, uplo, n, arf)
+        emu_lib.rfp_dpftrf(transr, uplo, n, arf, info, 0)
+        _ok(emu_lib)
+        assert info[0] == ref_info == 0
+        assert np.max(np.abs(arf - ref_f)) <= 1e-13 * max(1.0, np.max(np.abs(ref_f)))
+    finally:
+        raw.emu_set_step_rules(2048, 2048)
 
 
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
