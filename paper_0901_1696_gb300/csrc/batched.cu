@@ -93,9 +93,76 @@ __device__ __forceinline__ void ld4(const float *p, float (&v)[4])
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
 
+// The FP32 panel in registers: the kb x kb diagonal block by warp 0 (lane r
+// holds row r; each column's entries reach the other lanes by shuffles, so
+// the block takes no barrier), then every row below it by one thread, solved
+// against the block right-looking (l_rc = a_rc / l_cc, then a_rq -= l_rc l_qc
+// for q > c).  Each element sees the same operations in the same order as in
+// the column loop of factor_one; only the barriers between columns go.
+// Returns the failing column or -1 (the panel is then left as it was read).
+template <typename T, int NB>
+__device__ __forceinline__ int panel_in_registers(T *P, int kb, int rows, T *rinv, int *s_fail)
+{
+    constexpr int LDC = kPanelLd;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        T d[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) d[q] = (q < kb && lane < kb && q <= lane) ? P[q * LDC + lane] : T(0);
+        int fail = -1;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+            if (c < kb && fail < 0) {   // uniform across the warp
+                const T piv = __shfl_sync(0xffffffffu, d[c], c);
+                if (!(piv > T(0))) {
+                    fail = c;
+                } else {
+                    const T sq = sqrt(piv), ri = T(1) / sq;
+                    d[c] = lane == c ? sq : d[c] * ri;
+                    if (lane == 0) rinv[c] = ri;
+#pragma unroll
+                    for (int q = 1; q < NB; ++q) {   // constant trip count: d stays in registers
+                        if (q > c) {
+                            const T lqc = __shfl_sync(0xffffffffu, d[c], q);
+                            if (q < kb && lane >= q) d[q] -= d[c] * lqc;
+                        }
+                    }
+                }
+            }
+        }
+        if (fail < 0)
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < kb && lane < kb && q <= lane) P[q * LDC + lane] = d[q];
+        if (lane == 0) *s_fail = fail;
+    }
+    __syncthreads();
+    const int fail = *s_fail;
+    if (fail >= 0) return fail;
+    for (int r = kb + tid; r < rows; r += blockDim.x) {
+        T a[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) a[q] = q < kb ? P[q * LDC + r] : T(0);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+            if (c < kb) {
+                a[c] *= rinv[c];
+#pragma unroll
+                for (int q = c + 1; q < NB; ++q)
+                    if (q < kb) a[q] -= a[c] * P[c * LDC + q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+            if (q < kb) P[q * LDC + r] = a[q];
+    }
+    __syncthreads();
+    return -1;
+}
+
 // Factor one matrix in place; returns 0 or the 1-based failing index.
 template <typename T, int NB>
-__device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fail)
+__device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fail, T *rbuf)
 {
     constexpr int LDC = kPanelLd;
     const int tid = threadIdx.x;
@@ -109,7 +176,13 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
                 P[c * LDC + r] = (r >= c && r < rows) ? *A.at(k0 + r, k0 + c) : T(0);
         if (tid == 0) *s_fail = -1;
         __syncthreads();
-        // 2. right-looking Cholesky of the rows x kb panel, column by column
+        // 2. right-looking Cholesky of the rows x kb panel: in registers in
+        // FP32, whose pipe outruns the column loop's barriers; column by
+        // column in FP64, whose pipe the column loop keeps busy
+        if constexpr (sizeof(T) == 4) {
+            const int f = panel_in_registers<T, NB>(P, kb, rows, rbuf, s_fail);
+            if (f >= 0) return (int)(k0 + f + 1);
+        } else
         for (int c = 0; c < kb; ++c) {
             if (tid == 0) {   // pivot; scale the panel's own rows c+1 .. kb-1 of column c
                 const T d = P[c * LDC + c];
@@ -152,11 +225,20 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
         if (m > 0) {
             const int tm = (m + 3) / 4;
             const int ntiles = tm * (tm + 1) / 2;
+            // Consecutive threads take consecutive tiles along the unit stride
+            // of the block holding most of the trailing matrix (S, or T2 once
+            // the panel is past T1): down a tile column when its columns are
+            // contiguous, along a tile row otherwise.  Column order of the
+            // lower tiles is the reverse of the row order of the same
+            // triangle reflected about its anti-diagonal.
+            const bool colfast = (k0 + kb >= A.n1 ? A.t2.rs : A.s.rs) == 1;
             for (int t = tid; t < ntiles; t += blockDim.x) {
-                int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-                while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-                while (ti * (ti + 1) / 2 > t) --ti;
-                const int tj = t - ti * (ti + 1) / 2;
+                const int u = colfast ? ntiles - 1 - t : t;
+                int ui = (int)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+                while ((ui + 1) * (ui + 2) / 2 <= u) ++ui;
+                while (ui * (ui + 1) / 2 > u) --ui;
+                const int uj = u - ui * (ui + 1) / 2;
+                const int ti = colfast ? tm - 1 - uj : ui, tj = colfast ? tm - 1 - ui : uj;
                 const T *pa = P + kb + 4 * ti, *pb = P + kb + 4 * tj;   // zero beyond `rows`
                 // the tile's current values first: their load latency overlaps
                 // the multiply-adds below (nothing in the loop writes them)
@@ -319,9 +401,10 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(PlanHeader *hdr,
                  bview(arf + e.arf, e.t2, e.ld), e.n1};
         const int nb = e.nb < MAXNB ? e.nb : MAXNB;
         int fail;
-        if (nb == 16) fail = factor_one<T, 16>(A, e.n, P, s_rinv, &s_fail);
-        else if (MAXNB >= 24 && nb == 24) fail = factor_one<T, (MAXNB >= 24 ? 24 : 16)>(A, e.n, P, s_rinv, &s_fail);
-        else fail = factor_one<T, MAXNB>(A, e.n, P, s_rinv, &s_fail);
+        if (nb == 16) fail = factor_one<T, 16>(A, e.n, P, s_rinv, &s_fail, rdiag);
+        else if (MAXNB >= 24 && nb == 24)
+            fail = factor_one<T, (MAXNB >= 24 ? 24 : 16)>(A, e.n, P, s_rinv, &s_fail, rdiag);
+        else fail = factor_one<T, MAXNB>(A, e.n, P, s_rinv, &s_fail, rdiag);
         if (threadIdx.x == 0) info[e.index] = fail;
         __syncthreads();
         // up to kMaxRhs right-hand sides per pass; the factor (n <= 512) stays in L2

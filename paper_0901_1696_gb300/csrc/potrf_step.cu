@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kT = 64;              // bulk tile width; the widest panel
 // Panel width: 32 for triangles up to kNarrowPanels, 64 beyond.
-constexpr int64_t kNarrowPanels = 2048;
+constexpr int64_t kNarrowPanels = 4096;
 // Rows of a panel strip task: 32 for triangles up to kSmallStrips (their
 // factorization is bound by the diagonal chain, which shorter strips
 // shorten), 64 beyond (fewer, more efficient tasks beside the bulk update).

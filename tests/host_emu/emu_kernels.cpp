@@ -461,14 +461,14 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
 // potrf_step: one ordered launch (ticket order: the diagonal tile of panel
 // k+1, its 32-row (m <= 2048) or 64-row strips, then the lower 64 x 64 tiles
 // of A(k2:m, k2:m)) with the kernel's own tile decomposition; panels 32 wide
-// for m <= 2048, 64 beyond.  Besides the bounds checks, every element one
+// for m <= 4096, 64 beyond.  Besides the bounds checks, every element one
 // task writes is recorded, and a read of it by another task is a violation
 // unless it is the new diagonal tile read by a strip (which the kernel does
 // only after the diagonal task's flag).
-// The kernel's rules (panels 32 wide up to m = 2048, strips 32 rows up to
+// The kernel's rules (panels 32 wide up to m = 4096, strips 32 rows up to
 // m = 2048); emu_set_step_rules lowers the bounds so that small orders also
 // take the 64-wide panels and 64-row strips.
-static int64_t g_narrow_panels = 2048, g_small_strips = 2048;
+static int64_t g_narrow_panels = 4096, g_small_strips = 2048;
 extern "C" void emu_set_step_rules(long narrow_panels, long small_strips)
 {
     g_narrow_panels = narrow_panels;

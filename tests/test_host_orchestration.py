@@ -128,9 +128,9 @@ def test_emulated_path_matches_oracle(emu, transr, uplo, n):
                          ids=["panel64_strip64", "panel64_strip32", "panel32_strip64"])
 def test_emulated_step_rules(emu_lib, transr, uplo, n, rules):
     """The lookahead steps with 64-wide panels (the rule for triangles above
-    order 2048), and 32-wide panels with 64-row strips, at orders the emulator
-    covers: same bounds, ownership and ordering checks, same factor as the
-    oracle."""
+    order 4096), and 32-wide panels with 64-row strips (orders 2049 .. 4096),
+    at orders the emulator covers: same bounds, ownership and ordering checks,
+    same factor as the oracle."""
     raw = emu_lib.lib
     raw.emu_set_sms(152)
     raw.emu_set_step_rules(*rules)
@@ -145,7 +145,7 @@ def test_emulated_step_rules(emu_lib, transr, uplo, n, rules):
         assert info[0] == ref_info == 0
         assert np.max(np.abs(arf - ref_f)) <= 1e-13 * max(1.0, np.max(np.abs(ref_f)))
     finally:
-        raw.emu_set_step_rules(2048, 2048)
+        raw.emu_set_step_rules(4096, 2048)
 
 
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
