@@ -5,7 +5,7 @@
 //   forward:  L11 Y1 = B1;  B2 -= L21 Y1;  L22 Y2 = B2
 //   backward: L22^T X2 = Y2;  Y1 -= L21^T X2;  L11^T X1 = Y1.
 // Both directions are block substitutions on the n x n lower triangle L,
-// whose 64-row blocks are cut separately in T1 (rows [0, n1)) and T2 (rows
+// whose R-row blocks are cut separately in T1 (rows [0, n1)) and T2 (rows
 // [n1, n)), so every block of L lies inside one of T1, S or T2:
 //   forward, block row b:   X_b = L_bb^{-1} (B_b - sum_{j<b} L_bj X_j)
 //   backward, block row b:  X_b = L_bb^{-T} (Y_b - sum_{j>b} L_jb^T X_j).
@@ -21,14 +21,16 @@
 // that sees it gives up, and each task that gives up writes NaN into its own
 // block of X, so an incomplete solve cannot pass for a result.
 //
-// Per task: 128 threads, each owning 4 rows x 2 columns of the 64 x 16
-// block in registers.  Blocks of L are streamed through shared memory in
-// 64 x 16 chunks (register-staged, double-buffered); X_j is read from L2
-// (ld.global.cg: other SMs wrote it during this launch).  The diagonal block
-// is then solved in shared memory by substitution, one warp per 4 columns,
-// each lane holding two rows, the solved value broadcast by shuffles.
+// Per task: 128 threads, each owning R/16 rows x 2 columns of the R x 16
+// block in registers (R = 32 or 64 rows).  Blocks of L are streamed through
+// shared memory in R x 16 chunks (register-staged, double-buffered); X_j is
+// read from L2 (ld.global.cg: other SMs wrote it during this launch).  The
+// diagonal block is then solved by substitution, one warp per 4 columns,
+// each lane holding one column of R/8 rows, the solved values handed out by
+// shuffles.
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "rfp_internal.cuh"
 
@@ -181,17 +183,26 @@ struct DiagSmem {
     double Bs[R][kG + 1];       // the block's right-hand side, redistributed
     double rinv[R];             // 1 / L_bb(j, j)
 };
+// 64-row blocks share one region between the update's staging and the
+// diagonal block; 32-row blocks keep both (26 KB), so that the diagonal
+// block is loaded before the task's first wait, off the critical path.
 template <int R>
-union SolveSmem {
+union SolveSmemShared {
     UpdateSmem<R> u;
     DiagSmem<R> d;
 };
+template <int R>
+struct SolveSmemSplit {
+    UpdateSmem<R> u;
+    DiagSmem<R> d;
+};
+template <int R>
+using SolveSmem = std::conditional_t<R == 32, SolveSmemSplit<R>, SolveSmemShared<R>>;
 
 template <bool TRANS, int R>
 __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 {
     constexpr int RM = R / 16;       // rows per thread in the update (16 row groups)
-    constexpr int H = R / 32;        // rows per lane in the substitution
     __shared__ __align__(16) SolveSmem<R> sm;
     __shared__ int s_ticket, s_ok;
 
@@ -221,6 +232,26 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
             const int r = ty * RM + m, cc = tx * 2 + c;
             acc[m][c] = (r < rows && cc < cols) ? a.alpha * __ldcg(&Xb(r, cc)) : 0.0;
         }
+
+    // The lower triangle of L_bb and the reciprocals of its pivots into
+    // shared memory.
+    auto load_diag = [&]() {
+        const View<double> D = lblock<R>(a, b, b);
+        const bool rowfast = D.rs == 1;
+        // unrolled by 8: eight loads per thread in flight at a time
+#pragma unroll 8
+        for (int q = 0; q < R * R / kThreads; ++q) {
+            const int e = tid + q * kThreads, u = e % R, v = e / R;
+            const int i = rowfast ? u : v, jj = rowfast ? v : u;
+            if (i < rows && jj <= i) sm.d.Ld[i][jj] = D(i, jj);
+        }
+        // Reciprocals of the pivots, formed once in parallel: on GB300's
+        // narrow FP64 pipe a division per lane per step would cost more
+        // than the substitution's multiply-adds.
+        if (tid < rows) sm.d.rinv[tid] = 1.0 / D(tid, tid);
+    };
+    constexpr bool kEarlyDiag = R == 32;
+    if (kEarlyDiag) load_diag();   // ordered before its use by the barriers below
 
     bool ok = true;
     // Off-diagonal blocks in solve order: forward j = 0 .. b-1, backward j = nb-1 .. b+1.
@@ -283,83 +314,59 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
         return;
     }
 
-    // Diagonal block: the lower triangle of L_bb into shared memory, the
-    // right-hand side from the accumulators, then substitution.
-    {
-        const View<double> D = lblock<R>(a, b, b);
-        const bool rowfast = D.rs == 1;
-        // unrolled by 8: eight loads per thread in flight at a time (this
-        // load is on the critical path of the block substitution)
-#pragma unroll 8
-        for (int q = 0; q < R * R / kThreads; ++q) {
-            const int e = tid + q * kThreads, u = e % R, v = e / R;
-            const int i = rowfast ? u : v, jj = rowfast ? v : u;
-            if (i < rows && jj <= i) sm.d.Ld[i][jj] = D(i, jj);
-        }
-        // Reciprocals of the pivots, formed once in parallel: on GB300's
-        // narrow FP64 pipe a division per lane per step would cost more
-        // than the substitution's multiply-adds.
-        if (tid < rows) sm.d.rinv[tid] = 1.0 / D(tid, tid);
-    }
-    // The right-hand side is redistributed through shared memory: lane l of
-    // warp w takes rows l (and l + 32 when R = 64) of columns 4w .. 4w + 3.
+    // Diagonal block (64-row blocks: loaded now, into the staging region),
+    // the right-hand side from the accumulators, then substitution.
+    if (!kEarlyDiag) load_diag();
 #pragma unroll
     for (int m = 0; m < RM; ++m)
 #pragma unroll
         for (int c = 0; c < 2; ++c) sm.d.Bs[ty * RM + m][tx * 2 + c] = acc[m][c];
     __syncthreads();
-    double v[H][4];
-#pragma unroll
-    for (int h = 0; h < H; ++h)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[h][c] = sm.d.Bs[lane + 32 * h][warp * 4 + c];
 
-    // Step j: row j is broadcast from its owner lane and scaled by the
-    // pivot's reciprocal; every lane then removes x_j from its later
-    // (forward) or earlier (backward) rows.  Indices into v are compile-time
-    // (no local memory).
-    for (int q = 0; q < rows; ++q) {
-        const int j = TRANS ? rows - 1 - q : q;
-        const int owner = j & 31;
-        const bool hi = H > 1 && j >= 32;
-        const double ri = sm.d.rinv[j];
-        double xj[4];
+    // Substitution.  Lane (lr, lc) = (lane / 4, lane % 4) of warp w holds
+    // column 4 w + lc of rows lr + 8 k, k < R / 8.  Step j: the four lanes
+    // holding row j scale it by the pivot's reciprocal (one instruction for
+    // the four columns), a shuffle hands each lane its column's x_j, and
+    // every lane removes x_j from its later (forward) or earlier (backward)
+    // rows; registers whose rows are all finished drop out of the step at
+    // compile time.  On GB300's FP64 pipe, where a warp instruction costs
+    // the same whatever its active lanes, this is about 3.5 instructions a
+    // step for 32-row blocks against 8 with one lane per row.
+    constexpr int K = R / 8;
+    const int lr = lane >> 2, lc = lane & 3, col = warp * 4 + lc;
+    double v[K];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const double own = hi ? v[H - 1][c] : v[0][c];
-            xj[c] = __shfl_sync(0xffffffffu, own, owner) * ri;
-        }
+    for (int k = 0; k < K; ++k) v[k] = sm.d.Bs[lr + 8 * k][col];
 #pragma unroll
-        for (int hh = 0; hh < H; ++hh) {
-            const int r = lane + 32 * hh;
-            if (r == j) {
+    for (int q = 0; q < R; ++q) {
+        const int j = TRANS ? R - 1 - q : q;
+        if (j < rows) {    // uniform
+            const int kj = j >> 3, oj = j & 7;
+            const double xj = __shfl_sync(0xffffffffu, v[kj] * sm.d.rinv[j], oj * 4 + lc);
+            if (lr == oj) v[kj] = xj;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) v[hh][c] = xj[c];
-            } else if (TRANS ? r < j : (r > j && r < rows)) {
-                const double l = TRANS ? sm.d.Ld[j][r] : sm.d.Ld[r][j];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) v[hh][c] = fma(-l, xj[c], v[hh][c]);
+            for (int k = 0; k < K; ++k) {
+                if (TRANS ? k > kj : k < kj) continue;
+                const int r = lr + 8 * k;
+                if (TRANS ? r < j : (r > j && r < rows)) {
+                    const double l = TRANS ? sm.d.Ld[j][r] : sm.d.Ld[r][j];
+                    v[k] = fma(-l, xj, v[k]);
+                }
             }
         }
     }
-    if (Xb.rs == 1) {      // lanes along X's rows: coalesced as held
+    // out through shared memory, along X's unit stride
+    __syncthreads();   // every lane is done reading Bs
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int cc = warp * 4 + c;
-            if (cc >= cols) continue;
+    for (int k = 0; k < K; ++k) sm.d.Bs[lr + 8 * k][col] = v[k];
+    __syncthreads();
+    if (Xb.rs == 1) {      // X's rows contiguous
 #pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const int r = lane + 32 * h;
-                if (r < rows) Xb(r, cc) = v[h][c];
-            }
+        for (int q = 0; q < R * kG / kThreads; ++q) {
+            const int r = tid % R, cc = tid / R + (kThreads / R) * q;
+            if (r < rows && cc < cols) Xb(r, cc) = sm.d.Bs[r][cc];
         }
-    } else {               // X's columns contiguous: regroup through shared memory
-        __syncthreads();   // every lane is done reading Bs
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int h = 0; h < H; ++h) sm.d.Bs[lane + 32 * h][warp * 4 + c] = v[h][c];
-        __syncthreads();
+    } else {               // X's columns contiguous
 #pragma unroll
         for (int q = 0; q < R * kG / kThreads; ++q) {
             const int cc = tid % kG, r = tid / kG + (kThreads / kG) * q;
