@@ -12,7 +12,8 @@
 //   tickets 1 .. P       32- or 64-row strips of panel k+1 below the diagonal: the
 //                        update, then (once the flag is up) the solve
 //                        X L_D^T = strip with the new diagonal tile;
-//   the other tickets    64 x 64 lower tiles of A(k2:m, k2:m): the update.
+//   the other tickets    lower tiles of A(k2:m, k2:m), 64 x 64 or (when those
+//                        are too few to fill the device) 32 x 32: the update.
 // The strips wait only on ticket 0, which is running whenever they hold a
 // ticket, so every wait ends; each wait is also bounded in time (2 s).  The
 // diagonal chain of the factorization (tile POTRF, strip solve) thus runs
@@ -47,7 +48,8 @@ struct StepArgs {
     View<double> V;                 // the m x m lower triangle
     int64_t m, k0, k1, k2;          // panel k = [k0, k1), panel k+1 = [k1, k2)
     int nstrip;                     // strips of panel k+1 in rows [k2, m)
-    int64_t nbulk;                  // lower 64 x 64 tiles of A(k2:m, k2:m)
+    int bt;                         // bulk tile width (32 or 64)
+    int64_t nbulk;                  // lower bt x bt tiles of A(k2:m, k2:m)
     int32_t *info;                  // failure index (1-based, global); also the abort word
     int64_t base;                   // global index of V's first row
     int32_t *sync;                  // [0] ticket counter, [1] diagonal flag (1 ok, 2 failed)
@@ -201,6 +203,35 @@ __device__ __forceinline__ void updated_tile_to_smem(const StepArgs &a, Smem &sm
         }
 }
 
+// Bulk task: lower tile (ti, tj) of A(k2:m, k2:m) in BT x BT tiles (BT = 16 TM)
+// receives -= P_rows P_cols^T over panel k.
+template <int TM>
+__device__ __forceinline__ void bulk_tile(const StepArgs &a, Smem &sm, int64_t ti, int64_t tj)
+{
+    constexpr int BT = 16 * TM;
+    const int64_t r0 = a.k2 + ti * BT, c0 = a.k2 + tj * BT;
+    const int nr = (int)(a.m - r0 < BT ? a.m - r0 : BT), nc = (int)(a.m - c0 < BT ? a.m - c0 : BT);
+    const Owner<TM, TM> o(false);
+    double acc[TM][TM];
+    panel_product<TM, TM>(a, sm, r0, nr, c0, nc, (int)(a.k1 - a.k0), o, acc);
+    double cin[TM][TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+            const int r = o.ry * TM + i, c = o.cx * TM + j;
+            const bool in = r < nr && c < nc && (ti != tj || c <= r);
+            cin[i][j] = in ? a.V(r0 + r, c0 + c) : 0.0;
+        }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+            const int r = o.ry * TM + i, c = o.cx * TM + j;
+            if (r < nr && c < nc && (ti != tj || c <= r)) a.V(r0 + r, c0 + c) = cin[i][j] - acc[i][j];
+        }
+}
+
 // Element e of a rows x cols block written or read along V's unit stride.
 __device__ __forceinline__ void block_elem(const View<double> &V, int e, int rows, int cols, int &i,
                                            int &j)
@@ -319,15 +350,35 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
         __syncthreads();
         if (tid < wn) sm.rinv[tid] = 1.0 / sm.Ld[tid][tid];
         __syncthreads();
-        // X L_D^T = T, columns in increasing order; rows are independent
-        constexpr int kGroups = kTh / STRIP;
-        const int row = tid % STRIP, grp = tid / STRIP;
-        double *xr = sm.T[row];
-        for (int j = 0; j < wn; ++j) {
-            if (grp == 0) xr[j] *= sm.rinv[j];
-            __syncthreads();
-            const double xj = xr[j];
-            for (int c = j + 1 + grp; c < wn; c += kGroups) xr[c] -= xj * sm.Ld[c][j];
+        // X L_D^T = T, columns in increasing order; rows are independent.
+        // G = 256 / STRIP consecutive lanes share a row, lane g holding its
+        // columns g + G i in registers: column j is scaled by its owner lane
+        // and handed to the row's other lanes by a shuffle, so the solve takes
+        // no block barrier, and registers whose columns are all finished drop
+        // out of the step at compile time.
+        {
+            constexpr int G = kTh / STRIP, NC = PW / G;
+            const int row = tid / G, grp = tid % G;
+            double x[NC];
+#pragma unroll
+            for (int i = 0; i < NC; ++i) x[i] = sm.T[row][grp + G * i];
+#pragma unroll
+            for (int j = 0; j < PW; ++j) {
+                if (j < wn) {   // uniform
+                    const int oi = j / G, og = j % G;
+                    const double xj = __shfl_sync(0xffffffffu, x[oi] * sm.rinv[j], og, G);
+                    if (grp == og) x[oi] = xj;
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) {
+                        if (i < oi) continue;
+                        const int c = grp + G * i;
+                        if (c > j && c < wn) x[i] = fma(-sm.Ld[c][j], xj, x[i]);
+                    }
+                }
+            }
+            __syncthreads();   // every thread has read its row of T
+#pragma unroll
+            for (int i = 0; i < NC; ++i) sm.T[row][grp + G * i] = x[i];
             __syncthreads();
         }
         for (int e = tid; e < STRIP * PW; e += kTh) {
@@ -338,35 +389,15 @@ __global__ void __launch_bounds__(kTh) potrf_step_kernel(StepArgs a)
         return;
     }
 
-    // ---- a lower 64 x 64 tile of A(k2:m, k2:m): the update only
+    // ---- a lower bt x bt tile of A(k2:m, k2:m): the update only
     const int64_t b = t - 1 - a.nstrip;
     // single-precision guess (the FP64 pipe is narrow), corrected below
     int64_t ti = (int64_t)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
     while ((ti + 1) * (ti + 2) / 2 <= b) ++ti;
     while (ti * (ti + 1) / 2 > b) --ti;
     const int64_t tj = b - ti * (ti + 1) / 2;
-    const int64_t r0 = a.k2 + ti * kT, c0 = a.k2 + tj * kT;
-    const int nr = (int)(a.m - r0 < kT ? a.m - r0 : kT), nc = (int)(a.m - c0 < kT ? a.m - c0 : kT);
-    const Owner<4, 4> o(false);
-    double acc[4][4];
-    panel_product<4, 4>(a, sm, r0, nr, c0, nc, w, o, acc);
-    const int tx = tid % 16, ty = tid / 16;
-    double cin[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = ty * 4 + i, c = tx * 4 + j;
-            const bool in = r < nr && c < nc && (ti != tj || c <= r);
-            cin[i][j] = in ? a.V(r0 + r, c0 + c) : 0.0;
-        }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = ty * 4 + i, c = tx * 4 + j;
-            if (r < nr && c < nc && (ti != tj || c <= r)) a.V(r0 + r, c0 + c) = cin[i][j] - acc[i][j];
-        }
+    if (a.bt == 32) bulk_tile<2>(a, sm, ti, tj);
+    else bulk_tile<4>(a, sm, ti, tj);
 }
 
 }  // namespace
@@ -401,10 +432,11 @@ cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, i
     const int64_t k1 = k0 + pw < m ? k0 + pw : m;
     if (k1 >= m) return cudaSuccess;                  // no next panel
     const int64_t k2 = k1 + pw < m ? k1 + pw : m;
-    const int64_t rest = (m - k2 + kT - 1) / kT;      // row tiles of A(k2:m, k2:m)
     const int64_t strip = m <= kSmallStrips ? 32 : 64;
     const int64_t strips = (m - k2 + strip - 1) / strip;
-    StepArgs a{V, m, k0, k1, k2, (int)strips, rest * (rest + 1) / 2, info, base, sync};
+    const int bt = potrf_step_bulk_tile(m - k2, 2 * (int64_t)device_sm_count());   // 2 CTAs per SM
+    const int64_t rest = (m - k2 + bt - 1) / bt;      // row tiles of A(k2:m, k2:m)
+    StepArgs a{V, m, k0, k1, k2, (int)strips, bt, rest * (rest + 1) / 2, info, base, sync};
     const int64_t grid = 1 + a.nstrip + a.nbulk;
     if (grid > INT32_MAX) return cudaErrorInvalidValue;
     if (pw == 32) return strip == 32 ? launch_step<32, 32>(st, a, grid) : launch_step<32, 64>(st, a, grid);

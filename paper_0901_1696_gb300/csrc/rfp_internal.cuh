@@ -285,6 +285,21 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
 // for potrf_tile (global index base + column + 1; the launch does nothing if
 // *info is already non-zero).
 int potrf_step_width(int64_t m);
+// Tile width (32 or 64) of a lookahead step's bulk update of the trailing
+// triangle of order `rest` (rows below the next panel), with `slots`
+// resident step CTAs on the device: the 32-wide tile when it wins by 5% on
+// waves x tile area (a bulk tile's time grows with its area), i.e. when the
+// 64-wide tiles are too few to fill the device.
+inline int potrf_step_bulk_tile(int64_t rest, int64_t slots)
+{
+    if (rest <= 0) return 64;
+    slots = slots > 0 ? slots : 1;
+    auto est = [&](int64_t t) {
+        const int64_t r = (rest + t - 1) / t, tiles = r * (r + 1) / 2;
+        return (double)((tiles + slots - 1) / slots) * (double)(t * t);
+    };
+    return est(32) < 0.95 * est(64) ? 32 : 64;
+}
 size_t potrf_step_sync_words(int64_t m);
 cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, int32_t *info,
                        int64_t base, int32_t *sync);

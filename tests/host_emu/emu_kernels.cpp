@@ -459,20 +459,22 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
 }
 
 // potrf_step: one ordered launch (ticket order: the diagonal tile of panel
-// k+1, its 32-row (m <= 2048) or 64-row strips, then the lower 64 x 64 tiles
-// of A(k2:m, k2:m)) with the kernel's own tile decomposition; panels 32 wide
-// for m <= 4096, 64 beyond.  Besides the bounds checks, every element one
+// k+1, its 32-row (m <= 2048) or 64-row strips, then the lower tiles of
+// A(k2:m, k2:m), 32 or 64 wide by the kernel's rule) with the kernel's own
+// tile decomposition; panels 32 wide for m <= 4096, 64 beyond.  Besides the bounds checks, every element one
 // task writes is recorded, and a read of it by another task is a violation
 // unless it is the new diagonal tile read by a strip (which the kernel does
 // only after the diagonal task's flag).
 // The kernel's rules (panels 32 wide up to m = 4096, strips 32 rows up to
 // m = 2048); emu_set_step_rules lowers the bounds so that small orders also
-// take the 64-wide panels and 64-row strips.
-static int64_t g_narrow_panels = 4096, g_small_strips = 2048;
-extern "C" void emu_set_step_rules(long narrow_panels, long small_strips)
+// take the 64-wide panels and 64-row strips, and a bulk tile width can be
+// forced.
+static int64_t g_narrow_panels = 4096, g_small_strips = 2048, g_bulk_tile = 0;
+extern "C" void emu_set_step_rules(long narrow_panels, long small_strips, long bulk_tile)
 {
     g_narrow_panels = narrow_panels;
     g_small_strips = small_strips;
+    g_bulk_tile = bulk_tile;   // 0: the kernel's rule; 32 or 64: that width
 }
 
 int potrf_step_width(int64_t m)
@@ -489,9 +491,10 @@ size_t potrf_step_sync_words(int64_t m)
 cudaError_t potrf_step(cudaStream_t, View<double> V, int64_t m, int64_t k0, int32_t *info,
                        int64_t base, int32_t *sync)
 {
-    const int64_t T = 64, P = potrf_step_width(m), k1 = std::min(k0 + P, m);
+    const int64_t P = potrf_step_width(m), k1 = std::min(k0 + P, m);
     if (k1 >= m) return cudaSuccess;
     const int64_t k2 = std::min(k1 + P, m), w = k1 - k0, wn = k2 - k1;
+    const int64_t T = g_bulk_tile ? g_bulk_tile : potrf_step_bulk_tile(m - k2, 2 * (int64_t)device_sm_count());
     const int64_t S = m <= g_small_strips ? 32 : 64;  // rows per strip task
     const int64_t rest = (m - k2 + T - 1) / T, nstrip = (m - k2 + S - 1) / S, nbulk = rest * (rest + 1) / 2;
     Launch L;

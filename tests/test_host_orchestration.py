@@ -42,7 +42,7 @@ def emu_lib(tmp_path_factory):
     raw.emu_message.restype = ctypes.c_char_p
     raw.emu_launches.restype = ctypes.c_long
     raw.emu_set_sms.argtypes = [ctypes.c_int]
-    raw.emu_set_step_rules.argtypes = [ctypes.c_long, ctypes.c_long]
+    raw.emu_set_step_rules.argtypes = [ctypes.c_long, ctypes.c_long, ctypes.c_long]
     return lib
 
 
@@ -124,13 +124,15 @@ def test_emulated_path_matches_oracle(emu, transr, uplo, n):
 
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
 @pytest.mark.parametrize("n", [129, 258, 400])
-@pytest.mark.parametrize("rules", [(0, 0), (0, 4096), (4096, 0)],
-                         ids=["panel64_strip64", "panel64_strip32", "panel32_strip64"])
+@pytest.mark.parametrize("rules", [(0, 0, 0), (0, 4096, 0), (4096, 0, 0), (4096, 2048, 64),
+                                   (0, 0, 64), (0, 4096, 32)],
+                         ids=["panel64_strip64", "panel64_strip32", "panel32_strip64",
+                              "panel32_bulk64", "panel64_bulk64", "panel64_strip32_bulk32"])
 def test_emulated_step_rules(emu_lib, transr, uplo, n, rules):
     """The lookahead steps with 64-wide panels (the rule for triangles above
-    order 4096), and 32-wide panels with 64-row strips (orders 2049 .. 4096),
-    at orders the emulator covers: same bounds, ownership and ordering checks,
-    same factor as the oracle."""
+    order 4096), 32-wide panels with 64-row strips (orders 2049 .. 4096), and
+    either bulk tile width, at orders the emulator covers: same bounds,
+    ownership and ordering checks, same factor as the oracle."""
     raw = emu_lib.lib
     raw.emu_set_sms(152)
     raw.emu_set_step_rules(*rules)
@@ -145,7 +147,7 @@ def test_emulated_step_rules(emu_lib, transr, uplo, n, rules):
         assert info[0] == ref_info == 0
         assert np.max(np.abs(arf - ref_f)) <= 1e-13 * max(1.0, np.max(np.abs(ref_f)))
     finally:
-        raw.emu_set_step_rules(4096, 2048)
+        raw.emu_set_step_rules(4096, 2048, 0)
 
 
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
