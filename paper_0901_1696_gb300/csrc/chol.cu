@@ -9,9 +9,12 @@
 //          L22^T X2 = Y2; Y1 -= L21^T X2; L11^T X1 = Y1
 //   PFTRI: W21 = -L22^{-1} L21 L11^{-1}; T1 <- W11^T W11 + W21^T W21;
 //          S <- W22^T W21; T2 <- W22^T W22
-// Every step is in place and allocates nothing.  The in-place triangular
-// products are ordered so that no kernel reads a tile another CTA of the same
-// launch writes (right-looking blocked TRTRI and LAUUM below).
+// Every step works in place on the caller's array.  FP64 steps take small
+// stream-ordered scratch from a library pool: the sync words of the one-launch
+// kernels and, for triangles up to order 1024, PFTRI's W = L^{-1} and split-K
+// chunks.  The in-place triangular products are ordered so that no kernel
+// reads a tile another CTA of the same launch writes (right-looking blocked
+// TRTRI and LAUUM below).
 #include <algorithm>
 
 #include "rfp_internal.cuh"
@@ -153,6 +156,65 @@ cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View
     return cudaSuccess;
 }
 
+// Triangles of order kNb < m <= kSmallInverse are inverted (FP64, outside
+// graph capture) by one launch of the block substitution L W = I into pool
+// scratch, and their W^T W formed by one split-K product: each a fixed
+// number of launches instead of a serial chain of them per 64-wide panel,
+// which bounds these orders on GB300's FP64 pipe.
+constexpr int64_t kSmallInverse = 1024;
+
+// W = L^{-1}: W = I in scratch, L W = I with a lower-triangular right-hand
+// side (solution lower triangular), W's lower triangle back into V.  Returns
+// false when it did not run (FP32, order out of range, no scratch); *err
+// receives the result when it ran.
+template <typename T>
+bool trtri_by_solve(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort, cudaError_t *err)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (m <= kNb || m > kSmallInverse) return false;
+        const size_t wwords = (size_t)(m * m) * 2, swords = rfp_solve_sync_words(m);
+        int32_t *buf = nullptr;
+        if (solve_scratch_acquire(st, wwords + swords, &buf) != cudaSuccess) {
+            (void)cudaGetLastError();   // the failed scratch request is not the caller's error
+            return false;
+        }
+        View<double> W{reinterpret_cast<double *>(buf), 1, m};
+        cudaError_t e = identity_fill(st, W, m, abort);
+        if (e == cudaSuccess)
+            e = rfp_solve(st, V, V, V, m, 0, W, m, false, buf + wwords, abort, 1.0, true);
+        if (e == cudaSuccess) e = lower_copy(st, V, W, m, abort);
+        const cudaError_t e2 = solve_scratch_release(st, buf);
+        *err = e != cudaSuccess ? e : e2;
+        return true;
+    }
+    return false;
+}
+
+// Lower triangle of W^T W in place, as one split-K product: C(i, j) =
+// sum_{k >= max(i, j)} W(k, i) W(k, j) (both operands W^T, masked to k >= row),
+// the chunk products into scratch, their sum into V's lower triangle by the
+// second kernel.  Same conditions as trtri_by_solve.
+template <typename T>
+bool lauum_by_product(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort, cudaError_t *err)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (m <= kNb || m > kSmallInverse) return false;
+        const int splits = (int)std::min<int64_t>(8, std::max<int64_t>(2, (m + 127) / 128));
+        int32_t *buf = nullptr;
+        if (solve_scratch_acquire(st, (size_t)splits * (size_t)(m * m) * 2, &buf) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        const cudaError_t e = gemm_nt_splitk(st, V, V.t(), V.t(), m, m, m, 1.0, 0.0, MASK_LOWER,
+                                             MASK_UPPER, MASK_UPPER, abort, splits,
+                                             reinterpret_cast<double *>(buf));
+        const cudaError_t e2 = solve_scratch_release(st, buf);
+        *err = e != cudaSuccess ? e : e2;
+        return true;
+    }
+    return false;
+}
+
 // In-place W = L^{-1} on an m x m lower triangle V.  Right-looking over the
 // block columns p: with X = C_{p-1}^{-1} ... C_1^{-1} held where L was
 // consumed, step p applies C_p^{-1} (block column p of L):
@@ -161,6 +223,8 @@ cudaError_t trsm_left_lower_trans(cudaStream_t st, View<T> B, int64_t nrhs, View
 template <typename T>
 cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
 {
+    cudaError_t err = cudaSuccess;
+    if (trtri_by_solve(st, V, m, abort, &err)) return err;
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
         RFP_TRY(trtri_tile(st, V.sub(k0, k0), (int)w, abort));
@@ -184,6 +248,8 @@ cudaError_t trtri_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *
 template <typename T>
 cudaError_t lauum_blocked(cudaStream_t st, View<T> V, int64_t m, const int32_t *abort)
 {
+    cudaError_t err = cudaSuccess;
+    if (lauum_by_product(st, V, m, abort, &err)) return err;
     for (int64_t k0 = 0; k0 < m; k0 += kNb) {
         const int64_t k1 = std::min(k0 + kNb, m), w = k1 - k0;
         if (k0 > 0) {

@@ -120,7 +120,8 @@ struct GemmTileChoice {
     int kind;
 };
 inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, int inplace,
-                                       int elem_size, int num_sms, int occ_big, int occ_small)
+                                       int elem_size, int num_sms, int occ_big, int occ_small,
+                                       int64_t splits = 1)   // CTAs per tile (split K)
 {
     const int big = elem_size == 8 ? 64 : 128, sml = elem_size == 8 ? 32 : 64;
     if (inplace != GEMM_INPLACE_NONE) {
@@ -140,6 +141,7 @@ inline GemmTileChoice gemm_tile_choice(int64_t M, int64_t N, int cmode, int inpl
     };
     auto est = [&](int64_t c, int occ, int t) {
         occ = occ > 0 ? occ : 1;
+        c *= splits > 1 ? splits : 1;
         const int64_t slots = (int64_t)num_sms * occ;
         return (double)((c + slots - 1) / slots) * occ * (double)t * t;
     };
@@ -166,7 +168,9 @@ cudaError_t gemm_nt(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M,
 // gemm_nt with K split into `splits` chunks (one launch, grid z = chunk), the
 // chunk products written to work (splits x M x N, dense) and summed into C in
 // a fixed order by a second kernel.  For products with few output tiles and a
-// long K.  splits <= 1 or work == nullptr falls back to gemm_nt.  No in-place.
+// long K.  splits <= 1 or work == nullptr falls back to gemm_nt.  With
+// splits >= 2 and a work array, C may alias A or B: the chunk products
+// write only `work`, and C is written by the second kernel after them.
 template <typename T>
 cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t M, int64_t N,
                            int64_t K, T alpha, T beta, int cmode, int amask, int bmask,
@@ -191,6 +195,12 @@ cudaError_t trtri_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort);
 // In-place lower triangle of W^T W for one w x w lower-triangular tile W.
 template <typename T>
 cudaError_t lauum_tile(cudaStream_t st, View<T> A, int w, const int32_t *abort);
+
+// W = I (m x m), and dst's lower triangle = src's (m x m views), in FP64;
+// nothing is done if abort is non-null and non-zero at launch.
+cudaError_t identity_fill(cudaStream_t st, View<double> W, int64_t m, const int32_t *abort);
+cudaError_t lower_copy(cudaStream_t st, View<double> dst, View<double> src, int64_t m,
+                       const int32_t *abort);
 
 // *info = first j (1-based) with a zero diagonal in T1 then T2, else 0.
 template <typename T>
@@ -272,10 +282,14 @@ cudaError_t trsm_wavefront(cudaStream_t st, View<float> Lv, int64_t n, const flo
 // abort: if non-null and non-zero when the launch starts, nothing is done.
 // alpha scales the right-hand side (op(L) Y = alpha X).  If a wait between
 // tasks expires (2 s), the blocks of X not computed are set to NaN.
+// lower_rhs (forward, n2 = 0 only): X is lower triangular (column c zero in
+// rows < c), so the solution is too; blocks above a column group's first
+// row are neither read nor written, which cuts the work of L W = I from
+// n^3 / 2 to about n^3 / 6 multiply-adds.
 size_t rfp_solve_sync_words(int64_t nrhs);
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
-                      const int32_t *abort = nullptr, double alpha = 1.0);
+                      const int32_t *abort = nullptr, double alpha = 1.0, bool lower_rhs = false);
 // One panel step of the FP64 lookahead Cholesky of an m x m lower triangle V
 // (potrf_step.cu), panel k = [k0, k0 + pw) already factored, pw =
 // potrf_step_width(m) (32 or 64): the trailing update with it, and the
@@ -303,8 +317,10 @@ inline int potrf_step_bulk_tile(int64_t rest, int64_t slots)
 size_t potrf_step_sync_words(int64_t m);
 cudaError_t potrf_step(cudaStream_t st, View<double> V, int64_t m, int64_t k0, int32_t *info,
                        int64_t base, int32_t *sync);
-// Stream-ordered scratch for the sync words, from a library-private memory
-// pool.  cudaErrorNotSupported while `st` is being captured into a graph.
+// Stream-ordered scratch (`words` int32, 256-byte aligned) for the sync
+// words and work arrays of the FP64 one-launch forms, from a library-private
+// memory pool.  cudaErrorNotSupported while `st` is being captured into a
+// graph.
 cudaError_t solve_scratch_acquire(cudaStream_t st, size_t words, int32_t **out);
 cudaError_t solve_scratch_release(cudaStream_t st, int32_t *p);
 

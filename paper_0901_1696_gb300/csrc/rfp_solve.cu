@@ -60,6 +60,7 @@ struct SolveArgs {
     int32_t *counter, *prog, *err;
     const int32_t *abort;           // if set (non-zero) at launch, nothing is done
     double alpha;                   // the right-hand side is alpha X
+    int lower_rhs;                  // X lower triangular (forward, one triangle): see rfp_solve
 };
 
 __device__ __forceinline__ uint64_t rs_globaltimer()
@@ -215,10 +216,15 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     const int ticket = s_ticket;
     const int g = ticket % a.ng, p = ticket / a.ng;          // p: position in solve order
     const int b = TRANS ? a.nb - 1 - p : p;
+    const int64_t c0 = (int64_t)g * kG;
+    // A lower-triangular right-hand side (forward): the group's columns are
+    // zero above row c0 in B and in the solution, so blocks above c0's block
+    // are left as they are, publish nothing, and are not read below.
+    const int jf = a.lower_rhs ? (int)(c0 / R) : 0;
+    if (b < jf) return;
     int64_t r0;
     int rows;
     block_rows<R>(a, b, r0, rows);
-    const int64_t c0 = (int64_t)g * kG;
     const int cols = (int)(a.nrhs - c0 < kG ? a.nrhs - c0 : kG);
     const View<double> Xb = a.X.sub(r0, c0);
     int32_t *prog = a.prog + g;
@@ -254,9 +260,9 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     if (kEarlyDiag) load_diag();   // ordered before its use by the barriers below
 
     bool ok = true;
-    // Off-diagonal blocks in solve order: forward j = 0 .. b-1, backward j = nb-1 .. b+1.
+    // Off-diagonal blocks in solve order: forward j = jf .. b-1, backward j = nb-1 .. b+1.
     const int nblk = p;
-    for (int q = 0; q < nblk && ok; ++q) {
+    for (int q = jf; q < nblk && ok; ++q) {
         const int j = TRANS ? a.nb - 1 - q : q;
         if (tid == 0) {
             s_ok = wait_progress(prog, q + 1, a.err) ? 1 : 0;
@@ -387,10 +393,11 @@ size_t rfp_solve_sync_words(int64_t nrhs)
 
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> X, int64_t nrhs, bool trans, int32_t *sync,
-                      const int32_t *abort, double alpha)
+                      const int32_t *abort, double alpha, bool lower_rhs)
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    if (lower_rhs && (trans || n2 != 0)) return cudaErrorInvalidValue;
     const int64_t R = n <= kSmallSolve ? 32 : 64;
     const int64_t nb1 = (n1 + R - 1) / R, nb2 = (n2 + R - 1) / R, ng = (nrhs + kG - 1) / kG;
     const int64_t tasks = (nb1 + nb2) * ng;
@@ -400,7 +407,7 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
     cudaError_t e = cudaMemsetAsync(sync, 0, rfp_solve_sync_words(nrhs) * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, nrhs, (int)ng,
-                sync, sync + 2, sync + 1, abort, alpha};
+                sync, sync + 2, sync + 1, abort, alpha, lower_rhs ? 1 : 0};
     if (R == 32) {
         if (trans) rfp_solve_kernel<true, 32><<<(unsigned)tasks, kThreads, 0, st>>>(a);
         else rfp_solve_kernel<false, 32><<<(unsigned)tasks, kThreads, 0, st>>>(a);
@@ -418,7 +425,8 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
 // destroyed) from which each solve takes its few sync words with
 // cudaMallocFromPoolAsync and returns them with cudaFreeAsync on the same
 // stream, so concurrent solves on different streams never share them.  The
-// pool keeps up to 1 MiB between calls instead of returning it to the driver.
+// pool keeps up to 128 MiB between calls instead of returning it to the
+// driver (PFTRI of a small triangle takes up to 9 m^2 doubles, m <= 1024).
 // Under stream capture the caller does not use it (it runs the multi-launch
 // form instead).
 
@@ -449,7 +457,7 @@ cudaError_t solve_scratch_acquire(cudaStream_t st, size_t words, int32_t **out)
             cudaMemPool_t p;
             e = cudaMemPoolCreate(&p, &props);
             if (e != cudaSuccess) return e;
-            uint64_t keep = 1u << 20;
+            uint64_t keep = 128ull << 20;
             e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
             if (e != cudaSuccess) {
                 cudaMemPoolDestroy(p);

@@ -242,7 +242,12 @@ cudaError_t gemm_nt_splitk(cudaStream_t st, View<T> C, View<T> A, View<T> B, int
     GemmArgs<T> g{View<T>{work, 1, M}, A, B, M, N, K, T(1), T(0), cmode, amask, bmask, abort};
     g.kchunk = (K + splits - 1) / splits;
     g.zstride = M * N;
-    launch_gemm<T, typename GemmBig<T>::C>(st, g, (unsigned)splits);
+    int occ_big = 1, occ_small = 1;
+    gemm_occupancy((int)sizeof(T), &occ_big, &occ_small);
+    const GemmTileChoice tc = gemm_tile_choice(M, N, cmode, GEMM_INPLACE_NONE, (int)sizeof(T),
+                                               device_sm_count(), occ_big, occ_small, splits);
+    if (tc.kind == GEMM_TILE_SMALL) launch_gemm<T, typename GemmSmall<T>::C>(st, g, (unsigned)splits);
+    else launch_gemm<T, typename GemmBig<T>::C>(st, g, (unsigned)splits);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -759,6 +764,43 @@ cudaError_t check_diag(cudaStream_t st, View<T> t1, int64_t n1, View<T> t2, int6
     check_diag_kernel<T><<<1, 1024, 0, st>>>(t1, n1, t2, n2, info);
     note_launch();
     return cudaGetLastError();
+}
+
+// dst = I (mode 0) or dst(i, j) = src(i, j) for j <= i (mode 1), m x m; one
+// thread per element along dst's unit stride, grid-stride.
+__global__ void tri_fill_kernel(View<double> dst, View<double> src, int64_t m, int mode,
+                                const int32_t *abort)
+{
+    if (abort && *abort) return;
+    const bool rowfast = dst.rs == 1;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = e % m, v = e / m;
+        const int64_t i = rowfast ? u : v, j = rowfast ? v : u;
+        if (mode == 0) dst(i, j) = i == j ? 1.0 : 0.0;
+        else if (j <= i) dst(i, j) = src(i, j);
+    }
+}
+
+static cudaError_t tri_fill(cudaStream_t st, View<double> dst, View<double> src, int64_t m, int mode,
+                            const int32_t *abort)
+{
+    if (m <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((m * m + 255) / 256, 8 * (int64_t)device_sm_count());
+    tri_fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(dst, src, m, mode, abort);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t identity_fill(cudaStream_t st, View<double> W, int64_t m, const int32_t *abort)
+{
+    return tri_fill(st, W, W, m, 0, abort);
+}
+
+cudaError_t lower_copy(cudaStream_t st, View<double> dst, View<double> src, int64_t m,
+                       const int32_t *abort)
+{
+    return tri_fill(st, dst, src, m, 1, abort);
 }
 
 #define RFP_INSTANTIATE(T)                                                                    \

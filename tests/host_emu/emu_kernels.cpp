@@ -389,10 +389,11 @@ size_t rfp_solve_sync_words(int64_t nrhs) { return (size_t)(2 + (nrhs + 15) / 16
 
 cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> Xv, int64_t nrhs, bool trans, int32_t *sync,
-                      const int32_t *abort, double alpha)
+                      const int32_t *abort, double alpha, bool lower_rhs)
 {
     const int64_t n = n1 + n2;
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
+    if (lower_rhs && (trans || n2 != 0)) return cudaErrorInvalidValue;
     const int64_t R = n <= 4096 ? 32 : 64;             // block rows, as the kernel picks them
     const int64_t nb1 = (n1 + R - 1) / R, nb = nb1 + (n2 + R - 1) / R, ng = (nrhs + 15) / 16;
     Launch L;
@@ -417,13 +418,15 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
         L.cta = (int)t;
         L.wr(sync, (int32_t)(t + 1));                       // ticket counter
         const int64_t g = t % ng, p = t / ng, b = trans ? nb - 1 - p : p;
+        const int64_t c0 = g * 16, cols = std::min<int64_t>(16, nrhs - c0);
+        const int64_t jf = lower_rhs ? c0 / R : 0;   // blocks above stay zero, untouched
+        if (b < jf) continue;
         int64_t r0, rows;
         rows_of(b, r0, rows);
-        const int64_t c0 = g * 16, cols = std::min<int64_t>(16, nrhs - c0);
         std::vector<double> acc(rows * cols);
         for (int64_t c = 0; c < cols; ++c)
             for (int64_t r = 0; r < rows; ++r) acc[c * rows + r] = alpha * L.rd(xat(r0 + r, c0 + c));
-        for (int64_t q = 0; q < p; ++q) {
+        for (int64_t q = jf; q < p; ++q) {
             const int64_t j = trans ? nb - 1 - q : q;
             if (L.rd(prog + g) < q + 1) violation("X block read before its group's progress", prog + g);
             int64_t j0, kv;
@@ -584,6 +587,27 @@ cudaError_t potrf_step(cudaStream_t, View<double> V, int64_t m, int64_t k0, int3
                 wr(&V(r0 + i, c0 + j), rd(&V(r0 + i, c0 + j)) - prod(r0 + i, c0 + j));
             }
     }
+    return L.commit();
+}
+
+// identity_fill / lower_copy: one launch each, every element of the m x m
+// destination (lower triangle for the copy) written once.
+cudaError_t identity_fill(cudaStream_t, View<double> W, int64_t m, const int32_t *abort)
+{
+    Launch L;
+    if (aborted(L, abort)) return L.commit();
+    for (int64_t j = 0; j < m; ++j)
+        for (int64_t i = 0; i < m; ++i) L.wr(&W(i, j), i == j ? 1.0 : 0.0);
+    return L.commit();
+}
+
+cudaError_t lower_copy(cudaStream_t, View<double> dst, View<double> src, int64_t m,
+                       const int32_t *abort)
+{
+    Launch L;
+    if (aborted(L, abort)) return L.commit();
+    for (int64_t j = 0; j < m; ++j)
+        for (int64_t i = j; i < m; ++i) L.wr(&dst(i, j), L.rd(&src(i, j)));
     return L.commit();
 }
 
