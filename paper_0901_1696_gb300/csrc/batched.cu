@@ -241,14 +241,38 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
                 const int ti = colfast ? tm - 1 - uj : ui, tj = colfast ? tm - 1 - ui : uj;
                 const T *pa = P + kb + 4 * ti, *pb = P + kb + 4 * tj;   // zero beyond `rows`
                 // the tile's current values first: their load latency overlaps
-                // the multiply-adds below (nothing in the loop writes them)
+                // the multiply-adds below (nothing in the loop writes them).
+                // FP32: a tile inside one RFP block (all but those straddling
+                // row or column n1) is addressed from that block's base with
+                // 32-bit offsets, the FP32 pipe otherwise waiting on the address
+                // arithmetic; FP64 goes through A.at, its pipe hiding that
+                // arithmetic (and held addresses would cost it registers).
+                const int64_t gi0 = k0 + kb + 4 * ti, gj0 = k0 + kb + 4 * tj;
+                T *tb = nullptr;
+                int trs = 0, tcs = 0;
+                if constexpr (sizeof(T) == 4) {
+                    const View<T> *blk = nullptr;
+                    int64_t bi = gi0, bj = gj0;
+                    if (gj0 >= A.n1) { blk = &A.t2; bi -= A.n1; bj -= A.n1; }
+                    else if (gj0 + 3 < A.n1 && gi0 + 3 < A.n1) blk = &A.t1;
+                    else if (gj0 + 3 < A.n1 && gi0 >= A.n1) { blk = &A.s; bi -= A.n1; }
+                    if (blk) {
+                        tb = blk->p + bi * blk->rs + bj * blk->cs;
+                        trs = (int)blk->rs;
+                        tcs = (int)blk->cs;
+                    }
+                }
                 T cin[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int i = 4 * ti + u, j = 4 * tj + v;
-                        cin[u][v] = (i < m && j <= i) ? *A.at(k0 + kb + i, k0 + kb + j) : T(0);
+                        const bool in = i < m && j <= i;
+                        if constexpr (sizeof(T) == 4)
+                            cin[u][v] = in ? (tb ? tb[u * trs + v * tcs] : *A.at(gi0 + u, gj0 + v)) : T(0);
+                        else
+                            cin[u][v] = in ? *A.at(k0 + kb + i, k0 + kb + j) : T(0);
                     }
                 T acc[4][4] = {};
                 for (int c = 0; c < kb; ++c) {
@@ -265,7 +289,13 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int i = 4 * ti + u, j = 4 * tj + v;
-                        if (i < m && j <= i) *A.at(k0 + kb + i, k0 + kb + j) = cin[u][v] - acc[u][v];
+                        if (!(i < m && j <= i)) continue;
+                        if constexpr (sizeof(T) == 4) {
+                            T *q = tb ? tb + (u * trs + v * tcs) : A.at(gi0 + u, gj0 + v);
+                            *q = cin[u][v] - acc[u][v];
+                        } else {
+                            *A.at(k0 + kb + i, k0 + kb + j) = cin[u][v] - acc[u][v];
+                        }
                     }
             }
         }
