@@ -52,6 +52,36 @@ bool solve_one_launch(cudaStream_t st, View<T> V, int64_t m, View<T> X, int64_t 
     return false;
 }
 
+// C (lower m x m) = alpha A B^T + beta C with K-long operands: the SYRK of
+// PFTRF step 3 and PFTRI's T1 update.  In FP64, when the lower 32 x 32 tiles
+// are too few to fill the device twice over and K is long, K is split into
+// chunks summed by a second kernel (pool scratch; not under graph capture):
+// otherwise one CTA's serial K loop bounds the launch (n = 1001: 136 tiles
+// of K = 501, about 124 us on one SM, against about 100 us for the whole
+// product on all of them).
+template <typename T>
+cudaError_t update_lower(cudaStream_t st, View<T> C, View<T> A, View<T> B, int64_t m, int64_t K,
+                         T alpha, T beta, const int32_t *abort)
+{
+    if constexpr (sizeof(T) == 8) {
+        const int64_t t = (m + 31) / 32, tiles = t * (t + 1) / 2, sms = device_sm_count();
+        if (m > 0 && tiles < 2 * sms && K >= 256) {
+            int64_t splits = std::min<int64_t>(8, std::max<int64_t>(2, (4 * sms + tiles - 1) / tiles));
+            splits = std::min<int64_t>(splits, K / 64);
+            int32_t *buf = nullptr;
+            if (solve_scratch_acquire(st, (size_t)(splits * m * m) * 2, &buf) == cudaSuccess) {
+                const cudaError_t e = gemm_nt_splitk(st, C, A, B, m, m, K, alpha, beta, MASK_LOWER,
+                                                     MASK_NONE, MASK_NONE, abort, (int)splits,
+                                                     reinterpret_cast<double *>(buf));
+                const cudaError_t e2 = solve_scratch_release(st, buf);
+                return e != cudaSuccess ? e : e2;
+            }
+            (void)cudaGetLastError();   // the failed scratch request is not the caller's error
+        }
+    }
+    return gemm_nt(st, C, A, B, m, m, K, alpha, beta, MASK_LOWER, MASK_NONE, MASK_NONE, abort);
+}
+
 // ---- triangle-level building blocks ----------------------------------------
 
 // Right-looking blocked Cholesky of the m x m lower triangle V in place
@@ -298,8 +328,7 @@ cudaError_t pftrf_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
         else RFP_TRY(trsm_right_lower_trans(st, s, L.n2, t1, L.n1, info));
         stage_mark(st, "pftrf.trsm_s");
         // step 3: A22 <- A22 - L21 L21^T (lower triangle of T2)
-        RFP_TRY(gemm_nt(st, t2, s, s, L.n2, L.n2, L.n1, T(-1), T(1), MASK_LOWER, MASK_NONE,
-                        MASK_NONE, info));
+        RFP_TRY(update_lower(st, t2, s, s, L.n2, L.n1, T(-1), T(1), info));
         stage_mark(st, "pftrf.syrk_t2");
     }
     // step 4: L22 L22^T = A22
@@ -364,8 +393,7 @@ cudaError_t pftri_impl(cudaStream_t st, const Layout &L, T *arf, int32_t *info)
     RFP_TRY(lauum_blocked(st, t1, L.n1, info));
     stage_mark(st, "pftri.lauum_t1");
     if (L.n1 > 0 && L.n2 > 0) {
-        RFP_TRY(gemm_nt(st, t1, s.t(), s.t(), L.n1, L.n1, L.n2, T(1), T(1), MASK_LOWER,
-                        MASK_NONE, MASK_NONE, info));
+        RFP_TRY(update_lower(st, t1, s.t(), s.t(), L.n1, L.n2, T(1), T(1), info));
         stage_mark(st, "pftri.syrk_t1");
         // S <- W22^T W21 = L22^{-T} W21 (T2 still holds L22)
         cudaError_t e = cudaSuccess;

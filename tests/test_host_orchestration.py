@@ -150,6 +150,30 @@ def test_emulated_step_rules(emu_lib, transr, uplo, n, rules):
         raw.emu_set_step_rules(4096, 2048, 0)
 
 
+@pytest.mark.parametrize("transr,uplo", [("N", "L"), ("T", "U")])
+def test_emulated_split_k_updates(emu_lib, transr, uplo):
+    """n = 530: PFTRF step 3 and PFTRI's T1 update have K = 265 and few
+    output tiles, so they run as split-K products (chunks into scratch, summed
+    by a second kernel), checked like every other launch."""
+    n = 530
+    raw = emu_lib.lib
+    raw.emu_set_sms(152)
+    A = gen.spd_bbt(n, seed=17)
+    arf = oracle.pack(transr, uplo, A)
+    info = np.zeros(1, dtype=np.int32)
+    _register(emu_lib, arf, info)
+    ref_f, _ = oracle.pftrf(transr, uplo, n, arf)
+    emu_lib.rfp_dpftrf(transr, uplo, n, arf, info, 0)
+    _ok(emu_lib)
+    assert info[0] == 0
+    assert np.max(np.abs(arf - ref_f)) <= 1e-13 * max(1.0, np.max(np.abs(ref_f)))
+    ref_i, _ = oracle.pftri(transr, uplo, n, arf)
+    emu_lib.rfp_dpftri(transr, uplo, n, arf, info, 0)
+    _ok(emu_lib)
+    assert info[0] == 0
+    assert np.max(np.abs(arf - ref_i)) <= 1e-12 * max(1.0, np.max(np.abs(ref_i)))
+
+
 @pytest.mark.parametrize("transr,uplo", LAYOUTS)
 @pytest.mark.parametrize("n", [7, 130])
 def test_emulated_single_precision(emu, transr, uplo, n):
