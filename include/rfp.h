@@ -98,12 +98,15 @@ int rfp_sunpack(char transr, char uplo, int64_t n, const float *arf, float *A,
  * triangular solve of S, symmetric rank-n1 update of T2, Cholesky of T2.
  * *info (device) is set to 0, or to j > 0 when the leading minor of order j
  * is not positive definite (a pivot <= 0 or NaN); arf is then unspecified.
- * FP64 scratch: the triangle factorizations run one launch per 64-column
- * panel step (trailing update and the next panel's factorization together)
- * and step 2 runs as one launch; they take stream-ordered scratch from a
- * library-private memory pool (8 bytes per panel step, and 8 + 4 ceil(n2 /
- * 16) bytes for step 2), returned on `stream` when the call's work is done.  While `stream` is being captured into a CUDA graph, the routine
- * runs its multi-launch form instead, which takes none.
+ * FP64 scratch: the triangle factorizations run one launch per panel step
+ * (panels 32 columns wide up to triangle order 4096, 64 beyond; trailing
+ * update and the next panel's factorization together) and step 2 runs as one
+ * launch; they take stream-ordered scratch from a library-private memory pool
+ * (8 bytes per panel step, and 8 + 4 ceil(n2 / 16) bytes for step 2), and
+ * step 3 below order about 1540 splits its K into chunks held there (up to
+ * 8 n2^2 doubles), all returned on `stream` when the call's work is done.
+ * While `stream` is being captured into a CUDA graph, the routine runs its
+ * multi-launch form instead, which takes none.
  * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
  */
 int rfp_dpftrf(char transr, char uplo, int64_t n, double *arf, int32_t *info,
@@ -134,7 +137,11 @@ int rfp_spftrs(char transr, char uplo, int64_t n, int64_t nrhs, const float *arf
  * *info (device) is set to 0, or to j > 0 when the j-th diagonal entry of the
  * factor is exactly zero; arf is then unspecified.
  * FP64: the three solves with the factor (W21 and S <- L22^-T W21) run as
- * one launch each, with scratch as for rfp_dpftrs.
+ * one launch each, with scratch as for rfp_dpftrs.  A triangle T1 or T2 of
+ * order m, 64 < m <= 1024, is inverted by one solve L W = I and its W^T W
+ * formed by one split-K product, through up to 9 m^2 doubles of scratch from
+ * the same pool; larger triangles, and every triangle under graph capture,
+ * use the in-place blocked forms.
  * Arguments: 1 transr, 2 uplo, 3 n, 4 arf, 5 info, 6 stream.
  */
 int rfp_dpftri(char transr, char uplo, int64_t n, double *arf, int32_t *info,
@@ -321,6 +328,7 @@ const char *rfp_status_string(int status);
  * rfp_?tftri: the inverse of the triangular matrix in RFP, in place (the
  *   first stage of PFTRI).  diag 'N' or 'U'; with 'U' the diagonal is taken
  *   as 1 and is left unchanged, and `work` (n elements) holds it meanwhile.
+ *   FP64 takes pool scratch as rfp_dpftri does.
  *   *info (device) = 0, or the first exactly zero diagonal (1-based).
  *   Arguments: 1 transr, 2 uplo, 3 diag, 4 n, 5 arf, 6 info, 7 work, 8 stream.
  * rfp_?sfrk: C := alpha op(A) op(A)^T + beta C for the symmetric C in RFP

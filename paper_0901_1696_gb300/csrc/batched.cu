@@ -192,19 +192,34 @@ __device__ void left_update(const Mat<float> &A, int64_t k0, int kb, int rows, f
     const int tid = threadIdx.x;
     const int rpad = (rows + 3) & ~3, nq = (kb + 3) / 4, nquads = (rpad / 4) * nq;
     const int64_t nch = (k0 + KC - 1) / KC;
+    // Column kc + k of the factored part, rows k0 + r: one block for the
+    // whole column when it lies in T2; T1 above row n1 and S below otherwise.
+    auto col_src = [&](int64_t j, int r) -> const float * {
+        const int64_t i = k0 + r;
+        if (j >= A.n1) return &A.t2(i - A.n1, j - A.n1);
+        return i < A.n1 ? &A.t1(i, j) : &A.s(i - A.n1, j);
+    };
     auto issue = [&](int64_t ch, int buf) {
         const int64_t kc = ch * KC;
         const int kw = (int)(k0 - kc < KC ? k0 - kc : KC);
-        // along the unit stride of the block holding the chunk's first element
+        // along the unit stride of the block holding the chunk's first element;
+        // each thread keeps one column (rows fastest) or one row stride
         const bool colfast = (kc >= A.n1 ? A.t2.rs : (k0 >= A.n1 ? A.s.rs : A.t1.rs)) == 1;
         float *dst = Ls + buf * KC * LDC;
-        for (int e = tid; e < KC * rpad; e += kBatchThreads) {
-            int k, r;
-            if (colfast) { r = e % rpad; k = e / rpad; }
-            else { k = e % KC; r = e / KC; }
-            float *d = dst + k * LDC + r;
-            if (k < kw && r < rows) cp_async4(d, A.at(k0 + r, kc + k));
-            else *d = 0.f;
+        if (colfast) {
+            for (int k = 0; k < KC; ++k)
+                for (int r = tid; r < rpad; r += kBatchThreads) {
+                    float *d = dst + k * LDC + r;
+                    if (k < kw && r < rows) cp_async4(d, col_src(kc + k, r));
+                    else *d = 0.f;
+                }
+        } else {
+            const int k = tid % KC;
+            for (int r = tid / KC; r < rpad; r += kBatchThreads / KC) {
+                float *d = dst + k * LDC + r;
+                if (k < kw && r < rows) cp_async4(d, col_src(kc + k, r));
+                else *d = 0.f;
+            }
         }
         cp_async_commit();
     };
