@@ -73,19 +73,11 @@ __device__ __forceinline__ View<T> bview(T *base, const Block &b, int64_t ld)
 // reciprocals of D's diagonal and the current pivot's reciprocal.
 // A launch is sized for the widest panel among its plan's entries (16, 24
 // or 32 columns): in FP64 a 24-column panel leaves room for two CTAs per SM.
-// FP32 adds the staging buffers of its left-looking update (two chunks of
-// kLeftKc factored columns, kPanelLd rows each, 16-byte aligned).
 constexpr int kPanelLd = kBatchMaxN + 4;     // rows padded to a multiple of 4
 constexpr int kSolveNb = 32, kSolveLd = kSolveNb + 1, kMaxRhs = 8;
-constexpr int kLeftKc = 8;
-constexpr int smem_base(int maxnb)
-{
-    return (maxnb * kPanelLd + kSolveNb * kSolveLd + kSolveNb * kMaxRhs + kSolveNb + 2 + 3) & ~3;
-}
-template <typename T>
 constexpr int smem_elems(int maxnb)
 {
-    return smem_base(maxnb) + (sizeof(T) == 4 ? 2 * kLeftKc * kPanelLd : 0);
+    return maxnb * kPanelLd + kSolveNb * kSolveLd + kSolveNb * kMaxRhs + kSolveNb + 2;
 }
 
 // Four consecutive elements from shared memory (16-byte aligned).
@@ -168,144 +160,9 @@ __device__ __forceinline__ int panel_in_registers(T *P, int kb, int rows, T *rin
     return -1;
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// FP32 left-looking update of the panel in P (rows x kb, its first row the
-// matrix row k0): P(r, c) -= sum_{j < k0} L(k0 + r, j) L(k0 + c, j), the
-// product of the factored columns with themselves restricted to the panel's
-// columns.  The factored columns are staged through Ls in chunks of kLeftKc
-// (rows contiguous), double-buffered with cp.async; each thread accumulates
-// up to four 4 x 4 blocks of P in registers over all chunks, then subtracts
-// them once.
-template <int NB>
-__device__ void left_update(const Mat<float> &A, int64_t k0, int kb, int rows, float *P, float *Ls)
-{
-    constexpr int LDC = kPanelLd, KC = kLeftKc;
-    constexpr int QT = (kBatchMaxN / 4 * ((NB + 3) / 4) + kBatchThreads - 1) / kBatchThreads;
-    const int tid = threadIdx.x;
-    const int rpad = (rows + 3) & ~3, nq = (kb + 3) / 4, nquads = (rpad / 4) * nq;
-    const int64_t nch = (k0 + KC - 1) / KC;
-    // Column kc + k of the factored part, rows k0 + r: one block for the
-    // whole column when it lies in T2; T1 above row n1 and S below otherwise.
-    auto col_src = [&](int64_t j, int r) -> const float * {
-        const int64_t i = k0 + r;
-        if (j >= A.n1) return &A.t2(i - A.n1, j - A.n1);
-        return i < A.n1 ? &A.t1(i, j) : &A.s(i - A.n1, j);
-    };
-    auto issue = [&](int64_t ch, int buf) {
-        const int64_t kc = ch * KC;
-        const int kw = (int)(k0 - kc < KC ? k0 - kc : KC);
-        // along the unit stride of the block holding the chunk's first element;
-        // each thread keeps one column (rows fastest) or one row stride
-        const bool colfast = (kc >= A.n1 ? A.t2.rs : (k0 >= A.n1 ? A.s.rs : A.t1.rs)) == 1;
-        float *dst = Ls + buf * KC * LDC;
-        if (colfast) {
-            for (int k = 0; k < KC; ++k)
-                for (int r = tid; r < rpad; r += kBatchThreads) {
-                    float *d = dst + k * LDC + r;
-                    if (k < kw && r < rows) cp_async4(d, col_src(kc + k, r));
-                    else *d = 0.f;
-                }
-        } else {
-            const int k = tid % KC;
-            for (int r = tid / KC; r < rpad; r += kBatchThreads / KC) {
-                float *d = dst + k * LDC + r;
-                if (k < kw && r < rows) cp_async4(d, col_src(kc + k, r));
-                else *d = 0.f;
-            }
-        }
-        cp_async_commit();
-    };
-    int qr[QT], qc[QT];
-#pragma unroll
-    for (int j = 0; j < QT; ++j) {
-        const int u = tid + j * kBatchThreads;
-        qr[j] = u < nquads ? u / nq : -1;
-        qc[j] = u < nquads ? u % nq : 0;
-    }
-    float acc[QT][4][4] = {};
-    issue(0, 0);
-    for (int64_t ch = 0; ch < nch; ++ch) {
-        const int buf = (int)(ch & 1);
-        if (ch + 1 < nch) {
-            issue(ch + 1, buf ^ 1);   // its buffer was last read before the barrier ending ch - 1
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const float *ls = Ls + buf * KC * LDC;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-#pragma unroll
-            for (int j = 0; j < QT; ++j) {
-                if (qr[j] < 0) continue;
-                float a[4], b[4];
-                ld4(ls + k * LDC + 4 * qr[j], a);
-                ld4(ls + k * LDC + 4 * qc[j], b);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[j][u][v] = fma(a[u], b[v], acc[j][u][v]);
-            }
-        }
-        __syncthreads();   // this buffer is free for chunk ch + 2
-    }
-#pragma unroll
-    for (int j = 0; j < QT; ++j) {
-        if (qr[j] < 0) continue;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int r = 4 * qr[j] + u, c = 4 * qc[j] + v;
-                if (r < rows && c < kb && r >= c) P[c * LDC + r] -= acc[j][u][v];
-            }
-    }
-    __syncthreads();
-}
-
-// FP32: left-looking blocked Cholesky (Section 3's algorithm with each
-// panel's update gathered from the factored columns when the panel comes
-// up, so the trailing matrix is never rewritten): per NB-wide panel, read
-// it, subtract the factored columns' contribution (left_update), factor it
-// in registers, write it back.  Returns 0 or the 1-based failing index.
-template <int NB>
-__device__ int factor_left(const Mat<float> &A, int64_t n, float *P, float *Ls, float *rbuf,
-                           int *s_fail)
-{
-    constexpr int LDC = kPanelLd;
-    const int tid = threadIdx.x;
-    for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        const int kb = (int)(n - k0 < NB ? n - k0 : NB);
-        const int rows = (int)(n - k0);
-        const int rpad = (rows + 3) & ~3;
-        for (int c = 0; c < kb; ++c)
-            for (int r = tid; r < rpad; r += blockDim.x)
-                P[c * LDC + r] = (r >= c && r < rows) ? *A.at(k0 + r, k0 + c) : 0.f;
-        if (tid == 0) *s_fail = -1;
-        __syncthreads();
-        if (k0 > 0) left_update<NB>(A, k0, kb, rows, P, Ls);
-        const int f = panel_in_registers<float, NB>(P, kb, rows, rbuf, s_fail);
-        if (f >= 0) return (int)(k0 + f + 1);
-        for (int c = 0; c < kb; ++c)
-            for (int r = c + tid; r < rows; r += blockDim.x) *A.at(k0 + r, k0 + c) = P[c * LDC + r];
-        __syncthreads();   // the panel is read back by the next panels' staging
-    }
-    return 0;
-}
-
-// FP64: right-looking; factor one matrix in place; returns 0 or the 1-based
-// failing index.
+// Factor one matrix in place; returns 0 or the 1-based failing index.
 template <typename T, int NB>
-__device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fail)
+__device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fail, T *rbuf)
 {
     constexpr int LDC = kPanelLd;
     const int tid = threadIdx.x;
@@ -319,7 +176,13 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
                 P[c * LDC + r] = (r >= c && r < rows) ? *A.at(k0 + r, k0 + c) : T(0);
         if (tid == 0) *s_fail = -1;
         __syncthreads();
-        // 2. right-looking Cholesky of the rows x kb panel, column by column
+        // 2. right-looking Cholesky of the rows x kb panel: in registers in
+        // FP32, whose pipe outruns the column loop's barriers; column by
+        // column in FP64, whose pipe the column loop keeps busy
+        if constexpr (sizeof(T) == 4) {
+            const int f = panel_in_registers<T, NB>(P, kb, rows, rbuf, s_fail);
+            if (f >= 0) return (int)(k0 + f + 1);
+        } else
         for (int c = 0; c < kb; ++c) {
             if (tid == 0) {   // pivot; scale the panel's own rows c+1 .. kb-1 of column c
                 const T d = P[c * LDC + c];
@@ -378,14 +241,38 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
                 const int ti = colfast ? tm - 1 - uj : ui, tj = colfast ? tm - 1 - ui : uj;
                 const T *pa = P + kb + 4 * ti, *pb = P + kb + 4 * tj;   // zero beyond `rows`
                 // the tile's current values first: their load latency overlaps
-                // the multiply-adds below (nothing in the loop writes them)
+                // the multiply-adds below (nothing in the loop writes them).
+                // FP32: a tile inside one RFP block (all but those straddling
+                // row or column n1) is addressed from that block's base with
+                // 32-bit offsets, the FP32 pipe otherwise waiting on the address
+                // arithmetic; FP64 goes through A.at, its pipe hiding that
+                // arithmetic (and held addresses would cost it registers).
+                const int64_t gi0 = k0 + kb + 4 * ti, gj0 = k0 + kb + 4 * tj;
+                T *tb = nullptr;
+                int trs = 0, tcs = 0;
+                if constexpr (sizeof(T) == 4) {
+                    const View<T> *blk = nullptr;
+                    int64_t bi = gi0, bj = gj0;
+                    if (gj0 >= A.n1) { blk = &A.t2; bi -= A.n1; bj -= A.n1; }
+                    else if (gj0 + 3 < A.n1 && gi0 + 3 < A.n1) blk = &A.t1;
+                    else if (gj0 + 3 < A.n1 && gi0 >= A.n1) { blk = &A.s; bi -= A.n1; }
+                    if (blk) {
+                        tb = blk->p + bi * blk->rs + bj * blk->cs;
+                        trs = (int)blk->rs;
+                        tcs = (int)blk->cs;
+                    }
+                }
                 T cin[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int i = 4 * ti + u, j = 4 * tj + v;
-                        cin[u][v] = (i < m && j <= i) ? *A.at(k0 + kb + i, k0 + kb + j) : T(0);
+                        const bool in = i < m && j <= i;
+                        if constexpr (sizeof(T) == 4)
+                            cin[u][v] = in ? (tb ? tb[u * trs + v * tcs] : *A.at(gi0 + u, gj0 + v)) : T(0);
+                        else
+                            cin[u][v] = in ? *A.at(k0 + kb + i, k0 + kb + j) : T(0);
                     }
                 T acc[4][4] = {};
                 for (int c = 0; c < kb; ++c) {
@@ -402,7 +289,13 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int i = 4 * ti + u, j = 4 * tj + v;
-                        if (i < m && j <= i) *A.at(k0 + kb + i, k0 + kb + j) = cin[u][v] - acc[u][v];
+                        if (!(i < m && j <= i)) continue;
+                        if constexpr (sizeof(T) == 4) {
+                            T *q = tb ? tb + (u * trs + v * tcs) : A.at(gi0 + u, gj0 + v);
+                            *q = cin[u][v] - acc[u][v];
+                        } else {
+                            *A.at(k0 + kb + i, k0 + kb + j) = cin[u][v] - acc[u][v];
+                        }
                     }
             }
         }
@@ -526,7 +419,6 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(PlanHeader *hdr,
     T *Y = D + kSolveNb * kSolveLd;
     T *rdiag = Y + kSolveNb * kMaxRhs;
     T *s_rinv = rdiag + kSolveNb;
-    T *Ls = P + smem_base(MAXNB);   // FP32 only: left-looking staging
     __shared__ int s_idx, s_fail;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&hdr->counter, 1);
@@ -539,17 +431,10 @@ __global__ void __launch_bounds__(kBatchThreads) batched_kernel(PlanHeader *hdr,
                  bview(arf + e.arf, e.t2, e.ld), e.n1};
         const int nb = e.nb < MAXNB ? e.nb : MAXNB;
         int fail;
-        if constexpr (sizeof(T) == 4) {
-            if (nb == 16) fail = factor_left<16>(A, e.n, P, Ls, rdiag, &s_fail);
-            else if (MAXNB >= 24 && nb == 24)
-                fail = factor_left<(MAXNB >= 24 ? 24 : 16)>(A, e.n, P, Ls, rdiag, &s_fail);
-            else fail = factor_left<MAXNB>(A, e.n, P, Ls, rdiag, &s_fail);
-        } else {
-            if (nb == 16) fail = factor_one<T, 16>(A, e.n, P, s_rinv, &s_fail);
-            else if (MAXNB >= 24 && nb == 24)
-                fail = factor_one<T, (MAXNB >= 24 ? 24 : 16)>(A, e.n, P, s_rinv, &s_fail);
-            else fail = factor_one<T, MAXNB>(A, e.n, P, s_rinv, &s_fail);
-        }
+        if (nb == 16) fail = factor_one<T, 16>(A, e.n, P, s_rinv, &s_fail, rdiag);
+        else if (MAXNB >= 24 && nb == 24)
+            fail = factor_one<T, (MAXNB >= 24 ? 24 : 16)>(A, e.n, P, s_rinv, &s_fail, rdiag);
+        else fail = factor_one<T, MAXNB>(A, e.n, P, s_rinv, &s_fail, rdiag);
         if (threadIdx.x == 0) info[e.index] = fail;
         __syncthreads();
         // up to kMaxRhs right-hand sides per pass; the factor (n <= 512) stays in L2
@@ -602,7 +487,7 @@ template <typename T, int MAXNB>
 cudaError_t launch_batched(int64_t batch, PlanHeader *hdr, const PlanEntry *table, T *arf, T *B,
                            int32_t *info, cudaStream_t st)
 {
-    const int smem = smem_elems<T>(MAXNB) * (int)sizeof(T);
+    const int smem = smem_elems(MAXNB) * (int)sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(batched_kernel<T, MAXNB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
