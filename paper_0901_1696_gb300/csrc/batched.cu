@@ -170,10 +170,21 @@ __device__ int factor_one(const Mat<T> &A, int64_t n, T *P, T *s_rinv, int *s_fa
         const int kb = (int)(n - k0 < NB ? n - k0 : NB);
         const int rows = (int)(n - k0);
         const int rpad = (rows + 3) & ~3;
-        // 1. panel -> shared memory; zero above the diagonal and in the row padding
-        for (int c = 0; c < kb; ++c)
-            for (int r = tid; r < rpad; r += blockDim.x)
-                P[c * LDC + r] = (r >= c && r < rows) ? *A.at(k0 + r, k0 + c) : T(0);
+        // 1. panel -> shared memory; zero above the diagonal and in the row
+        // padding.  A thread's loads of one row go out eight at a time (one
+        // L2 latency per eight elements instead of one per element).
+        for (int r = tid; r < rpad; r += blockDim.x)
+            for (int c0 = 0; c0 < kb; c0 += 8) {
+                T v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = c0 + u;
+                    v[u] = (c < kb && r >= c && r < rows) ? *A.at(k0 + r, k0 + c) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c0 + u < kb) P[(c0 + u) * LDC + r] = v[u];
+            }
         if (tid == 0) *s_fail = -1;
         __syncthreads();
         // 2. right-looking Cholesky of the rows x kb panel: in registers in
@@ -315,10 +326,19 @@ __device__ __forceinline__ void rows_update_r(const Mat<T> &A, int64_t n, int64_
     const int64_t lo = FWD ? k0 + kb : 0, hi = FWD ? n : k0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         T acc[R] = {};
-        for (int c = 0; c < kb; ++c) {
-            const T l = FWD ? *A.at(i, k0 + c) : *A.at(k0 + c, i);
+        // eight loads of the row of L issued together, then their products
+        for (int c0 = 0; c0 < kb; c0 += 8) {
+            T l[8];
 #pragma unroll
-            for (int q = 0; q < R; ++q) acc[q] = fma(l, Y[c * kMaxRhs + q], acc[q]);
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + u;
+                l[u] = c < kb ? (FWD ? *A.at(i, k0 + c) : *A.at(k0 + c, i)) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < kb)
+#pragma unroll
+                    for (int q = 0; q < R; ++q) acc[q] = fma(l[u], Y[(c0 + u) * kMaxRhs + q], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) Bm[i + q * ldb] -= acc[q];
@@ -355,9 +375,18 @@ __device__ void solve_one(const Mat<T> &A, int64_t n, T *Bm, int64_t ldb, int nr
     const int64_t nblk = (n + SB - 1) / SB;
     for (int e = tid; e < SB * kMaxRhs; e += blockDim.x) Y[e] = T(0);
     auto stage_diag = [&](int64_t k0, int kb) {
-        for (int e = tid; e < kb * kb; e += blockDim.x) {
-            const int r = e % kb, c = e / kb;
-            D[r * LDD + c] = (r >= c) ? *A.at(k0 + r, k0 + c) : T(0);
+        // the block's (at most) 4 elements per thread loaded together
+        constexpr int Q = (SB * SB + kBatchThreads - 1) / kBatchThreads;
+        T v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int e = tid + q * kBatchThreads, r = e % SB, c = e / SB;
+            v[q] = (r < kb && c < kb && r >= c) ? *A.at(k0 + r, k0 + c) : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int e = tid + q * kBatchThreads, r = e % SB, c = e / SB;
+            if (r < kb && c < kb) D[r * LDD + c] = v[q];
         }
         __syncthreads();
         if (tid < kb) rdiag[tid] = T(1) / D[tid * LDD + tid];
