@@ -10,7 +10,7 @@
 //   forward, block row b:   X_b = L_bb^{-1} (B_b - sum_{j<b} L_bj X_j)
 //   backward, block row b:  X_b = L_bb^{-T} (Y_b - sum_{j>b} L_jb^T X_j).
 // One launch per direction computes all of it.  A task is (block row b,
-// group g of 16 right-hand-side columns).  Tasks take tickets from a device
+// group g of G right-hand-side columns, G = 8 or 16).  Tasks take tickets from a device
 // counter in solve order (block rows in solve order, then column groups).
 // For each group, blocks complete in solve order (block b needs every
 // earlier one), so one progress word per group says how many of its blocks
@@ -38,10 +38,10 @@ namespace rfp {
 
 namespace {
 
-constexpr int kG = 16;              // right-hand sides per task
+// Right-hand sides per task (G): 16, or 8 when there are at most 16 of them
+// (two chains of half the work each instead of one).
 constexpr int kKc = 16;             // K chunk staged in shared memory
 constexpr int kThreads = 128;
-constexpr int kXsLd = kG + 2;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kErrWait = 4;
 // Block rows: 64 for large orders (fewer, larger tasks), 32 up to
@@ -111,15 +111,15 @@ __device__ __forceinline__ bool wait_progress(const int32_t *prog, int need, int
 }
 
 // Staging of one R x 16 chunk of op(L_jb) (rows r < rv of the task's block,
-// k in [k0, k0 + 16) < kv) and of the matching 16 x 16 chunk of X_j.
+// k in [k0, k0 + 16) < kv) and of the matching 16 x G chunk of X_j.
 // A(r, k) = V(r, k) for a view V; both loaders read along their view's unit
 // stride (X's rows for a right-hand-side block, its columns for a
 // transposed RFP block).
-template <int R>
+template <int R, int G>
 struct ChunkRegs {
-    static constexpr int AQ = R * kKc / kThreads, ALd = R + 2;
+    static constexpr int AQ = R * kKc / kThreads, ALd = R + 2, XQ = kKc * G / kThreads, XLd = G + 2;
     double a[AQ];
-    double x[kKc * kG / kThreads];   // 2
+    double x[XQ];
 
     __device__ __forceinline__ void load(View<double> V, int rv, int k0, int kv, View<double> Xj,
                                          int cols)
@@ -140,20 +140,20 @@ struct ChunkRegs {
         }
         if (Xj.rs == 1) {     // X rows contiguous
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int k = k0 + tid % kKc, c = tid / kKc + 8 * q;
+            for (int q = 0; q < XQ; ++q) {
+                const int k = k0 + tid % kKc, c = tid / kKc + (kThreads / kKc) * q;
                 x[q] = (k < kv && c < cols) ? __ldcg(&Xj(k, c)) : 0.0;
             }
         } else {              // X columns contiguous
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int c = tid % kG, k = k0 + tid / kG + 8 * q;
+            for (int q = 0; q < XQ; ++q) {
+                const int c = tid % G, k = k0 + tid / G + (kThreads / G) * q;
                 x[q] = (k < kv && c < cols) ? __ldcg(&Xj(k, c)) : 0.0;
             }
         }
     }
     __device__ __forceinline__ void store(const View<double> &V, bool xrowfast, double (*As)[ALd],
-                                          double (*Xs)[kXsLd]) const
+                                          double (*Xs)[XLd]) const
     {
         const int tid = threadIdx.x;
         if (V.rs == 1) {
@@ -165,46 +165,48 @@ struct ChunkRegs {
         }
         if (xrowfast) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) Xs[tid % kKc][tid / kKc + 8 * q] = x[q];
+            for (int q = 0; q < XQ; ++q) Xs[tid % kKc][tid / kKc + (kThreads / kKc) * q] = x[q];
         } else {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) Xs[tid / kG + 8 * q][tid % kG] = x[q];
+            for (int q = 0; q < XQ; ++q) Xs[tid / G + (kThreads / G) * q][tid % G] = x[q];
         }
     }
 };
 
-template <int R>
+template <int R, int G>
 struct UpdateSmem {
     double As[2][kKc][R + 2];
-    double Xs[2][kKc][kXsLd];
+    double Xs[2][kKc][G + 2];
 };
-template <int R>
+template <int R, int G>
 struct DiagSmem {
     double Ld[R][R + 1];        // lower triangle of L_bb
-    double Bs[R][kG + 1];       // the block's right-hand side, redistributed
+    double Bs[R][G + 1];        // the block's right-hand side, redistributed
     double rinv[R];             // 1 / L_bb(j, j)
 };
 // 64-row blocks share one region between the update's staging and the
 // diagonal block; 32-row blocks keep both (26 KB), so that the diagonal
 // block is loaded before the task's first wait, off the critical path.
-template <int R>
+template <int R, int G>
 union SolveSmemShared {
-    UpdateSmem<R> u;
-    DiagSmem<R> d;
+    UpdateSmem<R, G> u;
+    DiagSmem<R, G> d;
 };
-template <int R>
+template <int R, int G>
 struct SolveSmemSplit {
-    UpdateSmem<R> u;
-    DiagSmem<R> d;
+    UpdateSmem<R, G> u;
+    DiagSmem<R, G> d;
 };
-template <int R>
-using SolveSmem = std::conditional_t<R == 32, SolveSmemSplit<R>, SolveSmemShared<R>>;
+template <int R, int G>
+using SolveSmem = std::conditional_t<R == 32, SolveSmemSplit<R, G>, SolveSmemShared<R, G>>;
 
-template <bool TRANS, int R>
+template <bool TRANS, int R, int G>
 __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 {
-    constexpr int RM = R / 16;       // rows per thread in the update (16 row groups)
-    __shared__ __align__(16) SolveSmem<R> sm;
+    constexpr int CP = G / 2;                 // column pairs of the update
+    constexpr int RM = R * CP / kThreads;     // rows per thread in the update
+    static_assert(RM >= 1 && R * CP == RM * kThreads, "update layout");
+    __shared__ __align__(16) SolveSmem<R, G> sm;
     __shared__ int s_ticket, s_ok;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     const int ticket = s_ticket;
     const int g = ticket % a.ng, p = ticket / a.ng;          // p: position in solve order
     const int b = TRANS ? a.nb - 1 - p : p;
-    const int64_t c0 = (int64_t)g * kG;
+    const int64_t c0 = (int64_t)g * G;
     // A lower-triangular right-hand side (forward): the group's columns are
     // zero above row c0 in B and in the solution, so blocks above c0's block
     // are left as they are, publish nothing, and are not read below.
@@ -225,11 +227,11 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     int64_t r0;
     int rows;
     block_rows<R>(a, b, r0, rows);
-    const int cols = (int)(a.nrhs - c0 < kG ? a.nrhs - c0 : kG);
+    const int cols = (int)(a.nrhs - c0 < G ? a.nrhs - c0 : G);
     const View<double> Xb = a.X.sub(r0, c0);
     int32_t *prog = a.prog + g;
 
-    const int tx = tid % 8, ty = tid / 8;                    // 2 columns x RM rows each
+    const int tx = tid % CP, ty = tid / CP;                  // 2 columns x RM rows each
     double acc[RM][2];
 #pragma unroll
     for (int m = 0; m < RM; ++m)
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
         const View<double> V = TRANS ? lblock<R>(a, j, b).t() : lblock<R>(a, b, j);
         const View<double> Xj = a.X.sub(j0, c0);
         const int nch = (kv + kKc - 1) / kKc;
-        ChunkRegs<R> st;
+        ChunkRegs<R, G> st;
         st.load(V, rows, 0, kv, Xj, cols);
         for (int ch = 0; ch < nch; ++ch) {
             const int buf = ch & 1;
@@ -291,11 +293,16 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 #pragma unroll
             for (int kk = 0; kk < kKc; ++kk) {
                 double av[RM];
+                if constexpr (RM % 2 == 0) {
 #pragma unroll
-                for (int m = 0; m < RM; m += 2) {
-                    const double2 t2 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * RM + m]);
-                    av[m] = t2.x;
-                    av[m + 1] = t2.y;
+                    for (int m = 0; m < RM; m += 2) {
+                        const double2 t2 = *reinterpret_cast<const double2 *>(&sm.u.As[buf][kk][ty * RM + m]);
+                        av[m] = t2.x;
+                        av[m + 1] = t2.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < RM; ++m) av[m] = sm.u.As[buf][kk][ty * RM + m];
                 }
                 const double2 x = *reinterpret_cast<const double2 *>(&sm.u.Xs[buf][kk][tx * 2]);
 #pragma unroll
@@ -329,31 +336,33 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
         for (int c = 0; c < 2; ++c) sm.d.Bs[ty * RM + m][tx * 2 + c] = acc[m][c];
     __syncthreads();
 
-    // Substitution.  Lane (lr, lc) = (lane / 4, lane % 4) of warp w holds
-    // column 4 w + lc of rows lr + 8 k, k < R / 8.  Step j: the four lanes
+    // Substitution.  Warp w takes columns CW w .. CW w + CW - 1 (CW = G / 4);
+    // lane (lr, lc) = (lane / CW, lane % CW) holds column CW w + lc of rows
+    // lr + RG k, k < R / RG (RG = 32 / CW row groups).  Step j: the CW lanes
     // holding row j scale it by the pivot's reciprocal (one instruction for
-    // the four columns), a shuffle hands each lane its column's x_j, and
+    // the warp's columns), a shuffle hands each lane its column's x_j, and
     // every lane removes x_j from its later (forward) or earlier (backward)
     // rows; registers whose rows are all finished drop out of the step at
     // compile time.  On GB300's FP64 pipe, where a warp instruction costs
     // the same whatever its active lanes, this is about 3.5 instructions a
-    // step for 32-row blocks against 8 with one lane per row.
-    constexpr int K = R / 8;
-    const int lr = lane >> 2, lc = lane & 3, col = warp * 4 + lc;
+    // step for 32-row blocks of 16 columns (2.5 for 8) against 8 with one
+    // lane per row.
+    constexpr int CW = G / 4, RG = 32 / CW, K = R / RG;
+    const int lr = lane / CW, lc = lane % CW, col = warp * CW + lc;
     double v[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = sm.d.Bs[lr + 8 * k][col];
+    for (int k = 0; k < K; ++k) v[k] = sm.d.Bs[lr + RG * k][col];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int j = TRANS ? R - 1 - q : q;
         if (j < rows) {    // uniform
-            const int kj = j >> 3, oj = j & 7;
-            const double xj = __shfl_sync(0xffffffffu, v[kj] * sm.d.rinv[j], oj * 4 + lc);
+            const int kj = j / RG, oj = j % RG;
+            const double xj = __shfl_sync(0xffffffffu, v[kj] * sm.d.rinv[j], oj * CW + lc);
             if (lr == oj) v[kj] = xj;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 if (TRANS ? k > kj : k < kj) continue;
-                const int r = lr + 8 * k;
+                const int r = lr + RG * k;
                 if (TRANS ? r < j : (r > j && r < rows)) {
                     const double l = TRANS ? sm.d.Ld[j][r] : sm.d.Ld[r][j];
                     v[k] = fma(-l, xj, v[k]);
@@ -364,18 +373,18 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
     // out through shared memory, along X's unit stride
     __syncthreads();   // every lane is done reading Bs
 #pragma unroll
-    for (int k = 0; k < K; ++k) sm.d.Bs[lr + 8 * k][col] = v[k];
+    for (int k = 0; k < K; ++k) sm.d.Bs[lr + RG * k][col] = v[k];
     __syncthreads();
     if (Xb.rs == 1) {      // X's rows contiguous
 #pragma unroll
-        for (int q = 0; q < R * kG / kThreads; ++q) {
+        for (int q = 0; q < R * G / kThreads; ++q) {
             const int r = tid % R, cc = tid / R + (kThreads / R) * q;
             if (r < rows && cc < cols) Xb(r, cc) = sm.d.Bs[r][cc];
         }
     } else {               // X's columns contiguous
 #pragma unroll
-        for (int q = 0; q < R * kG / kThreads; ++q) {
-            const int cc = tid % kG, r = tid / kG + (kThreads / kG) * q;
+        for (int q = 0; q < R * G / kThreads; ++q) {
+            const int cc = tid % G, r = tid / G + (kThreads / G) * q;
             if (r < rows && cc < cols) Xb(r, cc) = sm.d.Bs[r][cc];
         }
     }
@@ -386,9 +395,14 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 
 }  // namespace
 
+// Right-hand sides per task: 8 when there are at most 16 (two chains, each
+// with half the update per block and a shorter substitution), else 16.
+static int64_t group_width(int64_t nrhs) { return nrhs <= 16 ? 8 : 16; }
+
 size_t rfp_solve_sync_words(int64_t nrhs)
 {
-    return (size_t)(2 + (nrhs + kG - 1) / kG);
+    const int64_t G = group_width(nrhs);
+    return (size_t)(2 + (nrhs + G - 1) / G);
 }
 
 cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<double> t2, int64_t n1,
@@ -399,7 +413,8 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     if (lower_rhs && (trans || n2 != 0)) return cudaErrorInvalidValue;
     const int64_t R = n <= kSmallSolve ? 32 : 64;
-    const int64_t nb1 = (n1 + R - 1) / R, nb2 = (n2 + R - 1) / R, ng = (nrhs + kG - 1) / kG;
+    const int64_t G = group_width(nrhs);
+    const int64_t nb1 = (n1 + R - 1) / R, nb2 = (n2 + R - 1) / R, ng = (nrhs + G - 1) / G;
     const int64_t tasks = (nb1 + nb2) * ng;
     if (tasks > INT32_MAX) return cudaErrorInvalidValue;
     // sync: [0] ticket counter, [1] error word, [2 .. 2 + ng) progress per
@@ -408,12 +423,19 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
     if (e != cudaSuccess) return e;
     SolveArgs a{t1, s, t2, n1, n2, (int)nb1, (int)(nb1 + nb2), X, nrhs, (int)ng,
                 sync, sync + 2, sync + 1, abort, alpha, lower_rhs ? 1 : 0};
-    if (R == 32) {
-        if (trans) rfp_solve_kernel<true, 32><<<(unsigned)tasks, kThreads, 0, st>>>(a);
-        else rfp_solve_kernel<false, 32><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+    const unsigned grid = (unsigned)tasks;
+    if (R == 32 && G == 8) {
+        if (trans) rfp_solve_kernel<true, 32, 8><<<grid, kThreads, 0, st>>>(a);
+        else rfp_solve_kernel<false, 32, 8><<<grid, kThreads, 0, st>>>(a);
+    } else if (R == 32) {
+        if (trans) rfp_solve_kernel<true, 32, 16><<<grid, kThreads, 0, st>>>(a);
+        else rfp_solve_kernel<false, 32, 16><<<grid, kThreads, 0, st>>>(a);
+    } else if (G == 8) {
+        if (trans) rfp_solve_kernel<true, 64, 8><<<grid, kThreads, 0, st>>>(a);
+        else rfp_solve_kernel<false, 64, 8><<<grid, kThreads, 0, st>>>(a);
     } else {
-        if (trans) rfp_solve_kernel<true, 64><<<(unsigned)tasks, kThreads, 0, st>>>(a);
-        else rfp_solve_kernel<false, 64><<<(unsigned)tasks, kThreads, 0, st>>>(a);
+        if (trans) rfp_solve_kernel<true, 64, 16><<<grid, kThreads, 0, st>>>(a);
+        else rfp_solve_kernel<false, 64, 16><<<grid, kThreads, 0, st>>>(a);
     }
     note_launch();
     return cudaGetLastError();

@@ -378,14 +378,20 @@ cudaError_t trsm_wavefront(cudaStream_t, View<float> Lv, int64_t n, const float 
     return L.commit();
 }
 
-// rfp_solve: one ordered launch of (block row, 16-column group) tasks in
+// rfp_solve: one ordered launch of (block row, column group) tasks in
 // ticket order (block rows in solve order, then column groups).  Each task
 // reads its rows of X, the blocks of L to the left of its diagonal block
 // (forward) or below it (backward), transposed for the backward solve, and the
 // final X blocks of the earlier tasks of its group; it writes its X block
 // and its group's progress word.  L is addressed through the three RFP block
 // views exactly as the kernel addresses it.
-size_t rfp_solve_sync_words(int64_t nrhs) { return (size_t)(2 + (nrhs + 15) / 16); }
+// right-hand sides per task, as the kernel picks them
+static int64_t solve_group(int64_t nrhs) { return nrhs <= 16 ? 8 : 16; }
+size_t rfp_solve_sync_words(int64_t nrhs)
+{
+    const int64_t G = solve_group(nrhs);
+    return (size_t)(2 + (nrhs + G - 1) / G);
+}
 
 cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double> t2, int64_t n1,
                       int64_t n2, View<double> Xv, int64_t nrhs, bool trans, int32_t *sync,
@@ -395,7 +401,8 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     if (lower_rhs && (trans || n2 != 0)) return cudaErrorInvalidValue;
     const int64_t R = n <= 4096 ? 32 : 64;             // block rows, as the kernel picks them
-    const int64_t nb1 = (n1 + R - 1) / R, nb = nb1 + (n2 + R - 1) / R, ng = (nrhs + 15) / 16;
+    const int64_t G = solve_group(nrhs);
+    const int64_t nb1 = (n1 + R - 1) / R, nb = nb1 + (n2 + R - 1) / R, ng = (nrhs + G - 1) / G;
     Launch L;
     L.ordered = true;
     for (size_t w = 0; w < rfp_solve_sync_words(nrhs); ++w) L.wr(sync + w, 0);   // the memset
@@ -418,7 +425,7 @@ cudaError_t rfp_solve(cudaStream_t, View<double> t1, View<double> s, View<double
         L.cta = (int)t;
         L.wr(sync, (int32_t)(t + 1));                       // ticket counter
         const int64_t g = t % ng, p = t / ng, b = trans ? nb - 1 - p : p;
-        const int64_t c0 = g * 16, cols = std::min<int64_t>(16, nrhs - c0);
+        const int64_t c0 = g * G, cols = std::min<int64_t>(G, nrhs - c0);
         const int64_t jf = lower_rhs ? c0 / R : 0;   // blocks above stay zero, untouched
         if (b < jf) continue;
         int64_t r0, rows;
