@@ -29,8 +29,10 @@
 // each lane holding one column of R/8 rows, the solved values handed out by
 // shuffles.
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "rfp_internal.cuh"
 
@@ -395,6 +397,43 @@ __global__ void __launch_bounds__(kThreads) rfp_solve_kernel(SolveArgs a)
 
 }  // namespace
 
+// Dynamic shared memory that leaves room for one CTA of `fn` per SM (0 if
+// the device attributes cannot be read or set), cached per device and kernel.
+// A wide solve of a small triangle (many column groups, little work each)
+// is bound by its diagonal chain; with several resident tasks per SM the
+// tasks on that chain share their SM's FP64 pipe with tasks that are only
+// accumulating earlier blocks.  One per SM: n = 1001's 500-column solves
+// went from about 316 to 254 us (two per SM: 266 us).
+static int one_cta_per_sm_smem(const void *fn)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find({dev, fn});
+        if (it != cache.end()) return it->second;
+    }
+    int dyn = 0, per_sm = 0, per_block = 0;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess &&
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+        dyn = per_sm / 2 + 1 - (int)fa.sharedSizeBytes;   // two such CTAs exceed the SM
+        if (dyn < 0 || dyn + (int)fa.sharedSizeBytes > per_block ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+            dyn = 0;
+    }
+    (void)cudaGetLastError();   // a failed query is not the caller's error
+    std::lock_guard<std::mutex> lock(mu);
+    cache[{dev, fn}] = dyn;
+    return dyn;
+}
+
 // Right-hand sides per task: 8 when there are at most 16 (two chains, each
 // with half the update per block and a shorter substitution), else 16.
 static int64_t group_width(int64_t nrhs) { return nrhs <= 16 ? 8 : 16; }
@@ -428,8 +467,13 @@ cudaError_t rfp_solve(cudaStream_t st, View<double> t1, View<double> s, View<dou
         if (trans) rfp_solve_kernel<true, 32, 8><<<grid, kThreads, 0, st>>>(a);
         else rfp_solve_kernel<false, 32, 8><<<grid, kThreads, 0, st>>>(a);
     } else if (R == 32) {
-        if (trans) rfp_solve_kernel<true, 32, 16><<<grid, kThreads, 0, st>>>(a);
-        else rfp_solve_kernel<false, 32, 16><<<grid, kThreads, 0, st>>>(a);
+        // wide and small: one task per SM (see one_cta_per_sm_smem)
+        const bool cap = ng >= 8 && n * nrhs <= (int64_t(1) << 19);
+        const void *fn = trans ? (const void *)rfp_solve_kernel<true, 32, 16>
+                               : (const void *)rfp_solve_kernel<false, 32, 16>;
+        const int dyn = cap ? one_cta_per_sm_smem(fn) : 0;
+        if (trans) rfp_solve_kernel<true, 32, 16><<<grid, kThreads, dyn, st>>>(a);
+        else rfp_solve_kernel<false, 32, 16><<<grid, kThreads, dyn, st>>>(a);
     } else if (G == 8) {
         if (trans) rfp_solve_kernel<true, 64, 8><<<grid, kThreads, 0, st>>>(a);
         else rfp_solve_kernel<false, 64, 8><<<grid, kThreads, 0, st>>>(a);
